@@ -1,0 +1,219 @@
+/*
+ * kpsb.h - C ABI of the GB300 (sm_103a) Kronecker-product-sum split Bregman library.
+ *
+ * Method: Alsubhi & Renaut, "Split Bregman isotropic and anisotropic image deblurring
+ * with Kronecker product sum approximations using single precision enlarged-GKB or RSVD
+ * algorithms to provide low rank truncated SVDs" (arXiv 2410.00233).  Section, algorithm
+ * and equation numbers below refer to that paper.
+ *
+ * Conventions shared by every entry point
+ *  - Images, PSFs, factors and blocks of vectors are COLUMN-MAJOR (the paper's vec/array,
+ *    Sec. 1): element (i, j) of an m x n array is at [i + j*m].
+ *  - Square images only (m1 = m2 = n1 = n2 = n, Sec. 5.1): R(A) is n^2 x n^2.
+ *  - A PSF is s0 x s1 (rows x columns) with its centre tap at (s0/2, s1/2) (integer
+ *    division).  Blur = convolution:  b(r,c) = sum_{a,b} P(a,b) x(ext(r-a+s0/2), ext(c-b+s1/2)).
+ *    Zero boundary: out-of-range pixels are 0.  Reflexive boundary: half-sample mirror
+ *    (x[-1] = x[0], x[n] = x[n-1]); requires s0/2 <= n, s1/2 <= n and s-1-s/2 <= n.
+ *  - Every function returns a kpsb_status (0 = success, < 0 = error) and never throws;
+ *    kpsb_last_error() gives a thread-local message for the last failure.
+ *  - Host pointers ("host") are read/written synchronously: the call returns when the
+ *    data is in place.  Device pointers ("dev") must be device-accessible memory of the
+ *    current CUDA device; *_dev calls are asynchronous on the given stream (a
+ *    cudaStream_t passed as void*, NULL = the legacy default stream) unless stated.
+ *  - The caller owns every buffer it passes.  A kpsb_kp_t handle owns its device memory
+ *    until kp_free().  Handles are not thread-safe: use one per thread or lock.
+ */
+#ifndef KPSB_H
+#define KPSB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KPSB_OK = 0,
+  KPSB_EINVAL = -1,     /* invalid argument (size, pointer, option) */
+  KPSB_ENOMEM = -2,     /* device or host allocation failed */
+  KPSB_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+  KPSB_ETIMEOUT = -4,   /* a bounded device wait ran out (see kpsb_last_error) */
+  KPSB_EBREAKDOWN = -5, /* GKB/RSVD found no usable direction (k would be 0) */
+  KPSB_ENOTCONV = -6,   /* iteration hit its limit where convergence was required */
+  KPSB_EBUSY = -7,      /* admission refused: not enough free memory / slots */
+  KPSB_ENOTFOUND = -8   /* unknown request id */
+} kpsb_status;
+
+enum { KPSB_BC_ZERO = 0, KPSB_BC_REFLEXIVE = 1 };
+enum { KPSB_EGKB = 0, KPSB_RSVD = 1 };
+enum { KPSB_ANISO = 0, KPSB_ISO = 1 };
+/* Arithmetic of the Kronecker-sum GEMMs inside sb_solve / kp_apply.  Vectors, stopping
+ * tests and shrinkage are FP64 in every mode.
+ *  FP64  : FP64 FMA of the FP32 factors (exact in FP64) with FP64 images.
+ *  FP32  : FP32 FMA, images rounded to FP32, FP32 accumulation.
+ *  TF32X3: tensor cores (tcgen05 kind::tf32), each operand split into two TF32 parts,
+ *          three products accumulated in FP32 (error ~ FP32 rounding).
+ *  BF16X3: tensor cores (tcgen05 kind::f16, bf16), two bf16 parts, three products. */
+enum { KPSB_P_FP64 = 0, KPSB_P_FP32 = 1, KPSB_P_TF32X3 = 2, KPSB_P_BF16X3 = 3 };
+/* Shrinkage threshold of the d-subproblem argmin lambda^2||d-c||^2 + beta||d||_1
+ * (Sec. 3.2-3.3): EXACT = beta/(2 lambda^2) (its exact minimiser), PAPER = beta/lambda^2
+ * (the printed 1/gamma, which minimises with 2*beta). */
+enum { KPSB_THR_EXACT = 0, KPSB_THR_PAPER = 1 };
+
+typedef struct kpsb_kp* kpsb_kp_t;
+
+/* Options of kp_build; zero-initialise and set what you need (0 selects the default). */
+typedef struct {
+  int p;             /* enlargement (EGKB) / oversampling (RSVD): k_p = k + p.  Default
+                        max(2, ceil(k/4)) */
+  int k_min;         /* automatic rank: smallest k the nu rule may pick (default 3) */
+  int one_sided;     /* EGKB: 1 = reorthogonalise only the q_j (Alg. 1 step 6); default 0
+                        = also the s_j (the single-precision variant, Sec. 4.4) */
+  int power_iters;   /* RSVD power iterations q (Alg. 2 step 2), default 1 */
+  unsigned long long seed; /* Philox4x32-10 seed for the start vector / test matrix */
+  const float* start_host; /* optional host input: EGKB start vector y (n^2), or RSVD test
+                        matrix F (n^2 x k_p, column-major).  NULL = Philox + Box-Muller */
+  void* stream;      /* cudaStream_t for the work (NULL = legacy default stream) */
+} kpsb_build_opts;
+
+/* Options of sb_solve; zero-initialise, 0 selects the default. */
+typedef struct {
+  double beta;       /* TV weight beta; <= 0: beta = lambda^2/gamma with gamma = 2 (Sec. 5.3.1) */
+  double tau_sb;     /* stop when RC_SB (5.2) < tau_sb; 0 (default) runs all `iters` steps */
+  double tau_cgls;   /* CGLS stop on RC_CGLS (5.1) < tau_cgls; default 1e-4 */
+  int i_max;         /* CGLS iteration limit I_max; default 100 */
+  int fixed_inner;   /* 1: exactly i_max CGLS steps per outer step (no RC_CGLS test) */
+  int prec;          /* KPSB_P_* for the KP GEMMs; default KPSB_P_FP64 */
+  int threshold_rule;/* KPSB_THR_EXACT (default) or KPSB_THR_PAPER */
+  void* stream;      /* cudaStream_t */
+} kpsb_sb_opts;
+
+typedef struct {
+  int l_end;         /* outer (split Bregman) steps taken */
+  int iota_total;    /* total CGLS steps */
+  double rc_sb;      /* last RC_SB */
+  int status;        /* kpsb_status of this solve */
+} kpsb_sb_stats;
+
+/* ---- Build: TSVD of R(A) and Terms(A_k) ------------------------------------------------
+ * kp_build: approximate truncated SVD of the rearranged blur matrix R(A) (Sec. 2.1,
+ * eq. (2.2)) in FP32 by EGKB (Alg. 1, Sec. 2.2) or RSVD (Alg. 2, Sec. 2.3), R(A) applied
+ * matrix-free through the PSF's index map, then the KP terms (Theorem 2.1, Sec. 4.1.3):
+ * A ~ sum_i sigma_i Ax_i (x) Ay_i, Ax_i = array(u_i, n, n), Ay_i = array(v_i, n, n).
+ *   psf        host, s0 x s1 column-major FP64 (any scale; used as given)
+ *   rank_or_tol >= 1: fixed rank k = (int)rank_or_tol.  In (0,1): EGKB only, automatic
+ *              rank by the nu_j rule (eq. (2.6)) with relative tolerance tau = rank_or_tol
+ *              (nu_i < tau*nu_3), capped at k <= 30.
+ *   method     KPSB_EGKB or KPSB_RSVD.
+ *   out        receives a new handle (device factors resident until kp_free).
+ * The effective k may be smaller than asked when R(A) has smaller rank (rank <= s0*s1):
+ * the GKB recurrence stops at breakdown and RSVD drops null directions; kp_info reports
+ * the k and k_p used.  Errors: EINVAL (sizes, n < 2, s > 2n, k < 1, k_p > 64),
+ * ENOMEM, ECUDA, EBREAKDOWN (R(A) = 0). */
+kpsb_status kp_build(const double* psf, int s0, int s1, int n, int bc, double rank_or_tol,
+                     int method, const kpsb_build_opts* opts, kpsb_kp_t* out);
+
+/* Size of a handle: n, number of terms k, enlarged size k_p; sigma (host, length >= k)
+ * receives sigma_1 >= ... >= sigma_k (FP64).  Any output pointer may be NULL. */
+kpsb_status kp_info(kpsb_kp_t kp, int* n, int* k, int* kp_size, double* sigma);
+
+/* Host copies of the factors: Ax, Ay are k x (n x n) column-major FP32 (unit Frobenius
+ * norm each; the largest-magnitude entry of each Ay_i is positive), sigma FP64 (k).
+ * Any pointer may be NULL. */
+kpsb_status kp_get_factors(kpsb_kp_t kp, float* Ax, float* Ay, double* sigma);
+
+/* Make a handle from given factors (host, same layout as kp_get_factors): lets a caller
+ * run sb_solve on identical factors, or reuse cached ones. */
+kpsb_status kp_from_factors(int n, int k, const float* Ax, const float* Ay,
+                            const double* sigma, kpsb_kp_t* out);
+
+/* KP apply (Sec. 4.2, eq. (4.3)): Y = sum_i sigma_i Ay_i X Ax_i^T (transpose = 0) or
+ * X' = sum_i sigma_i Ay_i^T Y Ax_i (transpose = 1).  X, Y: n x n column-major FP64.
+ * kp_apply: host pointers (synchronous).  kp_apply_dev: device pointers, async on
+ * stream.  prec: KPSB_P_*.  X and Y must not overlap. */
+kpsb_status kp_apply(kpsb_kp_t kp, const double* X, double* Y, int transpose, int prec);
+kpsb_status kp_apply_dev(kpsb_kp_t kp, const double* X, double* Y, int transpose, int prec,
+                         void* stream);
+
+void kp_free(kpsb_kp_t kp);
+
+/* ---- Split Bregman deblurring -----------------------------------------------------------
+ * sb_solve: Alg. 3 (tv = KPSB_ANISO) or Alg. 4 (KPSB_ISO) with the KP operator of `kp`
+ * in place of A:  min_x mu||A_k x - b||^2 + beta TV(x), splitting penalty lambda^2, L the
+ * 1/2 forward difference with a zero last row (Sec. 5.3), x^(0) = b, d = g = 0.  Each
+ * outer step solves (3.7) by CGLS (Alg. 5) from x = 0 on
+ * Ahat = [sqrt(mu) A_k; lambda (L (x) I); lambda (I (x) L)], then shrinks (3.10)/(3.13)
+ * and updates g (3.8)-(3.9).  iters = L_max.
+ *   b, x_out: host n x n column-major FP64.  stats may be NULL.
+ * Errors: EINVAL (mu <= 0, lambda <= 0, iters < 1), ENOMEM, ECUDA. */
+kpsb_status sb_solve(kpsb_kp_t kp, const double* b, double mu, double lambda, int tv,
+                     int iters, const kpsb_sb_opts* opts, double* x_out,
+                     kpsb_sb_stats* stats);
+/* Same with device b and x_out (n x n FP64 each), async on opts->stream; stats (host) is
+ * filled when the call returns (the call synchronises the stream at its end). */
+kpsb_status sb_solve_dev(kpsb_kp_t kp, const double* b, double mu, double lambda, int tv,
+                         int iters, const kpsb_sb_opts* opts, double* x_out,
+                         kpsb_sb_stats* stats);
+
+/* ---- Batched (many independent problems in one set of launches) ------------------------ */
+typedef struct {
+  const double* psf; int s0, s1; int n; int bc; double rank_or_tol; int method;
+  kpsb_build_opts opts;  /* opts.stream is ignored: the batch picks its streams */
+} kpsb_problem;
+
+/* Builds `count` handles; problems run concurrently on internal streams.  outs[i] is
+ * NULL where problem i failed; the first error is returned. */
+kpsb_status kp_build_batched(int count, const kpsb_problem* probs, kpsb_kp_t* outs);
+
+typedef struct {
+  kpsb_kp_t kp;       /* factors (n taken from it) */
+  const double* b;    /* n x n FP64, host or device (see on_device) */
+  double* x;          /* n x n FP64 output, host or device */
+  double mu, lambda, beta; /* beta <= 0: lambda^2/2 */
+  int tv;             /* KPSB_ANISO / KPSB_ISO */
+  int iters;          /* L_max */
+  kpsb_sb_stats* stats; /* may be NULL */
+} kpsb_sb_job;
+
+/* Solves `count` jobs together: jobs with the same n share every launch (grouped GEMMs
+ * and vector kernels over problems, each problem with its own k and stopping state).
+ * on_device = 1: b and x are device pointers.  opts gives the shared settings (tau,
+ * i_max, prec, rule, stream).  The result of each job equals its sb_solve alone, up to
+ * the GEMM's rounding (identical in FP64/FP32 modes). */
+kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int on_device,
+                             const kpsb_sb_opts* opts);
+
+/* ---- Steps of the hot path, exposed for tests and composition -------------------------- */
+
+/* Blur with the exact operator A (Sec. 1): B = A X (transpose = 0) or A^T X (1).
+ * psf device FP64 s0 x s1; X, B device n x n FP64 (must not overlap).  Async. */
+kpsb_status kp_blur_dev(const double* psf, int s0, int s1, int n, int bc, const double* X,
+                        double* B, int transpose, void* stream);
+
+/* Matrix-free block apply of R(A) (eq. (2.2), R(A) = Kx P^T Ky^T through the index map):
+ * U = R(A) V (transpose = 0) or U = R(A)^T V (1).  psf device FP32 s0 x s1; V, U device
+ * n^2 x nb FP32 with leading dimension ldv, ldu >= n^2 (must not overlap).  Uses library
+ * scratch memory owned per device (allocated on first use).  Async. */
+kpsb_status kp_ra_apply_dev(const float* psf, int s0, int s1, int n, int bc, const float* V,
+                            int ldv, int nb, float* U, int ldu, int transpose, void* stream);
+
+/* Materialise R(A) densely from the index map (n^2 x n^2 FP32, column-major, device;
+ * n <= 128).  Each entry is a sum of PSF taps in a fixed order.  Async. */
+kpsb_status kp_ra_materialize_dev(const float* psf, int s0, int s1, int n, int bc, float* R,
+                                  void* stream);
+
+/* Dense SVD of a small m x nc FP64 matrix on the device (one thread block, one-sided
+ * Jacobi): A = U diag(S) V^T, S descending, m >= nc, m <= 128, nc <= 64.  Host pointers
+ * (synchronous): A (m x nc), U (m x nc), S (nc), V (nc x nc), column-major.  sweeps
+ * receives the Jacobi sweeps used (may be NULL). */
+kpsb_status kpsb_small_svd(int m, int nc, const double* A, double* U, double* S, double* V,
+                           int* sweeps);
+
+/* Thread-local message for the last error of this thread ("" if none). */
+const char* kpsb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KPSB_H */

@@ -1,0 +1,105 @@
+// Shared helpers of the kpsb CUDA library (sm_103a): status/error plumbing, launch
+// checks, deterministic grid reductions, warp/block sums.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/kpsb.h"
+
+namespace kpsb {
+
+// Thread-local last-error message (kpsb_last_error).
+void set_error(const char* fmt, ...);
+void clear_error();
+
+struct Status {
+  kpsb_status code;
+};
+
+#define KPSB_TRY_CUDA(expr)                                                            \
+  do {                                                                                 \
+    cudaError_t _e = (expr);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      ::kpsb::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(_e)); \
+      return KPSB_ECUDA;                                                               \
+    }                                                                                  \
+  } while (0)
+
+#define KPSB_TRY(expr)                     \
+  do {                                     \
+    kpsb_status _s = (expr);               \
+    if (_s != KPSB_OK) return _s;          \
+  } while (0)
+
+#define KPSB_CHECK_LAUNCH() KPSB_TRY_CUDA(cudaGetLastError())
+
+#define KPSB_REQUIRE(cond, ...)            \
+  do {                                     \
+    if (!(cond)) {                         \
+      ::kpsb::set_error(__VA_ARGS__);      \
+      return KPSB_EINVAL;                  \
+    }                                      \
+  } while (0)
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// --------------------------------------------------------------------------------------
+// Device helpers
+// --------------------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (fixed order, deterministic).  All threads receive the result.
+// `sh` must hold >= 32 elements.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T r = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+  if (wid == 0) r = warp_sum(r);
+  if (threadIdx.x == 0) sh[0] = r;
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// "Last block" protocol of a deterministic grid reduction: every block writes its
+// partial results, then calls this; exactly one block (the last to arrive) gets true and
+// may read all partials (with __ldcg) in a fixed order.  The counter is reset by the
+// last block so the next launch starts from zero.
+__device__ __forceinline__ bool last_block_arrive(unsigned int* counter, unsigned int nblocks) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == nblocks - 1);
+    if (s_last) *counter = 0u;  // no other block touches it again in this launch
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+__device__ __forceinline__ int ext_index(int q, int n, int bc) {
+  // Boundary extension: zero -> -1 for out-of-range; reflexive half-sample mirror.
+  if (q >= 0 && q < n) return q;
+  if (bc == KPSB_BC_ZERO) return -1;
+  return q < 0 ? -1 - q : 2 * n - 1 - q;
+}
+
+}  // namespace kpsb

@@ -1,0 +1,668 @@
+// kp_build: TSVD of R(A) by EGKB (Alg. 1) or RSVD (Alg. 2) in FP32 on the device,
+// FP64 bidiagonal / Gram SVDs on the device, then Terms(A_k) (Theorem 2.1, Sec. 4.1.3).
+#include <math.h>
+#include <stddef.h>
+#include <string.h>
+
+#include <string>
+#include <thread>
+
+#include "kpsb_internal.cuh"
+
+namespace kpsb {
+
+static constexpr int KP_MAX = 64;   // largest enlarged size k_p
+static constexpr int K_CAP = 30;    // automatic rank cap
+static constexpr int NGATE = 2 * (KP_MAX + 4);
+
+// Device-side scalar state of the GKB recurrence.
+struct EgkbState {
+  double alpha[KP_MAX + 4];  // alpha_j, j >= 1
+  double t[KP_MAX + 4];      // t_j, j >= 1
+  double zeta[KP_MAX + 4];
+  double nu[KP_MAX + 4];
+  double norm;     // last computed norm (t_j or alpha_j before acceptance)
+  double coef_s;   // -alpha_{j-1}: coefficient of s_{j-1} in s_j
+  double coef_q;   // -t_j: coefficient of q_{j-1} in q_j
+  double bnorm;    // running lower bound of ||R(A)||
+  int nq, ns;      // accepted q / s columns
+  int k_sel, kp_target;
+  int finished;    // 0 running, 1 complete, 2 breakdown in t, 3 breakdown in alpha
+  int gate[NGATE]; // gate[ph] != 0: kernels of phase ph skip (ph = 2j: s-phase, 2j+1: q)
+};
+
+// Device address of a field of the device-resident state (no host dereference).
+#define ST_FIELD(st, f) ((decltype(&((EgkbState*)0)->f))((char*)(st) + offsetof(EgkbState, f)))
+
+struct EgkbParams {
+  int k_fixed;      // > 0: fixed rank
+  int k_cap;
+  int p;
+  int k_min;
+  double tau;       // relative tolerance (auto mode)
+  double bd_tol;    // breakdown tolerance relative to bnorm
+};
+
+// Decide after t_j (s-phase of step j).  j = 1 is the start vector.
+__global__ void egkb_after_t(EgkbState* st, EgkbParams P, int j) {
+  if (st->gate[2 * j]) return;
+  double tj = st->norm;
+  int stop = 0;
+  if (j == 1) {
+    st->t[1] = tj;
+    st->ns = 1;
+    if (!(tj > 0.0)) { st->finished = 2; st->norm = 0.0; stop = 1; }
+  } else {
+    st->bnorm = fmax(st->bnorm, tj);
+    if (!(tj > P.bd_tol * st->bnorm)) {  // invariant subspace: s_j = 0, C's last row 0
+      st->t[j] = 0.0;
+      st->norm = 0.0;
+      st->ns = j;
+      st->finished = 2;
+      stop = 1;
+    } else {
+      st->t[j] = tj;
+      st->ns = j;
+      if (st->kp_target > 0 && st->nq >= st->kp_target) { st->finished = 1; stop = 1; }
+    }
+  }
+  st->coef_q = -st->t[j];
+  if (stop)
+    for (int ph = 2 * j + 1; ph < NGATE; ++ph) st->gate[ph] = 1;
+}
+
+// Decide after alpha_j (q-phase of step j): nu rule of Sec. 2.2 (eq. (2.6)).
+__global__ void egkb_after_alpha(EgkbState* st, EgkbParams P, int j) {
+  if (st->gate[2 * j + 1]) return;
+  double aj = st->norm;
+  st->bnorm = fmax(st->bnorm, aj);
+  if (!(aj > P.bd_tol * st->bnorm) || (j == 1 && !(aj > 0.0))) {
+    st->finished = 3;  // q_j is not accepted
+    for (int ph = 2 * j + 2; ph < NGATE; ++ph) st->gate[ph] = 1;
+    return;
+  }
+  st->alpha[j] = aj;
+  st->nq = j;
+  st->coef_s = -aj;
+  if (j >= 2) {
+    st->zeta[j] = aj * st->t[j];
+    if (j >= 3) st->nu[j] = sqrt(st->zeta[j] * st->zeta[j - 1]);
+  }
+  if (P.k_fixed <= 0 && st->k_sel < 0 && j >= 4) {
+    int i = j - 1;
+    int kmin = P.k_min > 3 ? P.k_min : 3;
+    if (i >= kmin && (st->nu[j] > st->nu[i] || st->nu[i] < P.tau * st->nu[3]))
+      st->k_sel = i;
+    else if (i >= P.k_cap)
+      st->k_sel = P.k_cap;
+    if (st->k_sel >= 0) {
+      int kp = st->k_sel + P.p;
+      st->kp_target = kp > st->nq ? kp : st->nq;
+    }
+  }
+}
+
+__global__ void egkb_init_state(EgkbState* st, EgkbParams P) {
+  memset(st, 0, sizeof(EgkbState));
+  st->k_sel = P.k_fixed > 0 ? P.k_fixed : -1;
+  st->kp_target = P.k_fixed > 0 ? P.k_fixed + P.p : -1;
+}
+
+// Sign convention: the entry of largest magnitude of each Ay_i is positive (ties: first).
+__global__ void sign_fix_kernel(float* Ax, float* Ay, long long N) {
+  __shared__ float bv[256];
+  __shared__ long long bi[256];
+  float* ay = Ay + (size_t)blockIdx.x * N;
+  float* ax = Ax + (size_t)blockIdx.x * N;
+  float best = -1.f;
+  long long bidx = 0;
+  for (long long e = threadIdx.x; e < N; e += blockDim.x) {
+    float a = fabsf(ay[e]);
+    if (a > best) { best = a; bidx = e; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      float v2 = bv[threadIdx.x + o];
+      long long i2 = bi[threadIdx.x + o];
+      if (v2 > bv[threadIdx.x] || (v2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+        bv[threadIdx.x] = v2;
+        bi[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  const bool flip = ay[bi[0]] < 0.f;
+  __syncthreads();
+  if (!flip) return;
+  for (long long e = threadIdx.x; e < N; e += blockDim.x) {
+    ay[e] = -ay[e];
+    ax[e] = -ax[e];
+  }
+}
+
+// SVQB preparation: d_i = G_ii, Gs = D^{-1/2} G D^{-1/2} (zero rows where d_i = 0).
+__global__ void svqb_scale_kernel(const double* G, int m, double* Gs, double* d) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    int i = e % m, j = e / m;
+    double di = G[i + i * m], dj = G[j + j * m];
+    Gs[e] = (di > 0.0 && dj > 0.0) ? G[e] / sqrt(di * dj) : 0.0;
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = G[i + i * m];
+}
+
+// T = D^{-1/2} W Lambda^{-1/2}, dropping eigenvalues below tol * lambda_max (null
+// directions of Y, i.e. the part of the space beyond the rank of R(A)).
+__global__ void svqb_transform_kernel(const double* W, const double* lam, const double* d, int m,
+                                      double tol, double* T) {
+  double lmax = lam[0];
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    int i = e % m, j = e / m;
+    double l = lam[j];
+    double v = 0.0;
+    if (l > tol * lmax && d[i] > 0.0) v = W[e] / sqrt(d[i]) / sqrt(l);
+    T[e] = v;
+  }
+}
+
+// RSVD final step: sigma_j = sqrt(lambda_j) of H H^T, T2 = U Sigma^{-1} (for V = H^T T2).
+__global__ void rsvd_sigma_kernel(const double* lam, const double* U, int m, int k, double tol,
+                                  double* sigma, double* T2) {
+  double lmax = lam[0];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) sigma[j] = lam[j] > 0.0 ? sqrt(lam[j]) : 0.0;
+  for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
+    int j = e / m;
+    double l = lam[j];
+    T2[e] = (l > tol * lmax) ? U[e] / sqrt(l) : 0.0;
+  }
+}
+
+// ---- workspace ---------------------------------------------------------------------------------
+struct BuildWork {
+  char* base = nullptr;
+  float* psf = nullptr;
+  float* S = nullptr;   // N x (KP + 1)
+  float* Q = nullptr;   // N x KP
+  float* T = nullptr;   // N x KP (RSVD temp)
+  double* h = nullptr;  // 128
+  double* small = nullptr;  // small matrices: C, U, S, V, G, ...
+  EgkbState* st = nullptr;
+  RAScratch ra;
+  RedScratch red;
+};
+
+static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+
+static kpsb_status work_alloc(BuildWork& w, int n, int s0, int s1, int kpmax, int nb_ra,
+                              cudaStream_t st) {
+  const size_t N = (size_t)n * n;
+  const int smax = std::max(s0, s1);
+  size_t off_psf = 0;
+  size_t off_S = off_psf + a256(sizeof(float) * s0 * s1);
+  size_t off_Q = off_S + a256(sizeof(float) * N * (kpmax + 1));
+  size_t off_T = off_Q + a256(sizeof(float) * N * (kpmax + 1));
+  size_t off_h = off_T + a256(sizeof(float) * N * (kpmax + 1));
+  size_t off_small = off_h + a256(sizeof(double) * 256);
+  size_t small_sz = a256(sizeof(double) * 12 * 130 * 66);
+  size_t off_st = off_small + small_sz;
+  size_t off_ra = off_st + a256(sizeof(EgkbState));
+  size_t ra_bytes = ra_scratch_bytes(n, nb_ra, smax);
+  size_t off_red = off_ra + a256(ra_bytes);
+  size_t red_bytes = a256(sizeof(double) * RED_MAX_BLOCKS * 64 * 64) + 256;
+  size_t total = off_red + red_bytes;
+  KPSB_TRY_CUDA(cudaMallocAsync((void**)&w.base, total, st));
+  w.psf = (float*)(w.base + off_psf);
+  w.S = (float*)(w.base + off_S);
+  w.Q = (float*)(w.base + off_Q);
+  w.T = (float*)(w.base + off_T);
+  w.h = (double*)(w.base + off_h);
+  w.small = (double*)(w.base + off_small);
+  w.st = (EgkbState*)(w.base + off_st);
+  w.ra = ra_scratch_carve(w.base + off_ra, n, nb_ra, smax);
+  w.red.counter = (unsigned int*)(w.base + off_red);
+  w.red.part = (double*)(w.base + off_red + 256);
+  // counters must start at zero
+  KPSB_TRY_CUDA(cudaMemsetAsync(w.ra.counters, 0, sizeof(unsigned int) * nb_ra, st));
+  KPSB_TRY_CUDA(cudaMemsetAsync(w.red.counter, 0, sizeof(unsigned int), st));
+  return KPSB_OK;
+}
+
+struct HostPsf {
+  std::vector<float> f;
+};
+
+// CGS2: two passes of v -= B (B^T v) against m columns; the second pass also gives ||v||.
+static kpsb_status cgs2(const float* B, int ldb, int m, float* v, long long N, double* h,
+                        double* norm_out, const RedScratch& red, const int* gate, cudaStream_t st) {
+  if (m > 0) {
+    KPSB_TRY(la_dot_block(B, ldb, m, v, N, h, red, gate, st));
+    KPSB_TRY(la_update(B, ldb, m, h, v, N, nullptr, red, gate, st));
+    KPSB_TRY(la_dot_block(B, ldb, m, v, N, h, red, gate, st));
+    KPSB_TRY(la_update(B, ldb, m, h, v, N, norm_out, red, gate, st));
+  } else {
+    KPSB_TRY(la_norm(v, N, norm_out, red, gate, st));
+  }
+  return KPSB_OK;
+}
+
+// ---- EGKB ------------------------------------------------------------------------------------
+// Steps (Alg. 1): t_1 = ||y||, s_1 = y/t_1; q_1 = R^T s_1 / alpha_1; for j >= 2:
+//   s_j = R q_{j-1} - alpha_{j-1} s_{j-1} [reorthogonalised against s_1..s_{j-1}], t_j,
+//   q_j = R^T s_j - t_j q_{j-1}, reorthogonalised against q_1..q_{j-1}, alpha_j, nu_j.
+// Reorthogonalisation is classical Gram-Schmidt applied twice (CGS2), the blocked form
+// of the modified Gram-Schmidt of the paper (same projection, at least as orthogonal).
+static kpsb_status egkb_run(BuildWork& w, int n, int s0, int s1, int bc, const EgkbParams& P,
+                            int full_reorth, int kpmax, const float* start_host,
+                            unsigned long long seed, cudaStream_t st, int* nq_out, int* ns_out,
+                            int* ksel_out, std::vector<double>& alpha, std::vector<double>& tvec) {
+  const long long N = (long long)n * n;
+  egkb_init_state<<<1, 1, 0, st>>>(w.st, P);
+  KPSB_CHECK_LAUNCH();
+  // s_1 = y / ||y||
+  if (start_host) {
+    KPSB_TRY_CUDA(cudaMemcpyAsync(w.S, start_host, sizeof(float) * N, cudaMemcpyHostToDevice, st));
+  } else {
+    KPSB_TRY(la_randn(w.S, N, seed, st));
+  }
+  int* gate = (int*)((char*)w.st + offsetof(EgkbState, gate));
+  double* d_norm = ST_FIELD(w.st, norm);
+  double* d_coef_s = ST_FIELD(w.st, coef_s);
+  double* d_coef_q = ST_FIELD(w.st, coef_q);
+  int* d_finished = ST_FIELD(w.st, finished);
+  KPSB_TRY(la_norm(w.S, N, d_norm, w.red, gate + 2, st));
+  egkb_after_t<<<1, 1, 0, st>>>(w.st, P, 1);
+  KPSB_CHECK_LAUNCH();
+  KPSB_TRY(la_scale_inv(w.S, N, d_norm, gate + 2, st));
+  // q_1 = R^T s_1 / alpha_1
+  KPSB_TRY(ra_apply(w.psf, s0, s1, n, bc, w.S, (int)N, 1, w.Q, (int)N, 1, nullptr, 0, nullptr, 0.f,
+                    gate + 3, w.ra, st));
+  KPSB_TRY(la_norm(w.Q, N, d_norm, w.red, gate + 3, st));
+  egkb_after_alpha<<<1, 1, 0, st>>>(w.st, P, 1);
+  KPSB_CHECK_LAUNCH();
+  KPSB_TRY(la_scale_inv(w.Q, N, d_norm, gate + 3, st));
+
+  int* h_fin = nullptr;
+  KPSB_TRY_CUDA(cudaMallocHost((void**)&h_fin, sizeof(int)));
+  *h_fin = 0;
+  kpsb_status status = KPSB_OK;
+  for (int j = 2; j <= kpmax + 1 && status == KPSB_OK; ++j) {
+    float* sj = w.S + (size_t)(j - 1) * N;
+    float* sjm1 = w.S + (size_t)(j - 2) * N;
+    float* qjm1 = w.Q + (size_t)(j - 2) * N;
+    float* qj = w.Q + (size_t)(j - 1) * N;
+    const int* gs = gate + 2 * j;
+    const int* gq = gate + 2 * j + 1;
+    // s-phase
+    status = ra_apply(w.psf, s0, s1, n, bc, qjm1, (int)N, 1, sj, (int)N, 0, sjm1, (int)N,
+                      d_coef_s, 0.f, gs, w.ra, st);
+    if (status) break;
+    status = cgs2(w.S, (int)N, full_reorth ? j - 1 : 0, sj, N, w.h, d_norm, w.red, gs, st);
+    if (status) break;
+    egkb_after_t<<<1, 1, 0, st>>>(w.st, P, j);
+    KPSB_CHECK_LAUNCH();
+    status = la_scale_inv(sj, N, d_norm, gs, st);
+    if (status) break;
+    if (j == kpmax + 1) break;  // only s_{kp+1} is needed from the last step
+    // q-phase
+    status = ra_apply(w.psf, s0, s1, n, bc, sj, (int)N, 1, qj, (int)N, 1, qjm1, (int)N,
+                      d_coef_q, 0.f, gq, w.ra, st);
+    if (status) break;
+    status = cgs2(w.Q, (int)N, j - 1, qj, N, w.h, d_norm, w.red, gq, st);
+    if (status) break;
+    egkb_after_alpha<<<1, 1, 0, st>>>(w.st, P, j);
+    KPSB_CHECK_LAUNCH();
+    status = la_scale_inv(qj, N, d_norm, gq, st);
+    if (status) break;
+    if (j % 4 == 0) {  // leave the loop early once the recurrence has finished
+      cudaError_t e = cudaMemcpyAsync(h_fin, d_finished, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        set_error("egkb: %s", cudaGetErrorString(e));
+        status = KPSB_ECUDA;
+        break;
+      }
+      if (*h_fin) break;
+    }
+  }
+  cudaFreeHost(h_fin);
+  if (status) return status;
+  EgkbState hs;
+  KPSB_TRY_CUDA(cudaMemcpyAsync(&hs, w.st, sizeof(EgkbState), cudaMemcpyDeviceToHost, st));
+  KPSB_TRY_CUDA(cudaStreamSynchronize(st));
+  *nq_out = hs.nq;
+  *ns_out = hs.ns;
+  *ksel_out = hs.k_sel;
+  alpha.assign(hs.alpha, hs.alpha + KP_MAX + 2);
+  tvec.assign(hs.t, hs.t + KP_MAX + 2);
+  return KPSB_OK;
+}
+
+static kpsb_status handle_alloc(kpsb_kp** out, int n, int k, int kpsize) {
+  kpsb_kp* h = new (std::nothrow) kpsb_kp();
+  if (!h) {
+    set_error("out of host memory");
+    return KPSB_ENOMEM;
+  }
+  h->n = n;
+  h->k = k;
+  h->kp = kpsize;
+  cudaGetDevice(&h->device);
+  size_t N = (size_t)n * n;
+  cudaError_t e = cudaMalloc((void**)&h->Ax, sizeof(float) * N * k * 2 + sizeof(double) * k + 256);
+  if (e != cudaSuccess) {
+    delete h;
+    set_error("handle allocation (%zu bytes): %s", sizeof(float) * N * k * 2, cudaGetErrorString(e));
+    return KPSB_ENOMEM;
+  }
+  h->Ay = h->Ax + N * k;
+  h->sigma_d = (double*)(((uintptr_t)(h->Ay + N * k) + 255) & ~(uintptr_t)255);
+  *out = h;
+  return KPSB_OK;
+}
+
+static kpsb_status build_egkb(const float* psf_host, int s0, int s1, int n, int bc, int k,
+                              double tau, const kpsb_build_opts& o, cudaStream_t st, kpsb_kp** out) {
+  EgkbParams P;
+  P.k_fixed = tau > 0.0 ? 0 : k;
+  P.k_cap = tau > 0.0 ? std::min(k, K_CAP) : k;
+  P.p = o.p;
+  P.k_min = o.k_min;
+  P.tau = tau;
+  P.bd_tol = 30.0 * 1.1920928955078125e-07;
+  const int kpmax = P.k_cap + P.p;
+  KPSB_REQUIRE(kpmax <= KP_MAX, "k + p = %d exceeds %d", kpmax, KP_MAX);
+  const long long N = (long long)n * n;
+  BuildWork w;
+  KPSB_TRY(work_alloc(w, n, s0, s1, kpmax, 1, st));
+  kpsb_status s = KPSB_OK;
+  do {
+    cudaError_t e = cudaMemcpyAsync(w.psf, psf_host, sizeof(float) * s0 * s1, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { set_error("psf upload: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+    int nq = 0, ns = 0, ksel = 0;
+    std::vector<double> alpha, tv;
+    s = egkb_run(w, n, s0, s1, bc, P, !o.one_sided, kpmax, o.start_host, o.seed, st, &nq, &ns,
+                 &ksel, alpha, tv);
+    if (s) break;
+    if (nq < 1) {
+      set_error("EGKB: R(A) applied to the start vector vanishes");
+      s = KPSB_EBREAKDOWN;
+      break;
+    }
+    int kk = ksel > 0 ? std::min(ksel, nq) : std::min(P.k_cap, nq);
+    // C ((nq+1) x nq lower bidiagonal) -> device, FP64 SVD (Alg. 1 step 15)
+    const int m = nq + 1, nc = nq;
+    std::vector<double> C((size_t)m * nc, 0.0);
+    for (int i = 0; i < nc; ++i) {
+      C[i + (size_t)i * m] = alpha[i + 1];
+      C[i + 1 + (size_t)i * m] = tv[i + 2];
+    }
+    double* dC = w.small;
+    double* dU = dC + 130 * 66;
+    double* dSg = dU + 130 * 66;
+    double* dV = dSg + 130;
+    e = cudaMemcpyAsync(dC, C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { set_error("C upload: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+    s = la_small_svd(dC, m, m, nc, dU, dSg, dV, nullptr, st);
+    if (s) break;
+    kpsb_kp* h = nullptr;
+    s = handle_alloc(&h, n, kk, nq);
+    if (s) break;
+    // Ritz vectors (steps 16-17): U = S_{nq+1} Uc[:, :k], V = Q_nq Vc[:, :k]
+    s = la_matmul_small(w.S, (int)N, N, m, dU, m, kk, h->Ax, (int)N, st);
+    if (!s) s = la_matmul_small(w.Q, (int)N, N, nc, dV, nc, kk, h->Ay, (int)N, st);
+    if (!s) {
+      sign_fix_kernel<<<kk, 256, 0, st>>>(h->Ax, h->Ay, N);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->sigma_d, dSg, sizeof(double) * kk, cudaMemcpyDeviceToDevice, st);
+      h->sigma.resize(kk);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->sigma.data(), dSg, sizeof(double) * kk, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) { set_error("EGKB terms: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; }
+    }
+    if (s) {
+      kp_free(h);
+      break;
+    }
+    *out = h;
+  } while (0);
+  cudaFreeAsync(w.base, st);
+  return s;
+}
+
+// Orthonormalise the m columns of Y (N x m) in place by SVQB twice (Gram matrix, its
+// eigen-decomposition, Y <- Y D^{-1/2} W Lambda^{-1/2}); null directions become zero.
+static kpsb_status svqb2(BuildWork& w, float* Y, long long N, int m, cudaStream_t st) {
+  double* G = w.small;
+  double* Gs = G + 64 * 64;
+  double* d = Gs + 64 * 64;
+  double* U = d + 64;
+  double* lam = U + 64 * 64;
+  double* W = lam + 64;
+  double* T = W + 64 * 64;
+  for (int pass = 0; pass < 2; ++pass) {
+    KPSB_TRY(la_gram(Y, (int)N, N, m, G, w.red, st));
+    svqb_scale_kernel<<<1, 256, 0, st>>>(G, m, Gs, d);
+    KPSB_CHECK_LAUNCH();
+    KPSB_TRY(la_small_svd(Gs, m, m, m, U, lam, W, nullptr, st));
+    svqb_transform_kernel<<<1, 256, 0, st>>>(W, lam, d, m, 1e-12, T);
+    KPSB_CHECK_LAUNCH();
+    KPSB_TRY(la_matmul_small(Y, (int)N, N, m, T, m, m, w.T, (int)N, st));
+    KPSB_TRY_CUDA(cudaMemcpyAsync(Y, w.T, sizeof(float) * N * m, cudaMemcpyDeviceToDevice, st));
+  }
+  return KPSB_OK;
+}
+
+// ---- RSVD --------------------------------------------------------------------------------------
+// Alg. 2 with q power iterations: Y = R F, orthonormalised after every apply of R or R^T
+// (step 2-3), H^T = R^T Q (step 4), SVD of H through the eigen-decomposition of H H^T
+// (k_p x k_p, FP64; step 5), U = Q U_H (step 6), V = H^T U_H Sigma^{-1}, truncation (step 7).
+static kpsb_status build_rsvd(const float* psf_host, int s0, int s1, int n, int bc, int k,
+                              const kpsb_build_opts& o, cudaStream_t st, kpsb_kp** out) {
+  const int kp = k + o.p;
+  KPSB_REQUIRE(kp <= KP_MAX, "k + p = %d exceeds %d", kp, KP_MAX);
+  const long long N = (long long)n * n;
+  BuildWork w;
+  KPSB_TRY(work_alloc(w, n, s0, s1, kp, kp, st));
+  kpsb_status s = KPSB_OK;
+  do {
+    cudaError_t e = cudaMemcpyAsync(w.psf, psf_host, sizeof(float) * s0 * s1, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { set_error("psf upload: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+    float* F = w.S;  // N x kp
+    if (o.start_host) {
+      e = cudaMemcpyAsync(F, o.start_host, sizeof(float) * N * kp, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) { set_error("F upload: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+    } else {
+      s = la_randn(F, N * kp, o.seed, st);
+      if (s) break;
+    }
+    float* Y = w.Q;
+    s = ra_apply(w.psf, s0, s1, n, bc, F, (int)N, kp, Y, (int)N, 0, nullptr, 0, nullptr, 0.f,
+                 nullptr, w.ra, st);
+    if (!s) s = svqb2(w, Y, N, kp, st);
+    for (int it = 0; it < o.power_iters && !s; ++it) {
+      s = ra_apply(w.psf, s0, s1, n, bc, Y, (int)N, kp, F, (int)N, 1, nullptr, 0, nullptr, 0.f,
+                   nullptr, w.ra, st);
+      if (!s) s = svqb2(w, F, N, kp, st);
+      if (!s) s = ra_apply(w.psf, s0, s1, n, bc, F, (int)N, kp, Y, (int)N, 0, nullptr, 0, nullptr,
+                           0.f, nullptr, w.ra, st);
+      if (!s) s = svqb2(w, Y, N, kp, st);
+    }
+    if (s) break;
+    // H^T = R^T Q  (N x kp) into F
+    float* Ht = F;
+    s = ra_apply(w.psf, s0, s1, n, bc, Y, (int)N, kp, Ht, (int)N, 1, nullptr, 0, nullptr, 0.f,
+                 nullptr, w.ra, st);
+    if (s) break;
+    double* G = w.small;
+    double* U = G + 64 * 64;
+    double* lam = U + 64 * 64;
+    double* W = lam + 64;
+    double* sig = W + 64 * 64;
+    double* T2 = sig + 64;
+    s = la_gram(Ht, (int)N, N, kp, G, w.red, st);
+    if (!s) s = la_small_svd(G, kp, kp, kp, U, lam, W, nullptr, st);
+    if (s) break;
+    rsvd_sigma_kernel<<<1, 256, 0, st>>>(lam, W, kp, k, 1e-12, sig, T2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error("rsvd: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+    // effective k: drop directions with zero singular value (rank of R(A) < k)
+    std::vector<double> hsig(k);
+    e = cudaMemcpyAsync(hsig.data(), sig, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { set_error("rsvd: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+    int kk = 0;
+    while (kk < k && hsig[kk] > 1e-6 * hsig[0]) ++kk;
+    if (kk == 0) {
+      set_error("RSVD: R(A) applied to the test matrix vanishes");
+      s = KPSB_EBREAKDOWN;
+      break;
+    }
+    kpsb_kp* h = nullptr;
+    s = handle_alloc(&h, n, kk, kp);
+    if (s) break;
+    s = la_matmul_small(Y, (int)N, N, kp, W, kp, kk, h->Ax, (int)N, st);  // U = Q U_H
+    if (!s) s = la_matmul_small(Ht, (int)N, N, kp, T2, kp, kk, h->Ay, (int)N, st);
+    if (!s) {
+      sign_fix_kernel<<<kk, 256, 0, st>>>(h->Ax, h->Ay, N);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->sigma_d, sig, sizeof(double) * kk, cudaMemcpyDeviceToDevice, st);
+      h->sigma.assign(hsig.begin(), hsig.begin() + kk);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) { set_error("RSVD terms: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; }
+    }
+    if (s) {
+      kp_free(h);
+      break;
+    }
+    *out = h;
+  } while (0);
+  cudaFreeAsync(w.base, st);
+  return s;
+}
+
+}  // namespace kpsb
+
+using namespace kpsb;
+
+// ---- C ABI ----------------------------------------------------------------------------------------
+extern "C" kpsb_status kp_build(const double* psf, int s0, int s1, int n, int bc, double rank_or_tol,
+                                int method, const kpsb_build_opts* opts, kpsb_kp_t* out) {
+  clear_error();
+  KPSB_REQUIRE(psf && out, "null pointer");
+  *out = nullptr;
+  KPSB_TRY(ra_check(s0, s1, n, bc));
+  KPSB_REQUIRE(method == KPSB_EGKB || method == KPSB_RSVD, "unknown method %d", method);
+  KPSB_REQUIRE(rank_or_tol > 0.0 && isfinite(rank_or_tol), "rank_or_tol must be > 0");
+  kpsb_build_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  double tau = 0.0;
+  int k;
+  if (rank_or_tol >= 1.0) {
+    k = (int)rank_or_tol;
+  } else {
+    KPSB_REQUIRE(method == KPSB_EGKB, "automatic rank needs EGKB (RSVD takes a fixed k)");
+    tau = rank_or_tol;
+    k = K_CAP;
+  }
+  KPSB_REQUIRE(k >= 1 && k <= KP_MAX, "rank %d outside [1, %d]", k, KP_MAX);
+  if (o.p <= 0) o.p = std::max(2, (k + 3) / 4);
+  if (o.power_iters <= 0) o.power_iters = 1;
+  if (o.k_min <= 0) o.k_min = 3;
+  KPSB_REQUIRE(std::min(k, K_CAP) + o.p <= KP_MAX || tau == 0.0, "k_cap + p exceeds %d", KP_MAX);
+  std::vector<float> pf((size_t)s0 * s1);
+  for (size_t i = 0; i < pf.size(); ++i) pf[i] = (float)psf[i];
+  cudaStream_t st = (cudaStream_t)o.stream;
+  if (method == KPSB_EGKB) return build_egkb(pf.data(), s0, s1, n, bc, k, tau, o, st, out);
+  return build_rsvd(pf.data(), s0, s1, n, bc, k, o, st, out);
+}
+
+extern "C" kpsb_status kp_info(kpsb_kp_t kp, int* n, int* k, int* kp_size, double* sigma) {
+  clear_error();
+  KPSB_REQUIRE(kp, "null handle");
+  if (n) *n = kp->n;
+  if (k) *k = kp->k;
+  if (kp_size) *kp_size = kp->kp;
+  if (sigma) memcpy(sigma, kp->sigma.data(), sizeof(double) * kp->k);
+  return KPSB_OK;
+}
+
+extern "C" kpsb_status kp_get_factors(kpsb_kp_t kp, float* Ax, float* Ay, double* sigma) {
+  clear_error();
+  KPSB_REQUIRE(kp, "null handle");
+  size_t bytes = sizeof(float) * (size_t)kp->n * kp->n * kp->k;
+  if (Ax) KPSB_TRY_CUDA(cudaMemcpy(Ax, kp->Ax, bytes, cudaMemcpyDeviceToHost));
+  if (Ay) KPSB_TRY_CUDA(cudaMemcpy(Ay, kp->Ay, bytes, cudaMemcpyDeviceToHost));
+  if (sigma) memcpy(sigma, kp->sigma.data(), sizeof(double) * kp->k);
+  return KPSB_OK;
+}
+
+extern "C" kpsb_status kp_from_factors(int n, int k, const float* Ax, const float* Ay,
+                                       const double* sigma, kpsb_kp_t* out) {
+  clear_error();
+  KPSB_REQUIRE(Ax && Ay && sigma && out, "null pointer");
+  KPSB_REQUIRE(n >= 2 && k >= 1 && k <= KP_MAX, "bad sizes n=%d k=%d", n, k);
+  kpsb_kp* h = nullptr;
+  KPSB_TRY(handle_alloc(&h, n, k, k));
+  size_t bytes = sizeof(float) * (size_t)n * n * k;
+  cudaError_t e = cudaMemcpy(h->Ax, Ax, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->Ay, Ay, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->sigma_d, sigma, sizeof(double) * k, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    kp_free(h);
+    set_error("kp_from_factors: %s", cudaGetErrorString(e));
+    return KPSB_ECUDA;
+  }
+  h->sigma.assign(sigma, sigma + k);
+  *out = h;
+  return KPSB_OK;
+}
+
+extern "C" void kp_free(kpsb_kp_t kp) {
+  if (!kp) return;
+  if (kp->tc) tc_free(kp->tc);
+  if (kp->Ax) cudaFree(kp->Ax);
+  delete kp;
+}
+
+extern "C" kpsb_status kp_build_batched(int count, const kpsb_problem* probs, kpsb_kp_t* outs) {
+  clear_error();
+  KPSB_REQUIRE(count >= 0 && (count == 0 || (probs && outs)), "bad batch");
+  if (count == 0) return KPSB_OK;
+  int dev = 0;
+  KPSB_TRY_CUDA(cudaGetDevice(&dev));
+  // Problems are independent: up to 8 host threads, each with its own stream, so the
+  // builds (and their few host synchronisations) overlap on the device.
+  const int NT = std::min(count, 8);
+  std::vector<kpsb_status> st(count, KPSB_OK);
+  std::vector<std::string> msg(count);
+  auto worker = [&](int t) {
+    cudaSetDevice(dev);
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      for (int i = t; i < count; i += NT) { st[i] = KPSB_ECUDA; msg[i] = "stream creation failed"; }
+      return;
+    }
+    for (int i = t; i < count; i += NT) {
+      kpsb_build_opts o = probs[i].opts;
+      o.stream = s;
+      outs[i] = nullptr;
+      st[i] = kp_build(probs[i].psf, probs[i].s0, probs[i].s1, probs[i].n, probs[i].bc,
+                       probs[i].rank_or_tol, probs[i].method, &o, &outs[i]);
+      if (st[i] != KPSB_OK) msg[i] = kpsb_last_error();
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < NT; ++t) th.emplace_back(worker, t);
+  for (auto& x : th) x.join();
+  for (int i = 0; i < count; ++i)
+    if (st[i] != KPSB_OK) {
+      set_error("problem %d: %s", i, msg[i].c_str());
+      return st[i];
+    }
+  return KPSB_OK;
+}

@@ -1,0 +1,104 @@
+// Internal declarations shared by the translation units of the kpsb library.
+#pragma once
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace kpsb {
+
+// ---- R(A) block apply (ra.cu) -----------------------------------------------------------
+struct RAScratch {
+  float* part;             // per-tile diagonal / anti-diagonal partial sums
+  float* w;                // mixed tap weights, nb x s_exp
+  unsigned int* counters;  // last-block counters, nb (must start at zero)
+};
+size_t ra_scratch_bytes(int n, int nb, int s_exp);
+RAScratch ra_scratch_carve(void* base, int n, int nb, int s_exp);
+kpsb_status ra_check(int s0, int s1, int n, int bc);
+// U = R(A) V (or R(A)^T V) [+ beta * prev], beta read from beta_dev when non-null.
+// skip (device int, may be null): when *skip != 0 the expand step writes nothing.
+kpsb_status ra_apply(const float* psf, int s0, int s1, int n, int bc, const float* V, int ldv,
+                     int nb, float* U, int ldu, int transpose, const float* prev, int ldp,
+                     const double* beta_dev, float beta_host, const int* skip,
+                     const RAScratch& scr, cudaStream_t st);
+
+// ---- dense helpers (la.cu) --------------------------------------------------------------
+// Scratch of a deterministic grid reduction (partials + counter).
+struct RedScratch {
+  double* part;           // >= RED_MAX_BLOCKS * width doubles
+  unsigned int* counter;  // 1 (starts at zero)
+};
+static constexpr int RED_MAX_BLOCKS = 304;
+
+// h[i] = sum_r S[r + i ldS] v[r], i < m  (FP64 result; m <= 128).
+kpsb_status la_dot_block(const float* S, int ldS, int m, const float* v, long long N,
+                         double* h, const RedScratch& red, const int* skip, cudaStream_t st);
+// v -= S h (m columns); when norm_out != null also writes ||v||_2 (after the update).
+kpsb_status la_update(const float* S, int ldS, int m, const double* h, float* v, long long N,
+                      double* norm_out, const RedScratch& red, const int* skip, cudaStream_t st);
+// ||v||_2 into norm_out (FP64).
+kpsb_status la_norm(const float* v, long long N, double* norm_out, const RedScratch& red,
+                    const int* skip, cudaStream_t st);
+// v *= 1 / *norm (norm device FP64; zero norm leaves v unchanged).
+kpsb_status la_scale_inv(float* v, long long N, const double* norm, const int* skip,
+                         cudaStream_t st);
+// G = Y^T Y (m x m FP64, column-major), Y N x m FP32 with leading dimension ldy; m <= 64.
+kpsb_status la_gram(const float* Y, int ldy, long long N, int m, double* G,
+                    const RedScratch& red, cudaStream_t st);
+// Out (N x kk, ldo) = Y (N x m, ldy) * T (m x kk FP64 column-major, ldt);  Out != Y.
+kpsb_status la_matmul_small(const float* Y, int ldy, long long N, int m, const double* T,
+                            int ldt, int kk, float* Out, int ldo, cudaStream_t st);
+// One-sided Jacobi SVD of an m x nc FP64 matrix in device memory (one thread block):
+// A = U diag(S) V^T, S descending.  m <= 128, nc <= 64, m >= nc.  sweeps may be null.
+kpsb_status la_small_svd(const double* A, int lda, int m, int nc, double* U, double* S,
+                         double* V, int* sweeps, cudaStream_t st);
+// Standard normal FP32 values from Philox4x32-10 (counter = element index, key = seed)
+// and the Box-Muller transform.
+kpsb_status la_randn(float* out, long long count, unsigned long long seed, cudaStream_t st);
+
+// ---- KP operator handle ---------------------------------------------------------------
+struct TCTables;  // tensor-core operand tables (kpgemm_tc.cu)
+
+}  // namespace kpsb
+
+struct kpsb_kp {
+  int n = 0, k = 0, kp = 0;
+  int device = 0;
+  float* Ax = nullptr;     // k x n x n, column-major, unit Frobenius norm
+  float* Ay = nullptr;     // k x n x n
+  double* sigma_d = nullptr;  // k
+  std::vector<double> sigma;  // host copy
+  kpsb::TCTables* tc = nullptr;  // lazily built GEMM operand tables
+  std::mutex mu;
+};
+
+namespace kpsb {
+
+// ---- KP apply (kpgemm.cu) ---------------------------------------------------------------
+// One problem of a batched KP apply.
+struct KPJob {
+  const float* Ax;
+  const float* Ay;
+  const double* sigma;
+  int n, k;
+  const double* X;     // input n x n FP64
+  double* Y;           // output n x n FP64
+  void* Z;             // intermediate: k x n x n (FP64 or FP32 by precision)
+  const int* active;   // skip when *active == 0 (may be null)
+};
+// Y = sum sigma_i Ay_i X Ax_i^T (transpose 0) / sum sigma_i Ay_i^T X Ax_i (transpose 1)
+// for every job (all with the same n).  jobs_d: device copy of the descriptors.
+kpsb_status kp_apply_batch(const KPJob* jobs_d, int njobs, int n, int kmax, int transpose,
+                           int prec, cudaStream_t st);
+size_t kp_z_bytes(int n, int k, int prec);
+
+// Tensor-core path (kpgemm_tc.cu).
+kpsb_status tc_apply_batch(kpsb_kp** kps, const KPJob* jobs_d, const KPJob* jobs_h, int njobs,
+                           int n, int kmax, int transpose, int prec, cudaStream_t st);
+bool tc_supported(int n, int prec);
+void tc_free(TCTables* t);
+
+}  // namespace kpsb

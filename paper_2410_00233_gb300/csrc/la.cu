@@ -1,0 +1,393 @@
+// Dense helpers of the TSVD phase: block dot products and updates of the (classical,
+// two-pass) Gram-Schmidt reorthogonalisation, norms, Gram matrices, skinny products,
+// the one-block FP64 Jacobi SVD and the Philox4x32-10 normal generator.
+#include <math.h>
+
+#include "kpsb_internal.cuh"
+
+namespace kpsb {
+
+static constexpr int LA_THREADS = 256;
+
+__device__ __forceinline__ bool gate_skip(const int* skip) { return skip && *skip; }
+
+static int red_blocks(long long N, int per_thread) {
+  long long b = (N + (long long)LA_THREADS * per_thread - 1) / ((long long)LA_THREADS * per_thread);
+  return (int)std::max(1LL, std::min<long long>(b, RED_MAX_BLOCKS));
+}
+
+// ---- h = S^T v --------------------------------------------------------------------------
+__global__ void __launch_bounds__(LA_THREADS) dot_block_kernel(
+    const float* __restrict__ S, int ldS, int m, const float* __restrict__ v, long long N,
+    double* __restrict__ part, unsigned int* __restrict__ counter, double* __restrict__ h,
+    const int* skip) {
+  if (gate_skip(skip)) return;
+  __shared__ double sh[32];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long r0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int c0 = 0; c0 < m; c0 += 8) {
+    float acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+    for (long long r = r0; r < N; r += stride) {
+      float x = v[r];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (c0 + u < m) acc[u] = fmaf(S[r + (size_t)(c0 + u) * ldS], x, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (c0 + u >= m) break;
+      double t = block_sum<double>((double)acc[u], sh);
+      if (threadIdx.x == 0) part[(size_t)blockIdx.x * m + c0 + u] = t;
+    }
+  }
+  if (!last_block_arrive(counter, gridDim.x)) return;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double t = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(part + (size_t)b * m + i);
+    h[i] = t;
+  }
+}
+
+kpsb_status la_dot_block(const float* S, int ldS, int m, const float* v, long long N, double* h,
+                         const RedScratch& red, const int* skip, cudaStream_t st) {
+  if (m <= 0) return KPSB_OK;
+  int nb = red_blocks(N, 4);
+  dot_block_kernel<<<nb, LA_THREADS, 0, st>>>(S, ldS, m, v, N, red.part, red.counter, h, skip);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+// ---- v -= S h, optional ||v|| -------------------------------------------------------------
+__global__ void __launch_bounds__(LA_THREADS) update_kernel(
+    const float* __restrict__ S, int ldS, int m, const double* __restrict__ h, float* __restrict__ v,
+    long long N, double* __restrict__ part, unsigned int* __restrict__ counter,
+    double* __restrict__ norm_out, const int* skip) {
+  if (gate_skip(skip)) return;
+  __shared__ float hs[128];
+  __shared__ double sh[32];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) hs[i] = (float)h[i];
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  float ss = 0.f;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += stride) {
+    float corr = 0.f;
+    for (int i = 0; i < m; ++i) corr = fmaf(S[r + (size_t)i * ldS], hs[i], corr);
+    float x = v[r] - corr;
+    v[r] = x;
+    ss = fmaf(x, x, ss);
+  }
+  if (!norm_out) return;
+  double t = block_sum<double>((double)ss, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (!last_block_arrive(counter, gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) a += __ldcg(part + b);
+    *norm_out = sqrt(a);
+  }
+}
+
+kpsb_status la_update(const float* S, int ldS, int m, const double* h, float* v, long long N,
+                      double* norm_out, const RedScratch& red, const int* skip, cudaStream_t st) {
+  int nb = red_blocks(N, 4);
+  update_kernel<<<nb, LA_THREADS, 0, st>>>(S, ldS, m, h, v, N, red.part, red.counter, norm_out,
+                                           skip);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+kpsb_status la_norm(const float* v, long long N, double* norm_out, const RedScratch& red,
+                    const int* skip, cudaStream_t st) {
+  return la_update(nullptr, 0, 0, nullptr, const_cast<float*>(v), N, norm_out, red, skip, st);
+}
+
+__global__ void scale_inv_kernel(float* __restrict__ v, long long N, const double* __restrict__ nrm,
+                                 const int* skip) {
+  if (gate_skip(skip)) return;
+  double d = *nrm;
+  float s = d > 0.0 ? (float)(1.0 / d) : 0.f;  // zero norm: the vector is cleared
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+       r += (long long)gridDim.x * blockDim.x)
+    v[r] *= s;
+}
+
+kpsb_status la_scale_inv(float* v, long long N, const double* norm, const int* skip,
+                         cudaStream_t st) {
+  int nb = (int)std::min<long long>((N + 1023) / 1024, 1216);
+  scale_inv_kernel<<<nb, LA_THREADS, 0, st>>>(v, N, norm, skip);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+// ---- G = Y^T Y (FP64) ----------------------------------------------------------------------
+__global__ void __launch_bounds__(LA_THREADS) gram_kernel(const float* __restrict__ Y, int ldy,
+                                                         long long N, int m,
+                                                         double* __restrict__ part,
+                                                         unsigned int* __restrict__ counter,
+                                                         double* __restrict__ G) {
+  __shared__ float ch[32][65];
+  const int npair = m * m;
+  double acc[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) acc[u] = 0.0;
+  for (long long rb = (long long)blockIdx.x * 32; rb < N; rb += (long long)gridDim.x * 32) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * m; e += blockDim.x) {
+      int rr = e % 32, c = e / 32;
+      long long r = rb + rr;
+      ch[rr][c] = r < N ? Y[r + (size_t)c * ldy] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      int p = threadIdx.x + u * LA_THREADS;
+      if (p < npair) {
+        int i = p % m, j = p / m;
+        double a = 0.0;
+        for (int rr = 0; rr < 32; ++rr) a = fma((double)ch[rr][i], (double)ch[rr][j], a);
+        acc[u] += a;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    int p = threadIdx.x + u * LA_THREADS;
+    if (p < npair) part[(size_t)blockIdx.x * npair + p] = acc[u];
+  }
+  if (!last_block_arrive(counter, gridDim.x)) return;
+  for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+    double a = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) a += __ldcg(part + (size_t)b * npair + p);
+    G[p] = a;  // column-major: p = i + j m
+  }
+}
+
+kpsb_status la_gram(const float* Y, int ldy, long long N, int m, double* G, const RedScratch& red,
+                    cudaStream_t st) {
+  KPSB_REQUIRE(m >= 1 && m <= 64, "gram width %d outside [1,64]", m);
+  int nb = (int)std::max(1LL, std::min<long long>((N + 31) / 32, 152));
+  gram_kernel<<<nb, LA_THREADS, 0, st>>>(Y, ldy, N, m, red.part, red.counter, G);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+// ---- Out = Y T --------------------------------------------------------------------------------
+__global__ void __launch_bounds__(LA_THREADS) matmul_small_kernel(
+    const float* __restrict__ Y, int ldy, long long N, int m, const double* __restrict__ T, int ldt,
+    int kk, float* __restrict__ Out, int ldo) {
+  __shared__ float Ts[64 * 64];
+  for (int e = threadIdx.x; e < m * kk; e += blockDim.x) {
+    int i = e % m, j = e / m;
+    Ts[i + j * 64] = (float)T[i + (size_t)j * ldt];
+  }
+  __syncthreads();
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+       r += (long long)gridDim.x * blockDim.x) {
+    for (int j0 = 0; j0 < kk; j0 += 16) {
+      float acc[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+      for (int i = 0; i < m; ++i) {
+        float y = Y[r + (size_t)i * ldy];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[u] = fmaf(y, Ts[i + (j0 + u) * 64], acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        if (j0 + u < kk) Out[r + (size_t)(j0 + u) * ldo] = acc[u];
+    }
+  }
+}
+
+kpsb_status la_matmul_small(const float* Y, int ldy, long long N, int m, const double* T, int ldt,
+                            int kk, float* Out, int ldo, cudaStream_t st) {
+  KPSB_REQUIRE(m >= 1 && m <= 64 && kk >= 1 && kk <= 64, "small matmul %dx%d outside 64", m, kk);
+  int nb = (int)std::min<long long>((N + LA_THREADS - 1) / LA_THREADS, 152 * 8);
+  matmul_small_kernel<<<nb, LA_THREADS, 0, st>>>(Y, ldy, N, m, T, ldt, kk, Out, ldo);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+// ---- one-sided Jacobi SVD (Hestenes) in one thread block -----------------------------------
+// Columns p < q are rotated so that they become orthogonal; a cyclic "round robin"
+// ordering visits every pair once per sweep with disjoint pairs handled by different warps.
+// After convergence the column norms are the singular values, the normalised columns the
+// left singular vectors and the accumulated rotations the right singular vectors.
+__global__ void __launch_bounds__(256) jacobi_svd_kernel(const double* __restrict__ A, int lda,
+                                                        int m, int nc, double* __restrict__ U,
+                                                        double* __restrict__ S,
+                                                        double* __restrict__ V,
+                                                        int* __restrict__ sweeps_out,
+                                                        int max_sweeps) {
+  extern __shared__ double smem[];
+  double* a = smem;            // m x nc, ld m
+  double* v = a + m * nc;      // nc x nc, ld nc
+  __shared__ int rot_count;
+  __shared__ double nrm[64];
+  __shared__ int perm[64];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (int e = tid; e < m * nc; e += blockDim.x) a[e] = A[(e % m) + (size_t)(e / m) * lda];
+  for (int e = tid; e < nc * nc; e += blockDim.x) v[e] = (e % nc == e / nc) ? 1.0 : 0.0;
+  __syncthreads();
+  const int ncp = nc + (nc & 1);
+  const double tol = fmax((double)m, 8.0) * 2.220446049250313e-16;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rot_count = 0;
+    __syncthreads();
+    for (int round = 0; round < ncp - 1; ++round) {
+      for (int pi = warp; pi < ncp / 2; pi += nwarps) {
+        int pos_a = pi, pos_b = ncp - 1 - pi;
+        int p = pos_a == 0 ? 0 : 1 + (pos_a - 1 + round) % (ncp - 1);
+        int q = 1 + (pos_b - 1 + round) % (ncp - 1);
+        if (p >= nc || q >= nc) continue;
+        if (p > q) { int t = p; p = q; q = t; }
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = lane; r < m; r += 32) {
+          double x = a[r + p * m], y = a[r + q * m];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (fabs(ga) > tol * sqrt(al * be) && ga != 0.0) {
+          double zeta = (be - al) / (2.0 * ga);
+          double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          for (int r = lane; r < m; r += 32) {
+            double x = a[r + p * m], y = a[r + q * m];
+            a[r + p * m] = c * x - s * y;
+            a[r + q * m] = s * x + c * y;
+          }
+          for (int r = lane; r < nc; r += 32) {
+            double x = v[r + p * nc], y = v[r + q * nc];
+            v[r + p * nc] = c * x - s * y;
+            v[r + q * nc] = s * x + c * y;
+          }
+          if (lane == 0) atomicAdd(&rot_count, 1);
+        }
+      }
+      __syncthreads();
+    }
+    if (rot_count == 0) break;
+    __syncthreads();
+  }
+  for (int j = warp; j < nc; j += nwarps) {
+    double s2 = 0.0;
+    for (int r = lane; r < m; r += 32) s2 = fma(a[r + j * m], a[r + j * m], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) nrm[j] = sqrt(s2);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < nc; ++j) perm[j] = j;
+    for (int i = 0; i < nc; ++i) {  // selection sort, descending, stable on ties
+      int best = i;
+      for (int j = i + 1; j < nc; ++j)
+        if (nrm[perm[j]] > nrm[perm[best]]) best = j;
+      int t = perm[i]; perm[i] = perm[best]; perm[best] = t;
+    }
+    if (sweeps_out) *sweeps_out = sweep + 1;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * nc; e += blockDim.x) {
+    int r = e % m, j = e / m, src = perm[j];
+    double sj = nrm[src];
+    U[e] = sj > 0.0 ? a[r + src * m] / sj : 0.0;
+  }
+  for (int e = tid; e < nc * nc; e += blockDim.x) V[e] = v[(e % nc) + perm[e / nc] * nc];
+  for (int j = tid; j < nc; j += blockDim.x) S[j] = nrm[perm[j]];
+}
+
+kpsb_status la_small_svd(const double* A, int lda, int m, int nc, double* U, double* S, double* V,
+                         int* sweeps, cudaStream_t st) {
+  KPSB_REQUIRE(nc >= 1 && nc <= 64 && m >= nc && m <= 128, "small SVD %dx%d outside limits", m, nc);
+  size_t sm = (size_t)(m * nc + nc * nc) * sizeof(double);
+  KPSB_TRY_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (128 * 64 + 64 * 64) * (int)sizeof(double)));
+  jacobi_svd_kernel<<<1, 256, sm, st>>>(A, lda, m, nc, U, S, V, sweeps, 60);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) + Box-Muller ---------------------------
+__device__ __forceinline__ void philox_round(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
+                                             uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  uint32_t hi0 = __umulhi(M0, x0), lo0 = M0 * x0;
+  uint32_t hi1 = __umulhi(M1, x2), lo1 = M1 * x2;
+  uint32_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+  x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+}
+
+__global__ void randn_kernel(float* __restrict__ out, long long count, uint32_t key0, uint32_t key1) {
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g * 4 < count;
+       g += (long long)gridDim.x * blockDim.x) {
+    uint32_t x0 = (uint32_t)g, x1 = (uint32_t)(g >> 32), x2 = 0u, x3 = 0u;
+    uint32_t k0 = key0, k1 = key1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      philox_round(x0, x1, x2, x3, k0, k1);
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint32_t xs[4] = {x0, x1, x2, x3};
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+      double u1 = ((double)xs[2 * pr] + 1.0) * 2.3283064365386963e-10;  // (0, 1]
+      double u2 = (double)xs[2 * pr + 1] * 2.3283064365386963e-10;       // [0, 1)
+      double rad = sqrt(-2.0 * log(u1));
+      double th = 6.283185307179586 * u2;
+      long long i0 = g * 4 + 2 * pr;
+      if (i0 < count) out[i0] = (float)(rad * cos(th));
+      if (i0 + 1 < count) out[i0 + 1] = (float)(rad * sin(th));
+    }
+  }
+}
+
+kpsb_status la_randn(float* out, long long count, unsigned long long seed, cudaStream_t st) {
+  int nb = (int)std::min<long long>((count / 4 + 255) / 256 + 1, 152 * 8);
+  randn_kernel<<<nb, 256, 0, st>>>(out, count, (uint32_t)seed, (uint32_t)(seed >> 32));
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+}  // namespace kpsb
+
+// ---- C ABI: small SVD (host pointers, synchronous) ---------------------------------------------
+using namespace kpsb;
+extern "C" kpsb_status kpsb_small_svd(int m, int nc, const double* A, double* U, double* S,
+                                      double* V, int* sweeps) {
+  clear_error();
+  KPSB_REQUIRE(A && U && S && V, "null pointer");
+  KPSB_REQUIRE(nc >= 1 && nc <= 64 && m >= nc && m <= 128, "small SVD %dx%d outside limits", m, nc);
+  double* d = nullptr;
+  size_t tot = (size_t)(2 * m * nc + nc + nc * nc) * sizeof(double) + sizeof(int);
+  KPSB_TRY_CUDA(cudaMalloc(&d, tot));
+  double *dA = d, *dU = dA + m * nc, *dS = dU + m * nc, *dV = dS + nc;
+  int* dsw = (int*)(dV + nc * nc);
+  kpsb_status s = KPSB_OK;
+  cudaError_t e = cudaMemcpy(dA, A, sizeof(double) * m * nc, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    s = la_small_svd(dA, m, m, nc, dU, dS, dV, dsw, 0);
+    if (s == KPSB_OK) e = cudaDeviceSynchronize();
+  }
+  if (e == cudaSuccess && s == KPSB_OK) {
+    cudaMemcpy(U, dU, sizeof(double) * m * nc, cudaMemcpyDeviceToHost);
+    cudaMemcpy(S, dS, sizeof(double) * nc, cudaMemcpyDeviceToHost);
+    cudaMemcpy(V, dV, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost);
+    int sw = 0;
+    e = cudaMemcpy(&sw, dsw, sizeof(int), cudaMemcpyDeviceToHost);
+    if (sweeps) *sweeps = sw;
+  }
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    set_error("small SVD: %s", cudaGetErrorString(e));
+    return KPSB_ECUDA;
+  }
+  return s;
+}

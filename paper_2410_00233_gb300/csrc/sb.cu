@@ -1,0 +1,543 @@
+// Split Bregman TV deblurring (Alg. 3 anisotropic, Alg. 4 isotropic) with CGLS (Alg. 5)
+// on the augmented system Ahat = [sqrt(mu) A_k; lambda (L (x) I); lambda (I (x) L)]
+// (eqs. (3.14)-(3.15)), batched over independent problems of one image size.
+//
+// FP64 vectors.  Per CGLS step: z1 = A_k w (KP GEMMs), |z|^2, x/r updates, f1 = A_k^T r1
+// (KP GEMMs), f and |f|^2, w = f + delta w.  All scalars live on the device; every
+// reduction is a fixed-order two-level sum, so results do not depend on the batch.
+// L = 1/2 forward difference with a zero last row (Sec. 5.3): Dx acts along columns
+// (horizontal, L_x (x) I), Dy along rows (vertical, I (x) L_y).
+#include <math.h>
+#include <stddef.h>
+#include <string.h>
+
+#include "kpsb_internal.cuh"
+
+namespace kpsb {
+
+static constexpr int SB_T = 256;
+static constexpr int SB_MAX_BLOCKS = 64;  // blocks per problem in the vector kernels
+
+struct SBScal {
+  double tau;      // ||f||^2 of the current direction
+  double step;     // mu_iota = tau / ||z||^2
+  double delta;    // tau_{iota+1} / tau_iota
+  double rc_cgls;
+  double rc_sb;
+  int active;      // CGLS of the current outer step still running
+  int sb_active;   // outer loop still running
+  int it;          // CGLS steps in the current outer step
+  int iota_total;
+  int l_end;
+  int pad;
+};
+
+struct SBProb {
+  int n, iters, iso, fixed_inner, i_max;
+  double sqrt_mu, lam, thr, tau_cgls, tau_sb;
+  const double* b;
+  double *x, *xprev, *w, *f, *r1, *r2, *r3, *z1, *f1, *dx, *dy, *gx, *gy;
+  SBScal* sc;
+  double* part;           // SB_MAX_BLOCKS * 2
+  unsigned int* counter;  // 1
+};
+
+__device__ __forceinline__ double dx_at(const double* X, int r, int c, int n) {  // (X L^T)(r,c)
+  return c < n - 1 ? 0.5 * (X[r + (size_t)c * n] - X[r + (size_t)(c + 1) * n]) : 0.0;
+}
+__device__ __forceinline__ double dy_at(const double* X, int r, int c, int n) {  // (L X)(r,c)
+  return r < n - 1 ? 0.5 * (X[r + (size_t)c * n] - X[r + 1 + (size_t)c * n]) : 0.0;
+}
+__device__ __forceinline__ double dxt_at(const double* Y, int r, int c, int n) {  // (Y L)(r,c)
+  double v = c < n - 1 ? 0.5 * Y[r + (size_t)c * n] : 0.0;
+  if (c >= 1) v -= 0.5 * Y[r + (size_t)(c - 1) * n];
+  return v;
+}
+__device__ __forceinline__ double dyt_at(const double* Y, int r, int c, int n) {  // (L^T Y)(r,c)
+  double v = r < n - 1 ? 0.5 * Y[r + (size_t)c * n] : 0.0;
+  if (r >= 1) v -= 0.5 * Y[r - 1 + (size_t)c * n];
+  return v;
+}
+
+__device__ __forceinline__ int sb_blocks(int n) {
+  int b = ((n * n) + SB_T * 4 - 1) / (SB_T * 4);
+  return b < SB_MAX_BLOCKS ? (b < 1 ? 1 : b) : SB_MAX_BLOCKS;
+}
+
+// Two-value fixed-order grid reduction inside one problem; returns true in the last block
+// with the totals in out[0..1].
+__device__ __forceinline__ bool prob_reduce2(const SBProb& P, double a, double b, double* out) {
+  __shared__ double sh[32];
+  double ta = block_sum<double>(a, sh);
+  double tb = block_sum<double>(b, sh);
+  if (threadIdx.x == 0) {
+    P.part[2 * blockIdx.x] = ta;
+    P.part[2 * blockIdx.x + 1] = tb;
+  }
+  const unsigned nb = (unsigned)sb_blocks(P.n);
+  if (!last_block_arrive(P.counter, nb)) return false;
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (unsigned i = 0; i < nb; ++i) {
+      sa += __ldcg(P.part + 2 * i);
+      sb += __ldcg(P.part + 2 * i + 1);
+    }
+    out[0] = sa;
+    out[1] = sb;
+  }
+  return true;
+}
+
+#define SB_PROLOGUE(cond)                                      \
+  const SBProb P = probs[blockIdx.y];                          \
+  if ((int)blockIdx.x >= sb_blocks(P.n)) return;               \
+  if (!(cond)) return;                                         \
+  const int n = P.n;                                           \
+  const long long N = (long long)n * n;                        \
+  const long long stride = (long long)sb_blocks(n) * SB_T;
+
+// x^(0) = b, d = g = 0, flags set (Alg. 3/4 initialisation).
+__global__ void __launch_bounds__(SB_T) sb_setup_kernel(const SBProb* __restrict__ probs) {
+  SB_PROLOGUE(true)
+  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
+    P.x[e] = P.b[e];
+    P.dx[e] = P.dy[e] = P.gx[e] = P.gy[e] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    memset(P.sc, 0, sizeof(SBScal));
+    P.sc->sb_active = 1;
+  }
+}
+
+// Outer step start: xprev = x; CGLS from x = 0 with r = bhat = [sqrt(mu) b; lam(dx-gx); lam(dy-gy)].
+__global__ void __launch_bounds__(SB_T) sb_outer_init_kernel(const SBProb* __restrict__ probs) {
+  SB_PROLOGUE(P.sc->sb_active)
+  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
+    P.xprev[e] = P.x[e];
+    P.x[e] = 0.0;
+    P.r1[e] = P.sqrt_mu * P.b[e];
+    P.r2[e] = P.lam * (P.dx[e] - P.gx[e]);
+    P.r3[e] = P.lam * (P.dy[e] - P.gy[e]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.sc->active = 1;
+    P.sc->it = 0;
+  }
+}
+
+// f = Ahat^T r = sqrt(mu) f1 + lam Dx^T r2 + lam Dy^T r3 (Alg. 5 step 7 / init) and
+// tau' = ||f||^2 (step 8); delta = tau'/tau (step 9).  init: tau = tau', delta = 0.
+__global__ void __launch_bounds__(SB_T) sb_cgls_f_kernel(const SBProb* __restrict__ probs, int init) {
+  SB_PROLOGUE(P.sc->active)
+  double ss = 0.0;
+  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
+    int r = (int)(e % n), c = (int)(e / n);
+    double v = P.sqrt_mu * P.f1[e] + P.lam * (dxt_at(P.r2, r, c, n) + dyt_at(P.r3, r, c, n));
+    P.f[e] = v;
+    ss = fma(v, v, ss);
+  }
+  double tot[2];
+  if (!prob_reduce2(P, ss, 0.0, tot)) return;
+  if (threadIdx.x == 0) {
+    SBScal* s = P.sc;
+    double taun = tot[0];
+    if (init) {
+      s->delta = 0.0;
+    } else {
+      s->delta = s->tau > 0.0 ? taun / s->tau : 0.0;
+    }
+    s->tau = taun;
+    if (!(taun > 0.0)) s->active = 0;  // exact solution reached (or b-hat = 0)
+  }
+}
+
+// w = f + delta w (step 10).
+__global__ void __launch_bounds__(SB_T) sb_cgls_w_kernel(const SBProb* __restrict__ probs) {
+  SB_PROLOGUE(P.sc->active)
+  const double dl = P.sc->delta;
+  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride)
+    P.w[e] = fma(dl, P.w[e], P.f[e]);
+}
+
+// ||z||^2 with z = Ahat w = [sqrt(mu) z1; lam Dx w; lam Dy w] (steps 3-4).
+__global__ void __launch_bounds__(SB_T) sb_cgls_zz_kernel(const SBProb* __restrict__ probs) {
+  SB_PROLOGUE(P.sc->active)
+  double ss = 0.0;
+  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
+    int r = (int)(e % n), c = (int)(e / n);
+    double a = P.sqrt_mu * P.z1[e], bx = P.lam * dx_at(P.w, r, c, n), by = P.lam * dy_at(P.w, r, c, n);
+    ss = fma(a, a, fma(bx, bx, fma(by, by, ss)));
+  }
+  double tot[2];
+  if (!prob_reduce2(P, ss, 0.0, tot)) return;
+  if (threadIdx.x == 0) {
+    SBScal* s = P.sc;
+    if (tot[0] > 0.0) {
+      s->step = s->tau / tot[0];
+    } else {
+      s->step = 0.0;
+      s->active = 0;
+    }
+  }
+}
+
+// x += mu w; r -= mu z (steps 5-6); RC_CGLS = ||mu w|| / ||x|| (eq. (5.1)) and the stop test.
+__global__ void __launch_bounds__(SB_T) sb_cgls_x_kernel(const SBProb* __restrict__ probs) {
+  SB_PROLOGUE(P.sc->active)
+  const double mu = P.sc->step;
+  double sx = 0.0, sw = 0.0;
+  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
+    int r = (int)(e % n), c = (int)(e / n);
+    double w = P.w[e];
+    double xn = fma(mu, w, P.x[e]);
+    P.x[e] = xn;
+    P.r1[e] -= mu * (P.sqrt_mu * P.z1[e]);
+    P.r2[e] -= mu * (P.lam * dx_at(P.w, r, c, n));
+    P.r3[e] -= mu * (P.lam * dy_at(P.w, r, c, n));
+    sx = fma(xn, xn, sx);
+    sw = fma(w, w, sw);
+  }
+  double tot[2];
+  if (!prob_reduce2(P, sx, sw, tot)) return;
+  if (threadIdx.x == 0) {
+    SBScal* s = P.sc;
+    double xn = sqrt(tot[0]);
+    s->rc_cgls = xn > 0.0 ? mu * sqrt(tot[1]) / xn : INFINITY;
+    s->it += 1;
+    s->iota_total += 1;
+    if (s->it >= P.i_max || (!P.fixed_inner && s->rc_cgls < P.tau_cgls)) s->active = 0;
+  }
+}
+
+// Shrinkage (3.10) / (3.13) and Bregman updates (3.8)-(3.9); RC_SB (5.2).
+__global__ void __launch_bounds__(SB_T) sb_shrink_kernel(const SBProb* __restrict__ probs) {
+  SB_PROLOGUE(P.sc->sb_active)
+  double sd = 0.0, sp = 0.0;
+  const double thr = P.thr;
+  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
+    int r = (int)(e % n), c = (int)(e / n);
+    double cx = dx_at(P.x, r, c, n) + P.gx[e];
+    double cy = dy_at(P.x, r, c, n) + P.gy[e];
+    double dxv, dyv;
+    if (P.iso) {
+      double s = sqrt(cx * cx + cy * cy);
+      double sc = s > 0.0 ? fmax(s - thr, 0.0) / s : 0.0;
+      dxv = cx * sc;
+      dyv = cy * sc;
+    } else {
+      dxv = copysign(fmax(fabs(cx) - thr, 0.0), cx);
+      dyv = copysign(fmax(fabs(cy) - thr, 0.0), cy);
+    }
+    P.dx[e] = dxv;
+    P.dy[e] = dyv;
+    P.gx[e] = cx - dxv;
+    P.gy[e] = cy - dyv;
+    double dd = P.x[e] - P.xprev[e], xp = P.xprev[e];
+    sd = fma(dd, dd, sd);
+    sp = fma(xp, xp, sp);
+  }
+  double tot[2];
+  if (!prob_reduce2(P, sd, sp, tot)) return;
+  if (threadIdx.x == 0) {
+    SBScal* s = P.sc;
+    s->rc_sb = tot[1] > 0.0 ? sqrt(tot[0]) / sqrt(tot[1]) : INFINITY;
+    s->l_end += 1;
+    if (s->l_end >= P.iters || s->rc_sb < P.tau_sb) s->sb_active = 0;
+  }
+}
+
+// ---- host driver -------------------------------------------------------------------------------
+struct SBJobIn {
+  kpsb_kp* kp;
+  const double* b;  // device
+  double* x;        // device
+  double mu, lambda, beta;
+  int tv, iters;
+};
+
+static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Runs all jobs (same n) to completion on stream st.  stats_out receives one entry per job.
+static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_opts& o,
+                                cudaStream_t st, std::vector<kpsb_sb_stats>& stats_out) {
+  const int P = (int)jobs.size();
+  const int n = jobs[0].kp->n;
+  const size_t N = (size_t)n * n;
+  int kmax = 0;
+  for (auto& j : jobs) kmax = std::max(kmax, j.kp->k);
+  const bool tc = o.prec == KPSB_P_TF32X3 || o.prec == KPSB_P_BF16X3;
+  const size_t zbytes = tc ? 0 : a256(kp_z_bytes(n, kmax, o.prec));
+  const size_t per = a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
+                     a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256;
+  const size_t total = per * P + a256(sizeof(SBProb) * P) + 2 * a256(sizeof(KPJob) * P);
+  char* base = nullptr;
+  KPSB_TRY_CUDA(cudaMallocAsync((void**)&base, total, st));
+  std::vector<SBProb> hp(P);
+  std::vector<KPJob> fwd(P), bwd(P);
+  std::vector<kpsb_kp*> kps(P);
+  for (int p = 0; p < P; ++p) {
+    char* q = base + per * p;
+    SBProb& S = hp[p];
+    const SBJobIn& J = jobs[p];
+    double* v = (double*)q;
+    S.n = n;
+    S.iters = J.iters;
+    S.iso = J.tv == KPSB_ISO;
+    S.fixed_inner = o.fixed_inner;
+    S.i_max = o.i_max;
+    S.sqrt_mu = sqrt(J.mu);
+    S.lam = J.lambda;
+    S.thr = o.threshold_rule == KPSB_THR_PAPER ? J.beta / (J.lambda * J.lambda)
+                                                : J.beta / (2.0 * J.lambda * J.lambda);
+    S.tau_cgls = o.tau_cgls;
+    S.tau_sb = o.tau_sb;
+    S.b = J.b;
+    S.x = J.x;
+    S.xprev = v + 0 * N; S.w = v + 1 * N; S.f = v + 2 * N; S.r1 = v + 3 * N; S.r2 = v + 4 * N;
+    S.r3 = v + 5 * N; S.z1 = v + 6 * N; S.f1 = v + 7 * N; S.dx = v + 8 * N; S.dy = v + 9 * N;
+    S.gx = v + 10 * N; S.gy = v + 11 * N;
+    q += a256(13 * N * sizeof(double));
+    void* Z = q;
+    q += zbytes;
+    S.sc = (SBScal*)q;
+    q += a256(sizeof(SBScal));
+    S.part = (double*)q;
+    q += a256(sizeof(double) * SB_MAX_BLOCKS * 2);
+    S.counter = (unsigned int*)q;
+    kps[p] = J.kp;
+    KPJob& F = fwd[p];
+    F.Ax = J.kp->Ax; F.Ay = J.kp->Ay; F.sigma = J.kp->sigma_d; F.n = n; F.k = J.kp->k;
+    F.X = S.w; F.Y = S.z1; F.Z = Z;
+    F.active = (const int*)((char*)S.sc + offsetof(SBScal, active));
+    KPJob& B = bwd[p];
+    B = F;
+    B.X = S.r1; B.Y = S.f1;
+  }
+  SBProb* dprobs = (SBProb*)(base + per * P);
+  KPJob* dfwd = (KPJob*)((char*)dprobs + a256(sizeof(SBProb) * P));
+  KPJob* dbwd = (KPJob*)((char*)dfwd + a256(sizeof(KPJob) * P));
+  kpsb_status s = KPSB_OK;
+  cudaError_t e = cudaSuccess;
+  SBScal* hsc = nullptr;
+  do {
+    for (int p = 0; p < P && e == cudaSuccess; ++p)
+      e = cudaMemsetAsync(hp[p].counter, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dprobs, hp.data(), sizeof(SBProb) * P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dfwd, fwd.data(), sizeof(KPJob) * P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dbwd, bwd.data(), sizeof(KPJob) * P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&hsc, sizeof(SBScal) * P);
+    if (e != cudaSuccess) { set_error("sb setup: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+    const int blocks = std::max(1, std::min(SB_MAX_BLOCKS, (int)((N + SB_T * 4 - 1) / (SB_T * 4))));
+    dim3 gv(blocks, P);
+    auto kp_fwd = [&]() -> kpsb_status {
+      return tc ? tc_apply_batch(kps.data(), dfwd, fwd.data(), P, n, kmax, 0, o.prec, st)
+                : kp_apply_batch(dfwd, P, n, kmax, 0, o.prec, st);
+    };
+    auto kp_bwd = [&]() -> kpsb_status {
+      return tc ? tc_apply_batch(kps.data(), dbwd, bwd.data(), P, n, kmax, 1, o.prec, st)
+                : kp_apply_batch(dbwd, P, n, kmax, 1, o.prec, st);
+    };
+    sb_setup_kernel<<<gv, SB_T, 0, st>>>(dprobs);
+    KPSB_CHECK_LAUNCH();
+    int max_iters = 0;
+    for (auto& j : jobs) max_iters = std::max(max_iters, j.iters);
+    const int CHUNK = 4;
+    for (int ell = 0; ell < max_iters && s == KPSB_OK; ++ell) {
+      sb_outer_init_kernel<<<gv, SB_T, 0, st>>>(dprobs);
+      KPSB_CHECK_LAUNCH();
+      if ((s = kp_bwd())) break;
+      sb_cgls_f_kernel<<<gv, SB_T, 0, st>>>(dprobs, 1);
+      sb_cgls_w_kernel<<<gv, SB_T, 0, st>>>(dprobs);
+      KPSB_CHECK_LAUNCH();
+      for (int it = 0; it < o.i_max; ++it) {
+        if ((s = kp_fwd())) break;
+        sb_cgls_zz_kernel<<<gv, SB_T, 0, st>>>(dprobs);
+        sb_cgls_x_kernel<<<gv, SB_T, 0, st>>>(dprobs);
+        KPSB_CHECK_LAUNCH();
+        if ((s = kp_bwd())) break;
+        sb_cgls_f_kernel<<<gv, SB_T, 0, st>>>(dprobs, 0);
+        sb_cgls_w_kernel<<<gv, SB_T, 0, st>>>(dprobs);
+        KPSB_CHECK_LAUNCH();
+        if (!o.fixed_inner && (it + 1) % CHUNK == 0 && it + 1 < o.i_max) {
+          for (int p = 0; p < P && e == cudaSuccess; ++p)
+            e = cudaMemcpyAsync(hsc + p, hp[p].sc, sizeof(SBScal), cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+          if (e != cudaSuccess) break;
+          bool any = false;
+          for (int p = 0; p < P; ++p) any |= hsc[p].active != 0;
+          if (!any) break;
+        }
+      }
+      if (s) break;
+      if (e != cudaSuccess) { set_error("sb loop: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+      sb_shrink_kernel<<<gv, SB_T, 0, st>>>(dprobs);
+      KPSB_CHECK_LAUNCH();
+      if (o.tau_sb > 0.0 && (ell + 1) % 2 == 0) {
+        for (int p = 0; p < P && e == cudaSuccess; ++p)
+          e = cudaMemcpyAsync(hsc + p, hp[p].sc, sizeof(SBScal), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { set_error("sb loop: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+        bool any = false;
+        for (int p = 0; p < P; ++p) any |= hsc[p].sb_active != 0;
+        if (!any) break;
+      }
+    }
+    if (s) break;
+    for (int p = 0; p < P && e == cudaSuccess; ++p)
+      e = cudaMemcpyAsync(hsc + p, hp[p].sc, sizeof(SBScal), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { set_error("sb finish: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+    stats_out.resize(P);
+    for (int p = 0; p < P; ++p) {
+      stats_out[p].l_end = hsc[p].l_end;
+      stats_out[p].iota_total = hsc[p].iota_total;
+      stats_out[p].rc_sb = hsc[p].rc_sb;
+      stats_out[p].status = KPSB_OK;
+    }
+  } while (0);
+  if (hsc) cudaFreeHost(hsc);
+  cudaFreeAsync(base, st);
+  return s;
+}
+
+static kpsb_status sb_defaults(const kpsb_sb_opts* opts, kpsb_sb_opts& o) {
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.tau_cgls <= 0.0) o.tau_cgls = 1e-4;
+  if (o.i_max <= 0) o.i_max = 100;
+  KPSB_REQUIRE(o.prec >= KPSB_P_FP64 && o.prec <= KPSB_P_BF16X3, "unknown precision %d", o.prec);
+  KPSB_REQUIRE(o.threshold_rule == KPSB_THR_EXACT || o.threshold_rule == KPSB_THR_PAPER,
+               "unknown threshold rule %d", o.threshold_rule);
+  return KPSB_OK;
+}
+
+static kpsb_status sb_check_job(kpsb_kp* kp, double mu, double lambda, int tv, int iters) {
+  KPSB_REQUIRE(kp, "null handle");
+  KPSB_REQUIRE(mu > 0.0 && lambda > 0.0 && isfinite(mu) && isfinite(lambda), "mu and lambda must be > 0");
+  KPSB_REQUIRE(tv == KPSB_ANISO || tv == KPSB_ISO, "unknown TV type %d", tv);
+  KPSB_REQUIRE(iters >= 1, "iters must be >= 1");
+  return KPSB_OK;
+}
+
+}  // namespace kpsb
+
+using namespace kpsb;
+
+extern "C" kpsb_status sb_solve_dev(kpsb_kp_t kp, const double* b, double mu, double lambda, int tv,
+                                    int iters, const kpsb_sb_opts* opts, double* x_out,
+                                    kpsb_sb_stats* stats) {
+  clear_error();
+  KPSB_TRY(sb_check_job(kp, mu, lambda, tv, iters));
+  KPSB_REQUIRE(b && x_out && b != x_out, "null or aliased pointer");
+  kpsb_sb_opts o;
+  KPSB_TRY(sb_defaults(opts, o));
+  double beta = o.beta > 0.0 ? o.beta : lambda * lambda / 2.0;
+  std::vector<SBJobIn> jobs(1);
+  jobs[0] = SBJobIn{kp, b, x_out, mu, lambda, beta, tv, iters};
+  std::vector<kpsb_sb_stats> st;
+  kpsb_status s = sb_run_group(jobs, o, (cudaStream_t)o.stream, st);
+  if (s == KPSB_OK && stats) *stats = st[0];
+  return s;
+}
+
+extern "C" kpsb_status sb_solve(kpsb_kp_t kp, const double* b, double mu, double lambda, int tv,
+                                int iters, const kpsb_sb_opts* opts, double* x_out,
+                                kpsb_sb_stats* stats) {
+  clear_error();
+  KPSB_TRY(sb_check_job(kp, mu, lambda, tv, iters));
+  KPSB_REQUIRE(b && x_out, "null pointer");
+  const size_t bytes = sizeof(double) * (size_t)kp->n * kp->n;
+  kpsb_sb_opts o;
+  KPSB_TRY(sb_defaults(opts, o));
+  cudaStream_t st = (cudaStream_t)o.stream;
+  double* d = nullptr;
+  KPSB_TRY_CUDA(cudaMallocAsync((void**)&d, 2 * bytes, st));
+  kpsb_status s = KPSB_OK;
+  cudaError_t e = cudaMemcpyAsync(d, b, bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    s = sb_solve_dev(kp, d, mu, lambda, tv, iters, &o, d + bytes / sizeof(double), stats);
+    if (s == KPSB_OK) e = cudaMemcpyAsync(x_out, d + bytes / sizeof(double), bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFreeAsync(d, st);
+  if (e != cudaSuccess) {
+    set_error("sb_solve: %s", cudaGetErrorString(e));
+    return KPSB_ECUDA;
+  }
+  return s;
+}
+
+extern "C" kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int on_device,
+                                        const kpsb_sb_opts* opts) {
+  clear_error();
+  KPSB_REQUIRE(count >= 0 && (count == 0 || jobs), "bad batch");
+  if (count == 0) return KPSB_OK;
+  kpsb_sb_opts o;
+  KPSB_TRY(sb_defaults(opts, o));
+  cudaStream_t st = (cudaStream_t)o.stream;
+  for (int i = 0; i < count; ++i) {
+    KPSB_TRY(sb_check_job(jobs[i].kp, jobs[i].mu, jobs[i].lambda, jobs[i].tv, jobs[i].iters));
+    KPSB_REQUIRE(jobs[i].b && jobs[i].x, "job %d: null pointer", i);
+  }
+  // group by image size; each group shares its launches
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return jobs[a].kp->n < jobs[b].kp->n; });
+  size_t host_bytes = 0;
+  for (int i = 0; i < count; ++i) host_bytes += 2 * sizeof(double) * (size_t)jobs[i].kp->n * jobs[i].kp->n;
+  double* dbuf = nullptr;
+  if (!on_device) KPSB_TRY_CUDA(cudaMallocAsync((void**)&dbuf, host_bytes, st));
+  std::vector<double*> db(count), dx(count);
+  kpsb_status s = KPSB_OK;
+  cudaError_t e = cudaSuccess;
+  size_t off = 0;
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    size_t nn = (size_t)jobs[i].kp->n * jobs[i].kp->n;
+    if (on_device) {
+      db[i] = const_cast<double*>(jobs[i].b);
+      dx[i] = jobs[i].x;
+    } else {
+      db[i] = dbuf + off;
+      dx[i] = dbuf + off + nn;
+      off += 2 * nn;
+      e = cudaMemcpyAsync(db[i], jobs[i].b, nn * sizeof(double), cudaMemcpyHostToDevice, st);
+    }
+  }
+  if (e != cudaSuccess) {
+    set_error("sb_solve_batched upload: %s", cudaGetErrorString(e));
+    s = KPSB_ECUDA;
+  }
+  int g0 = 0;
+  while (s == KPSB_OK && g0 < count) {
+    int g1 = g0;
+    const int n = jobs[order[g0]].kp->n;
+    std::vector<SBJobIn> grp;
+    while (g1 < count && jobs[order[g1]].kp->n == n) {
+      const kpsb_sb_job& J = jobs[order[g1]];
+      double beta = J.beta > 0.0 ? J.beta : J.lambda * J.lambda / 2.0;
+      grp.push_back(SBJobIn{J.kp, db[order[g1]], dx[order[g1]], J.mu, J.lambda, beta, J.tv, J.iters});
+      ++g1;
+    }
+    std::vector<kpsb_sb_stats> stv;
+    s = sb_run_group(grp, o, st, stv);
+    if (s == KPSB_OK)
+      for (int t = g0; t < g1; ++t)
+        if (jobs[order[t]].stats) *jobs[order[t]].stats = stv[t - g0];
+    g0 = g1;
+  }
+  if (s == KPSB_OK && !on_device) {
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+      size_t nn = (size_t)jobs[i].kp->n * jobs[i].kp->n;
+      e = cudaMemcpyAsync(jobs[i].x, dx[i], nn * sizeof(double), cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_error("sb_solve_batched download: %s", cudaGetErrorString(e));
+      s = KPSB_ECUDA;
+    }
+  }
+  if (dbuf) cudaFreeAsync(dbuf, st);
+  if (s == KPSB_OK) cudaStreamSynchronize(st);
+  return s;
+}

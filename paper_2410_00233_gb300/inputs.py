@@ -64,7 +64,9 @@ def psf_gaussian_mixture(s: int, g: np.random.Generator) -> np.ndarray:
 
 
 def psf_turbulence(s: int, g: np.random.Generator) -> np.ndarray:
-    """Turbulence-like PSF exp(-(rho/r0)^(5/3)), rho anisotropic (a/b in [1,2]) and rotated."""
+    """Turbulence-like speckle PSF: envelope exp(-(rho/r0)^(5/3)) with anisotropic, rotated
+    rho (a/b in [1,2], r0 in [2, s/6]) times a pixelwise speckle factor 1 + 0.5 U[-1,1]
+    (non-separable, slowly decaying Kronecker spectrum like the paper's speckle PSFs)."""
     th = g.uniform(0.0, math.pi)
     ratio = g.uniform(1.0, 2.0)
     r0 = g.uniform(2.0, max(2.0, s / 6.0))
@@ -72,7 +74,8 @@ def psf_turbulence(s: int, g: np.random.Generator) -> np.ndarray:
     u = math.cos(th) * dx + math.sin(th) * dy
     v = -math.sin(th) * dx + math.cos(th) * dy
     rho = np.sqrt((u / ratio) ** 2 + v**2)
-    return _normalise(np.exp(-((rho / r0) ** (5.0 / 3.0))))
+    speckle = 1.0 + 0.5 * g.uniform(-1.0, 1.0, size=(s, s))
+    return _normalise(np.exp(-((rho / r0) ** (5.0 / 3.0))) * speckle)
 
 
 def psf_separable(s: int, g: np.random.Generator) -> np.ndarray:

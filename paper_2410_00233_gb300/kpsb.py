@@ -1,0 +1,340 @@
+"""Thin ctypes binding of the kpsb C ABI (include/kpsb.h); argument marshalling only.
+
+Every computation runs in libkpsb.so (CUDA, sm_103a).  Images and factors are column-major
+(numpy Fortran order); host arrays are copied into Fortran-contiguous float64/float32
+buffers before the call.  Device pointers are plain integers (e.g. ``tensor.data_ptr()``)
+and streams are ``cudaStream_t`` handles as integers (``torch.cuda.Stream.cuda_stream``).
+The library must have been built (``python -m paper_2410_00233_gb300.build`` or
+``__graft_entry__.build()``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkpsb.so")
+
+KPSB_OK = 0
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBREAKDOWN",
+          -6: "ENOTCONV", -7: "EBUSY", -8: "ENOTFOUND"}
+BC_ZERO, BC_REFLEXIVE = 0, 1
+EGKB, RSVD = 0, 1
+ANISO, ISO = 0, 1
+P_FP64, P_FP32, P_TF32X3, P_BF16X3 = 0, 1, 2, 3
+THR_EXACT, THR_PAPER = 0, 1
+
+
+class KpsbError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__(f"{fn} failed: {STATUS.get(code, code)} ({msg})")
+        self.code = code
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("p", C.c_int), ("k_min", C.c_int), ("one_sided", C.c_int), ("power_iters", C.c_int),
+                ("seed", C.c_ulonglong), ("start_host", C.POINTER(C.c_float)), ("stream", C.c_void_p)]
+
+
+class SBOpts(C.Structure):
+    _fields_ = [("beta", C.c_double), ("tau_sb", C.c_double), ("tau_cgls", C.c_double),
+                ("i_max", C.c_int), ("fixed_inner", C.c_int), ("prec", C.c_int),
+                ("threshold_rule", C.c_int), ("stream", C.c_void_p)]
+
+
+class SBStats(C.Structure):
+    _fields_ = [("l_end", C.c_int), ("iota_total", C.c_int), ("rc_sb", C.c_double), ("status", C.c_int)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("psf", C.POINTER(C.c_double)), ("s0", C.c_int), ("s1", C.c_int), ("n", C.c_int),
+                ("bc", C.c_int), ("rank_or_tol", C.c_double), ("method", C.c_int), ("opts", BuildOpts)]
+
+
+class SBJob(C.Structure):
+    _fields_ = [("kp", C.c_void_p), ("b", C.c_void_p), ("x", C.c_void_p), ("mu", C.c_double),
+                ("lambda_", C.c_double), ("beta", C.c_double), ("tv", C.c_int), ("iters", C.c_int),
+                ("stats", C.POINTER(SBStats))]
+
+
+_lib = None
+
+_SIGS = {
+    "kp_build": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                           C.c_int, C.POINTER(BuildOpts), C.POINTER(C.c_void_p)]),
+    "kp_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                          C.POINTER(C.c_double)]),
+    "kp_get_factors": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                 C.POINTER(C.c_double)]),
+    "kp_from_factors": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_void_p)]),
+    "kp_apply": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_int]),
+    "kp_apply_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "kp_free": (None, [C.c_void_p]),
+    "sb_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_double, C.c_int, C.c_int,
+                           C.POINTER(SBOpts), C.POINTER(C.c_double), C.POINTER(SBStats)]),
+    "sb_solve_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
+                               C.POINTER(SBOpts), C.c_void_p, C.POINTER(SBStats)]),
+    "kp_build_batched": (C.c_int, [C.c_int, C.POINTER(Problem), C.POINTER(C.c_void_p)]),
+    "sb_solve_batched": (C.c_int, [C.c_int, C.POINTER(SBJob), C.c_int, C.POINTER(SBOpts)]),
+    "kp_blur_dev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                              C.c_int, C.c_void_p]),
+    "kp_ra_apply_dev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                  C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "kp_ra_materialize_dev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                        C.c_void_p]),
+    "kpsb_small_svd": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "kpsb_last_error": (C.c_char_p, []),
+}
+
+
+def lib() -> C.CDLL:
+    """Loads libkpsb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it first (paper_2410_00233_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().kpsb_last_error().decode()
+
+
+def _check(fn: str, code: int):
+    if code != KPSB_OK:
+        raise KpsbError(fn, code, last_error())
+
+
+def _f64(a) -> np.ndarray:
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def _f32(a) -> np.ndarray:
+    return np.asfortranarray(np.asarray(a, dtype=np.float32))
+
+
+def _pd(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _pf(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class KP:
+    """Owning handle of a KP-sum operator (device factors)."""
+
+    def __init__(self, ptr: int):
+        self.ptr = C.c_void_p(ptr)
+
+    def close(self):
+        if self.ptr and self.ptr.value:
+            lib().kp_free(self.ptr)
+            self.ptr = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self):
+        return kp_info(self)
+
+
+def _build_opts(p=0, k_min=0, one_sided=False, power_iters=0, seed=0, start=None, stream=0):
+    o = BuildOpts()
+    o.p, o.k_min, o.one_sided, o.power_iters = int(p), int(k_min), int(bool(one_sided)), int(power_iters)
+    o.seed = int(seed)
+    keep = None
+    if start is not None:
+        keep = _f32(start)
+        o.start_host = _pf(keep)
+    o.stream = C.c_void_p(int(stream)) if stream else None
+    return o, keep
+
+
+def kp_build(psf, n: int, bc: int, rank_or_tol: float, method: int = EGKB, *, p=0, k_min=0,
+             one_sided=False, power_iters=0, seed=0, start=None, stream=0) -> KP:
+    """TSVD of R(A) + Terms(A_k) (see kp_build in include/kpsb.h)."""
+    ps = _f64(psf)
+    o, keep = _build_opts(p, k_min, one_sided, power_iters, seed, start, stream)
+    out = C.c_void_p()
+    _check("kp_build", lib().kp_build(_pd(ps), ps.shape[0], ps.shape[1], int(n), int(bc),
+                                      float(rank_or_tol), int(method), C.byref(o), C.byref(out)))
+    del keep
+    return KP(out.value)
+
+
+def kp_info(kp: KP):
+    n, k, kps = C.c_int(), C.c_int(), C.c_int()
+    _check("kp_info", lib().kp_info(kp.ptr, C.byref(n), C.byref(k), C.byref(kps), None))
+    sig = np.zeros(k.value)
+    _check("kp_info", lib().kp_info(kp.ptr, None, None, None, _pd(sig)))
+    return dict(n=n.value, k=k.value, kp=kps.value, sigma=sig)
+
+
+def kp_get_factors(kp: KP):
+    inf = kp_info(kp)
+    n, k = inf["n"], inf["k"]
+    Ax = np.zeros((n * n * k,), dtype=np.float32)
+    Ay = np.zeros((n * n * k,), dtype=np.float32)
+    sig = np.zeros(k)
+    _check("kp_get_factors", lib().kp_get_factors(kp.ptr, _pf(Ax), _pf(Ay), _pd(sig)))
+    # term i is the column-major n x n block i
+    Ax = Ax.reshape(k, n * n).reshape(k, n, n).transpose(0, 2, 1)
+    Ay = Ay.reshape(k, n * n).reshape(k, n, n).transpose(0, 2, 1)
+    return np.ascontiguousarray(Ax), np.ascontiguousarray(Ay), sig
+
+
+def kp_from_factors(Ax, Ay, sigma) -> KP:
+    Ax = np.asarray(Ax, dtype=np.float32)
+    Ay = np.asarray(Ay, dtype=np.float32)
+    k, n, _ = Ax.shape
+    ax = np.ascontiguousarray(Ax.transpose(0, 2, 1)).reshape(-1)  # column-major blocks
+    ay = np.ascontiguousarray(Ay.transpose(0, 2, 1)).reshape(-1)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    out = C.c_void_p()
+    _check("kp_from_factors", lib().kp_from_factors(n, k, _pf(ax), _pf(ay), _pd(sg), C.byref(out)))
+    return KP(out.value)
+
+
+def kp_apply(kp: KP, X, transpose: int = 0, prec: int = P_FP64) -> np.ndarray:
+    Xf = _f64(X)
+    Y = np.zeros_like(Xf, order="F")
+    _check("kp_apply", lib().kp_apply(kp.ptr, _pd(Xf), _pd(Y), int(transpose), int(prec)))
+    return Y
+
+
+def kp_apply_dev(kp: KP, X_ptr: int, Y_ptr: int, transpose: int = 0, prec: int = P_FP64, stream=0):
+    _check("kp_apply_dev", lib().kp_apply_dev(kp.ptr, C.c_void_p(X_ptr), C.c_void_p(Y_ptr), int(transpose),
+                                              int(prec), C.c_void_p(int(stream)) if stream else None))
+
+
+def _sb_opts(beta=0.0, tau_sb=0.0, tau_cgls=0.0, i_max=0, fixed_inner=False, prec=P_FP64,
+             threshold_rule=THR_EXACT, stream=0) -> SBOpts:
+    o = SBOpts()
+    o.beta, o.tau_sb, o.tau_cgls = float(beta), float(tau_sb), float(tau_cgls)
+    o.i_max, o.fixed_inner, o.prec, o.threshold_rule = int(i_max), int(bool(fixed_inner)), int(prec), int(threshold_rule)
+    o.stream = C.c_void_p(int(stream)) if stream else None
+    return o
+
+
+@dataclass
+class Stats:
+    l_end: int
+    iota_total: int
+    rc_sb: float
+    status: int
+
+
+def _stats(s: SBStats) -> Stats:
+    return Stats(s.l_end, s.iota_total, s.rc_sb, s.status)
+
+
+def sb_solve(kp: KP, b, mu: float, lam: float, tv: int, iters: int, **opts):
+    """Split Bregman deblurring on host arrays; returns (x, Stats)."""
+    bf = _f64(b)
+    x = np.zeros_like(bf, order="F")
+    st = SBStats()
+    o = _sb_opts(**opts)
+    _check("sb_solve", lib().sb_solve(kp.ptr, _pd(bf), float(mu), float(lam), int(tv), int(iters),
+                                      C.byref(o), _pd(x), C.byref(st)))
+    return x, _stats(st)
+
+
+def sb_solve_dev(kp: KP, b_ptr: int, x_ptr: int, mu: float, lam: float, tv: int, iters: int, **opts):
+    st = SBStats()
+    o = _sb_opts(**opts)
+    _check("sb_solve_dev", lib().sb_solve_dev(kp.ptr, C.c_void_p(b_ptr), float(mu), float(lam), int(tv),
+                                              int(iters), C.byref(o), C.c_void_p(x_ptr), C.byref(st)))
+    return _stats(st)
+
+
+def kp_build_batched(problems) -> list:
+    """problems: list of dicts with psf, n, bc, rank_or_tol, method and build options."""
+    arr = (Problem * len(problems))()
+    keep = []
+    for i, pr in enumerate(problems):
+        ps = _f64(pr["psf"])
+        keep.append(ps)
+        o, k2 = _build_opts(pr.get("p", 0), pr.get("k_min", 0), pr.get("one_sided", False),
+                            pr.get("power_iters", 0), pr.get("seed", 0), pr.get("start"))
+        keep.append(k2)
+        arr[i].psf = _pd(ps)
+        arr[i].s0, arr[i].s1 = ps.shape
+        arr[i].n, arr[i].bc = int(pr["n"]), int(pr["bc"])
+        arr[i].rank_or_tol = float(pr["rank_or_tol"])
+        arr[i].method = int(pr.get("method", EGKB))
+        arr[i].opts = o
+    outs = (C.c_void_p * len(problems))()
+    _check("kp_build_batched", lib().kp_build_batched(len(problems), arr, outs))
+    return [KP(outs[i]) for i in range(len(problems))]
+
+
+def sb_solve_batched(jobs, on_device: bool = False, **opts):
+    """jobs: list of dicts with kp, b, mu, lam, tv, iters (and beta).  Host mode: b are
+    arrays and the results are returned; device mode: b and x are device pointers."""
+    arr = (SBJob * len(jobs))()
+    stats = (SBStats * len(jobs))()
+    keep, outs = [], []
+    for i, j in enumerate(jobs):
+        arr[i].kp = j["kp"].ptr
+        if on_device:
+            arr[i].b, arr[i].x = j["b"], j["x"]
+        else:
+            bf = _f64(j["b"])
+            xf = np.zeros_like(bf, order="F")
+            keep.append(bf)
+            outs.append(xf)
+            arr[i].b, arr[i].x = bf.ctypes.data, xf.ctypes.data
+        arr[i].mu, arr[i].lambda_ = float(j["mu"]), float(j["lam"])
+        arr[i].beta = float(j.get("beta", 0.0))
+        arr[i].tv, arr[i].iters = int(j["tv"]), int(j["iters"])
+        arr[i].stats = C.pointer(stats[i])
+    o = _sb_opts(**opts)
+    _check("sb_solve_batched", lib().sb_solve_batched(len(jobs), arr, int(bool(on_device)), C.byref(o)))
+    st = [_stats(stats[i]) for i in range(len(jobs))]
+    return (st if on_device else (outs, st))
+
+
+def kp_blur_dev(psf_ptr: int, s0: int, s1: int, n: int, bc: int, X_ptr: int, B_ptr: int,
+                transpose: int = 0, stream=0):
+    _check("kp_blur_dev", lib().kp_blur_dev(C.c_void_p(psf_ptr), s0, s1, n, bc, C.c_void_p(X_ptr),
+                                            C.c_void_p(B_ptr), int(transpose),
+                                            C.c_void_p(int(stream)) if stream else None))
+
+
+def kp_ra_apply_dev(psf_ptr: int, s0: int, s1: int, n: int, bc: int, V_ptr: int, ldv: int, nb: int,
+                    U_ptr: int, ldu: int, transpose: int = 0, stream=0):
+    _check("kp_ra_apply_dev", lib().kp_ra_apply_dev(C.c_void_p(psf_ptr), s0, s1, n, bc, C.c_void_p(V_ptr),
+                                                    ldv, nb, C.c_void_p(U_ptr), ldu, int(transpose),
+                                                    C.c_void_p(int(stream)) if stream else None))
+
+
+def kp_ra_materialize_dev(psf_ptr: int, s0: int, s1: int, n: int, bc: int, R_ptr: int, stream=0):
+    _check("kp_ra_materialize_dev", lib().kp_ra_materialize_dev(
+        C.c_void_p(psf_ptr), s0, s1, n, bc, C.c_void_p(R_ptr), C.c_void_p(int(stream)) if stream else None))
+
+
+def kpsb_small_svd(A):
+    Af = _f64(A)
+    m, nc = Af.shape
+    U = np.zeros((m, nc), order="F")
+    S = np.zeros(nc)
+    V = np.zeros((nc, nc), order="F")
+    sw = C.c_int()
+    _check("kpsb_small_svd", lib().kpsb_small_svd(m, nc, _pd(Af), _pd(U), _pd(S), _pd(V), C.byref(sw)))
+    return U, S, V, sw.value

@@ -1,0 +1,63 @@
+"""The C-ABI library loads and exports every function include/kpsb.h declares (no GPU)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([a-z][a-z0-9_]*)\s*\(",
+                             txt, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_hot_path_calls():
+    names = _declared()
+    for required in ("kp_build", "sb_solve", "kp_apply", "kp_free", "kpsb_last_error"):
+        assert required in names
+
+
+def test_library_exports_all_declared_symbols():
+    from paper_2410_00233_gb300 import build as B
+    from paper_2410_00233_gb300 import kpsb as K
+
+    if not os.path.exists(K.LIB_PATH):
+        B.build()
+    L = K.lib()
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+    assert L.kpsb_last_error() is not None
+
+
+def test_binding_covers_header():
+    from paper_2410_00233_gb300 import kpsb as K
+
+    missing = [n for n in _declared() if n not in K._SIGS]
+    assert not missing, missing
+
+
+def test_invalid_arguments_fail_without_touching_the_gpu():
+    import numpy as np
+
+    from paper_2410_00233_gb300 import kpsb as K
+
+    with pytest.raises(K.KpsbError) as e:
+        K.kp_build(np.ones((3, 3)), 1, K.BC_ZERO, 2, K.EGKB)  # n < 2
+    assert e.value.code == -1
+    with pytest.raises(K.KpsbError) as e:
+        K.kp_build(np.ones((3, 3)), 8, 7, 2, K.EGKB)  # unknown boundary
+    assert e.value.code == -1
+    with pytest.raises(K.KpsbError) as e:
+        K.kp_build(np.ones((3, 3)), 8, K.BC_ZERO, 0.5, K.RSVD)  # RSVD needs a fixed rank
+    assert "RSVD" in str(e.value)
+    with pytest.raises(K.KpsbError):
+        K.kp_build(np.ones((40, 40)), 8, K.BC_REFLEXIVE, 2, K.EGKB)  # overhang > image

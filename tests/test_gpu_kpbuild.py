@@ -1,0 +1,146 @@
+"""kp_build (EGKB / RSVD in FP32 on the GPU) vs the FP64 oracle and the closed form.
+
+Bounds: leading sigma_k within 1e-4 * sigma_1 for the FP32 paths; well-separated leading
+factor pairs equal up to sign (|<u_gpu, u_ref>| within 1e-3 of 1).
+"""
+import numpy as np
+import pytest
+
+from oracle import kpsb_oracle as O
+from paper_2410_00233_gb300 import inputs as I
+from tests.gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _factor_vectors(K, kp):
+    Ax, Ay, sig = K.kp_get_factors(kp)
+    U = np.stack([O.vec(a) for a in Ax], axis=1).astype(np.float64)
+    V = np.stack([O.vec(a) for a in Ay], axis=1).astype(np.float64)
+    return U, sig, V
+
+
+def _check_close(sig, ref_sig, U, V, ref_U, ref_V, nvec, tol=1e-4):
+    k = len(sig)
+    np.testing.assert_allclose(sig, ref_sig[:k], rtol=0, atol=tol * ref_sig[0])
+    for i in range(nvec):
+        nxt = ref_sig[i + 1] if i + 1 < len(ref_sig) else 0.0
+        gap = min(abs(ref_sig[i] - nxt), abs(ref_sig[i - 1] - ref_sig[i]) if i else np.inf)
+        if gap < 1e-2 * ref_sig[0]:
+            continue  # nearly repeated: only the subspace is unique
+        assert abs(abs(U[:, i] @ ref_U[:, i]) - 1) < 1e-3
+        assert abs(abs(V[:, i] @ ref_V[:, i]) - 1) < 1e-3
+
+
+def test_egkb_small_config_vs_oracle_and_closed_form():
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    pr = I.problem_small(0)  # n = 32, 9x9 PSF, zero boundary, k = 5 enlarged to 10
+    n = pr.n
+    kp = K.kp_build(pr.psf, n, pr.bc, pr.k, K.EGKB, p=pr.p, start=pr.start.astype(np.float32))
+    inf = K.kp_info(kp)
+    F = O.r_factors(pr.psf, n, pr.bc)
+    ref = O.egkb(lambda v: O.r_apply(F, v), lambda u: O.r_apply_t(F, u),
+                 pr.start.astype(np.float32).astype(np.float64), pr.k, pr.p)
+    cf = O.r_sigma_closed_form(F)
+    # rank(R(A)) <= 9 < k_p = 10: both stop at the breakdown of the recurrence
+    assert inf["k"] == ref.k == 5 and inf["kp"] <= 9
+    U, sig, V = _factor_vectors(K, kp)
+    _check_close(sig, ref.sigma, U, V, ref.U, ref.V, 5)
+    np.testing.assert_allclose(sig, cf[:5], rtol=0, atol=1e-4 * cf[0])
+    # unit factors and the sign convention
+    Ax, Ay, _ = K.kp_get_factors(kp)
+    for i in range(inf["k"]):
+        assert abs(np.linalg.norm(Ax[i]) - 1) < 1e-5 and abs(np.linalg.norm(Ay[i]) - 1) < 1e-5
+        v = Ay[i].reshape(-1)
+        assert v[np.argmax(np.abs(v))] > 0
+
+
+@pytest.mark.parametrize("one_sided", [False, True])
+def test_egkb_medium_auto_rank(one_sided):
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    pr = I.problem_medium(0)  # n = 128, 31x31 mixture, reflexive, tau = 1e-3, cap 30
+    n = pr.n
+    start = pr.start.astype(np.float32)
+    kp = K.kp_build(pr.psf, n, pr.bc, pr.tau, K.EGKB, p=pr.p, start=start, one_sided=one_sided)
+    inf = K.kp_info(kp)
+    F = O.r_factors(pr.psf, n, pr.bc)
+    ref = O.egkb(lambda v: O.r_apply(F, v), lambda u: O.r_apply_t(F, u), start.astype(np.float64),
+                 pr.k, pr.p, tau=pr.tau, full_reorth=not one_sided)
+    if inf["k"] != ref.k:  # the rule may flip only where nu is flat at the deciding index
+        j = min(inf["k"], ref.k) + 1
+        nu = ref.info["nu"]
+        assert abs(nu[j] - nu[j - 1]) < 1e-4 * nu[j - 1]
+    k = min(inf["k"], ref.k)
+    U, sig, V = _factor_vectors(K, kp)
+    cf = O.r_sigma_closed_form(F)
+    np.testing.assert_allclose(sig[:k], ref.sigma[:k], rtol=0, atol=1e-4 * ref.sigma[0])
+    np.testing.assert_allclose(sig[:k], cf[:k], rtol=0, atol=1e-4 * cf[0])
+    _check_close(sig[:k], ref.sigma, U[:, :k], V[:, :k], ref.U, ref.V, min(k, 4))
+
+
+def test_rsvd_same_test_matrix_vs_oracle():
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    pr = I.problem_small(1)
+    n = pr.n
+    kp_ = 15
+    Fm = I.gaussian((n * n, kp_), I.rng(99)).astype(np.float32)
+    kp = K.kp_build(pr.psf, n, pr.bc, 5, K.RSVD, p=kp_ - 5, start=Fm)
+    Fo = O.r_factors(pr.psf, n, pr.bc)
+    ref = O.rsvd(lambda v: O.r_apply(Fo, v), lambda u: O.r_apply_t(Fo, u), Fm.astype(np.float64), 5)
+    U, sig, V = _factor_vectors(K, kp)
+    assert K.kp_info(kp)["k"] == 5
+    _check_close(sig, ref.sigma, U, V, ref.U, ref.V, 5)
+
+
+def test_rsvd_medium_vs_closed_form():
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    pr = I.problem_medium(1)
+    n = pr.n
+    kp = K.kp_build(pr.psf, n, pr.bc, 12, K.RSVD, p=10, seed=1234)
+    inf = K.kp_info(kp)
+    cf = O.r_sigma_closed_form(O.r_factors(pr.psf, n, pr.bc))
+    np.testing.assert_allclose(inf["sigma"], cf[:inf["k"]], rtol=0, atol=1e-4 * cf[0])
+
+
+def test_egkb_breakdown_small_rank():
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    n, s = 24, 5
+    psf = I.psf_random(s, I.rng(5))
+    for method in (K.EGKB, K.RSVD):
+        kp = K.kp_build(psf, n, K.BC_ZERO, 4, method, p=6, seed=7)
+        inf = K.kp_info(kp)
+        cf = O.r_sigma_closed_form(O.r_factors(psf, n, K.BC_ZERO))
+        assert inf["k"] == 4
+        if method == K.EGKB:
+            assert inf["kp"] <= s  # rank(R(A)) <= s: the recurrence stops at breakdown
+        np.testing.assert_allclose(inf["sigma"], cf[:4], rtol=0, atol=1e-4 * cf[0])
+    # separable PSF: R(A) has rank 1, so k drops to 1
+    kp = K.kp_build(I.psf_separable(7, I.rng(2)), n, K.BC_REFLEXIVE, 3, K.EGKB, seed=3)
+    assert K.kp_info(kp)["k"] == 1
+
+
+def test_large_config_sampled_sigma_vs_closed_form():
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    pr = I.problem_large(0)  # n = 512, 63x63 turbulence-like PSF, k = 20, k_p = 40
+    kp = K.kp_build(pr.psf, pr.n, pr.bc, pr.k, K.EGKB, p=pr.p, seed=11)
+    inf = K.kp_info(kp)
+    cf = O.r_sigma_closed_form(O.r_factors(pr.psf, pr.n, pr.bc))
+    assert inf["k"] == 20
+    np.testing.assert_allclose(inf["sigma"], cf[:20], rtol=0, atol=1e-4 * cf[0])
+    # factors: the exact leading pair (closed form) up to sign
+    Ucf, _, Vcf = O.r_tsvd_closed_form(O.r_factors(pr.psf, pr.n, pr.bc), 2)
+    U, sig, V = _factor_vectors(K, kp)
+    assert abs(abs(U[:, 0] @ Ucf[:, 0]) - 1) < 1e-3
+    assert abs(abs(V[:, 0] @ Vcf[:, 0]) - 1) < 1e-3
