@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the KP-sum + split Bregman deblurring hot path on GB300.
+
+One step = one batch of independent deblur requests through the whole path:
+kp_build (TSVD of R(A) by EGKB in FP32 with automatic rank, then Terms(A_k)) for every
+request, then split Bregman (isotropic TV, 100 outer steps, CGLS <= 100 inner steps) for
+all of them in one batched solve.  Workload: n = 128 images, 31 x 31 two-Gaussian
+mixture PSFs, reflexive boundary, noise 1 % and 5 % (alternating), mu = 1, lambda = 0.1,
+beta = lambda^2/2 (gamma = 2).  Seeded synthetic inputs (paper_2410_00233_gb300.inputs)
+stand in for the paper's IR Tools images and PSFs.
+
+value: deblurs/s of the mixed path (KP GEMMs in the selected precision, FP64 vectors),
+inputs resident in HBM, L2 flushed between timed steps.  e2e: the same through the
+host-pointer C ABI (PSFs and b uploaded from pinned memory, x read back, every step).
+plain: FP32 EGKB + FP64 split Bregman, one request at a time (the paper's arithmetic).
+
+--impl reference times the CPU oracle (test infrastructure) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_IMG = 128
+PSF_S = 31
+OUTER = 100
+MU, LAM = 1.0, 0.1
+WORKLOAD = ("n=128 images, 31x31 two-Gaussian-mixture PSF, reflexive boundary, EGKB(FP32) "
+            "automatic rank (tau=1e-3, cap 30), isotropic split Bregman 100 outer, noise 1%/5%")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-worker", type=float, default=0.0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm): a bounded sample in a single-threaded process
+# ---------------------------------------------------------------------------------------
+
+def cpu_worker(seconds: float) -> dict:
+    import numpy as np
+
+    from oracle import kpsb_oracle as O
+    from paper_2410_00233_gb300 import inputs as I
+
+    pr = I.problem_medium(0)
+    t0 = time.perf_counter()
+    Kop, ts = O.kp_build(pr.psf, pr.n, pr.bc, pr.k, pr.p, "egkb", tau=pr.tau, start=pr.start)
+    t_build = time.perf_counter() - t0
+    b_true = O.blur(pr.psf, pr.x_true, pr.bc)
+    b = b_true + I.noise_vector(b_true, pr.eta, pr.zeta)
+    # the first m outer steps of the real solve, m sized from a one-step probe to the budget
+    A = lambda X: O.kp_apply(Kop, X)  # noqa: E731
+    AT = lambda Y: O.kp_apply_t(Kop, Y)  # noqa: E731
+    t1 = time.perf_counter()
+    O.split_bregman(A, AT, b, MU, LAM, LAM * LAM / 2, True, 1)
+    probe = time.perf_counter() - t1
+    done = int(min(OUTER, max(1, (seconds - t_build - probe) / max(probe, 1e-3))))
+    t1 = time.perf_counter()
+    O.split_bregman(A, AT, b, MU, LAM, LAM * LAM / 2, True, done)
+    t_outer = (time.perf_counter() - t1) / done
+    total = t_build + t_outer * OUTER
+    return dict(value=1.0 / total, t_build=t_build, t_outer=t_outer, outer_timed=done, k=ts.k,
+                sample=(f"1 request (n=128): full EGKB(FP64 oracle, k={ts.k}) + the first {done} of {OUTER} "
+                        f"split Bregman outer steps (CGLS to RC<1e-4), extrapolated to the full solve"))
+
+
+def run_cpu_baseline(seconds: float) -> dict:
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(seconds)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError("cpu worker failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    d["cores"] = 1
+    return d
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        d = run_cpu_baseline(20.0)
+        if i >= args.warmup:
+            vals.append(d["value"])
+        last = d
+    v = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": "deblurs/sec + p50/p99 latency, mixed-precision vs plain path, equal ISNR",
+        "value": v, "unit": "deblurs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch": 1, "parallelism": "host, 1 thread"},
+        "cpu_baseline": {"value": v, "unit": "deblurs/s", "cores": 1, "kind": "oracle", "sample": last["sample"]},
+        "e2e": {"value": v, "unit": "deblurs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(K, I, torch, count: int, first: int, dev):
+    """Requests first..first+count-1: PSF (host), x_true, b on the device (exact blur on the
+    GPU, noise scaled on the host as in the paper's experiments)."""
+    import numpy as np
+
+    reqs = []
+    for i in range(first, first + count):
+        pr = I.problem_medium(i)
+        psf_d = torch.from_numpy(np.asfortranarray(pr.psf).reshape(-1, order="F").copy()).to(dev)
+        x_d = torch.from_numpy(pr.x_true.reshape(-1, order="F").copy()).to(dev)
+        bt_d = torch.empty_like(x_d)
+        K.kp_blur_dev(psf_d.data_ptr(), PSF_S, PSF_S, N_IMG, pr.bc, x_d.data_ptr(), bt_d.data_ptr())
+        torch.cuda.synchronize()
+        b_true = bt_d.cpu().numpy().reshape(N_IMG, N_IMG, order="F")
+        b = b_true + I.noise_vector(b_true, pr.eta, pr.zeta)
+        b_d = torch.from_numpy(b.reshape(-1, order="F").copy()).to(dev)
+        reqs.append(dict(pr=pr, b=b, b_d=b_d, x_d=torch.zeros_like(b_d)))
+    return reqs
+
+
+def run_step(K, reqs, prec):
+    """The whole hot path for one batch: kp_build for all, one batched split Bregman."""
+    probs = [dict(psf=r["pr"].psf, n=N_IMG, bc=r["pr"].bc, rank_or_tol=r["pr"].tau, method=K.EGKB,
+                  p=r["pr"].p, seed=r["pr"].seed) for r in reqs]
+    kps = K.kp_build_batched(probs)
+    jobs = [dict(kp=kp, b=r["b_d"].data_ptr(), x=r["x_d"].data_ptr(), mu=MU, lam=LAM, tv=K.ISO, iters=OUTER)
+            for kp, r in zip(kps, reqs)]
+    stats = K.sb_solve_batched(jobs, on_device=True, prec=prec)
+    return kps, stats
+
+
+def main():
+    args = parse()
+    if args.cpu_worker > 0:
+        print(json.dumps(cpu_worker(args.cpu_worker)), flush=True)
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2410_00233_gb300 import inputs as I
+    from paper_2410_00233_gb300 import kpsb as K
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if not os.path.exists(K.LIB_PATH):
+        from paper_2410_00233_gb300 import build as B
+
+        B.build()
+    K.lib()
+    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "bf16x3": K.P_BF16X3}
+    prec_name = args.prec
+    if prec_name == "auto":
+        prec_name = os.environ.get("KPSB_BENCH_PREC", "fp32")
+    prec = precs[prec_name]
+    B = args.batch
+    W, S = args.warmup, args.steps
+    # inputs of every step, distinct requests per rank and step
+    base = rank * 100000
+    steps_in = [make_inputs(K, I, torch, B, base + s * B, dev) for s in range(W + S)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    # warm-up
+    for s in range(W):
+        run_step(K, steps_in[s], prec)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    times = []
+    launches0 = K.kpsb_kernel_launches()
+    clocks = ClockSampler(local)
+    K.kpsb_gemm_timing(True)
+    ks = []
+    stats_first = None
+    for s in range(W, W + S):
+        flush.fill_(float(s))  # evict L2 between timed steps
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        kps, stats = run_step(K, steps_in[s], prec)
+        ev1.record()
+        barrier()
+        times.append(ev0.elapsed_time(ev1) / 1000.0)
+        ks.extend(K.kp_info(kp)["k"] for kp in kps)
+        if stats_first is None:
+            stats_first = stats
+        del kps
+    gl, gms, gflops = K.kpsb_gemm_stats()
+    K.kpsb_gemm_timing(False)
+    clk = clocks.stop()
+    launches = K.kpsb_kernel_launches() - launches0
+    t_rank = sum(times)
+    if dist is not None:
+        tt = torch.tensor([t_rank], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    else:
+        t_max = t_rank
+    value = world * B * S / t_max
+
+    # ISNR of the mixed path on the first timed step
+    reqs = steps_in[W]
+    isnr_mixed = []
+    for r in reqs:
+        x = r["x_d"].cpu().numpy().reshape(N_IMG, N_IMG, order="F")
+        isnr_mixed.append(20 * math.log10(np.linalg.norm(r["b"] - r["pr"].x_true) /
+                                          np.linalg.norm(x - r["pr"].x_true)))
+
+    # end to end through the host-pointer C ABI (pinned host buffers), every step
+    e2e = None
+    if rank == 0 or True:
+        n_e2e = min(S, 3)
+        pins = []
+        for s in range(W, W + n_e2e):
+            bufs = []
+            for r in steps_in[s]:
+                bp = torch.empty((N_IMG * N_IMG,), dtype=torch.float64).pin_memory()
+                bp.numpy()[:] = r["b"].reshape(-1, order="F")
+                xp = torch.empty((N_IMG * N_IMG,), dtype=torch.float64).pin_memory()
+                bufs.append((bp, xp))
+            pins.append(bufs)
+        t_e2e = 0.0
+        for j, s in enumerate(range(W, W + n_e2e)):
+            flush.fill_(float(j))
+            barrier()
+            t0 = time.perf_counter()
+            probs = [dict(psf=r["pr"].psf, n=N_IMG, bc=r["pr"].bc, rank_or_tol=r["pr"].tau, method=K.EGKB,
+                          p=r["pr"].p, seed=r["pr"].seed) for r in steps_in[s]]
+            kps = K.kp_build_batched(probs)
+            import ctypes as C
+
+            arr = (K.SBJob * B)()
+            st_arr = (K.SBStats * B)()
+            for i, (kp, (bp, xp)) in enumerate(zip(kps, pins[j])):
+                arr[i].kp = kp.ptr
+                arr[i].b, arr[i].x = bp.data_ptr(), xp.data_ptr()
+                arr[i].mu, arr[i].lambda_, arr[i].beta = MU, LAM, 0.0
+                arr[i].tv, arr[i].iters = K.ISO, OUTER
+                arr[i].stats = C.pointer(st_arr[i])
+            o = K._sb_opts(prec=prec)
+            K._check("sb_solve_batched", K.lib().sb_solve_batched(B, arr, 0, C.byref(o)))
+            t_e2e += time.perf_counter() - t0
+            del kps
+        h2d = B * (N_IMG * N_IMG * 8 + PSF_S * PSF_S * 8)
+        d2h = B * N_IMG * N_IMG * 8
+        e2e = {"value": B * n_e2e / t_e2e, "unit": "deblurs/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    out = None
+    if rank == 0:
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks = json.load(f)
+        except Exception:
+            pass
+        # plain path: FP32 EGKB + FP64 split Bregman, one request at a time
+        plain = None
+        if not args.no_plain:
+            r = steps_in[W][0]
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            xd = torch.zeros_like(r["b_d"])
+            torch.cuda.synchronize()
+            ev0.record()
+            kp = K.kp_build(r["pr"].psf, N_IMG, r["pr"].bc, r["pr"].tau, K.EGKB, p=r["pr"].p, seed=r["pr"].seed)
+            st = K.sb_solve_dev(kp, r["b_d"].data_ptr(), xd.data_ptr(), MU, LAM, K.ISO, OUTER, prec=K.P_FP64)
+            ev1.record()
+            torch.cuda.synchronize()
+            tp = ev0.elapsed_time(ev1) / 1000.0
+            x = xd.cpu().numpy().reshape(N_IMG, N_IMG, order="F")
+            isnr_plain = 20 * math.log10(np.linalg.norm(r["b"] - r["pr"].x_true) /
+                                         np.linalg.norm(x - r["pr"].x_true))
+            plain = {"value": 1.0 / tp, "unit": "deblurs/s", "latency_ms": tp * 1000.0,
+                     "isnr_db": isnr_plain, "isnr_mixed_db": isnr_mixed[0],
+                     "isnr_abs_diff_db": abs(isnr_plain - isnr_mixed[0]),
+                     "iota_total": st.iota_total, "iota_total_mixed": stats_first[0].iota_total}
+        # roofline of the dominant kernel (KP GEMM)
+        achieved = gflops / (gms / 1000.0) / 1e12 if gms > 0 else None
+        if prec in (K.P_TF32X3,):
+            peak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
+            roof = {"bound": "tensor", "peak_note": "TF32 = measured sustained bf16 x 1.1/2.25 (of measured)"}
+        elif prec == K.P_BF16X3:
+            peak = peaks.get("bf16_tflops_sustained", 1700.0)
+            roof = {"bound": "tensor", "peak_note": "measured sustained bf16 (of measured)"}
+        elif prec == K.P_FP32:
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof = {"bound": "alu", "peak_note": "FP32 FMA: 152 SM x 128 lanes x 2 x max SM clock"}
+        else:
+            peak = 152 * 2 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof = {"bound": "alu", "peak_note": "FP64 FMA: 152 SM x 2 lanes x 2 x max SM clock"}
+        roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "launches": gl, "kernel_ms": gms,
+                     "algorithmic_flops_per_launch": (gflops / gl) if gl else None})
+        cpu = None
+        if not args.no_cpu:
+            try:
+                d = run_cpu_baseline(20.0)
+                cpu = {"value": d["value"], "unit": "deblurs/s", "cores": d["cores"], "kind": "oracle",
+                       "sample": d["sample"]}
+            except Exception as e:  # reported, not fatal
+                cpu = {"value": None, "unit": "deblurs/s", "cores": 1, "kind": "oracle", "sample": str(e)[:200]}
+        lat = sorted(times)
+        out = {
+            "metric": "deblurs/sec + p50/p99 latency, mixed-precision vs plain path, equal ISNR",
+            "value": value, "unit": "deblurs/s", "n_gpus": world, "steps": S, "warmup": W,
+            "ms_per_step": 1000.0 * t_max / S, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": f"{prec_name}+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch_per_gpu": B, "global_batch": B * world,
+                       "n": N_IMG, "psf": PSF_S, "outer_iters": OUTER, "mean_k": statistics.mean(ks),
+                       "kp_gemm": prec_name, "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"dp{world} (independent requests per GPU)"},
+            "p50_ms": 1000.0 * lat[len(lat) // 2], "p99_ms": 1000.0 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "isnr_db_mean": statistics.mean(isnr_mixed),
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+            "plain": plain, "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -210,6 +210,17 @@ kpsb_status kp_ra_materialize_dev(const float* psf, int s0, int s1, int n, int b
 kpsb_status kpsb_small_svd(int m, int nc, const double* A, double* U, double* S, double* V,
                            int* sweeps);
 
+/* ---- Instrumentation ----------------------------------------------------------------- */
+/* Kernels launched by this library in this process (all entry points, all threads). */
+unsigned long long kpsb_kernel_launches(void);
+/* enable = 1: clear the totals and record a CUDA event pair, on the launching stream,
+ * around every Kronecker-sum GEMM apply (two kernel launches on the CUDA-core path, one
+ * on the tensor-core path) until called with enable = 0. */
+kpsb_status kpsb_gemm_timing(int enable);
+/* Totals of the recorded applies (waits for their events): kernel launches, summed
+ * device milliseconds, and algorithmic flops (4 k n^3 per problem per apply, Sec. 4.2). */
+kpsb_status kpsb_gemm_stats(unsigned long long* launches, double* ms, double* flops);
+
 /* Thread-local message for the last error of this thread ("" if none). */
 const char* kpsb_last_error(void);
 

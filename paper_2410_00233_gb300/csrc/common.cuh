@@ -15,6 +15,11 @@ namespace kpsb {
 // Thread-local last-error message (kpsb_last_error).
 void set_error(const char* fmt, ...);
 void clear_error();
+// Process-wide count of kernels launched by this library (kpsb_kernel_launches).
+void count_launch();
+// CUDA-event timing of the Kronecker-sum GEMM launches (kpsb_gemm_timing / _stats).
+int gemm_timer_begin(cudaStream_t st);
+void gemm_timer_end(int slot, cudaStream_t st, double flops, int launches);
 
 struct Status {
   kpsb_status code;
@@ -35,7 +40,11 @@ struct Status {
     if (_s != KPSB_OK) return _s;          \
   } while (0)
 
-#define KPSB_CHECK_LAUNCH() KPSB_TRY_CUDA(cudaGetLastError())
+#define KPSB_CHECK_LAUNCH()     \
+  do {                          \
+    ::kpsb::count_launch();     \
+    KPSB_TRY_CUDA(cudaGetLastError()); \
+  } while (0)
 
 #define KPSB_REQUIRE(cond, ...)            \
   do {                                     \

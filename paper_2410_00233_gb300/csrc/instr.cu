@@ -1,0 +1,88 @@
+// Instrumentation: process-wide kernel-launch counter and CUDA-event timing of the
+// Kronecker-sum GEMM launches (recorded on the stream each apply runs on).
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "kpsb_internal.cuh"
+
+namespace kpsb {
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+struct TimerRec {
+  cudaEvent_t a = nullptr, b = nullptr;
+  double flops = 0.0;
+  int launches = 0;
+  bool used = false;
+};
+std::mutex g_tm;
+bool g_timing = false;
+std::vector<TimerRec> g_recs;
+size_t g_next = 0;
+}  // namespace
+
+int gemm_timer_begin(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_tm);
+  if (!g_timing) return -1;
+  if (g_next == g_recs.size()) {
+    TimerRec r;
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+    g_recs.push_back(r);
+  }
+  int slot = (int)g_next++;
+  cudaEventRecord(g_recs[slot].a, st);
+  return slot;
+}
+
+void gemm_timer_end(int slot, cudaStream_t st, double flops, int launches) {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_tm);
+  if (slot >= (int)g_recs.size()) return;
+  TimerRec& r = g_recs[slot];
+  cudaEventRecord(r.b, st);
+  r.flops = flops;
+  r.launches = launches;
+  r.used = true;
+}
+
+}  // namespace kpsb
+
+using namespace kpsb;
+
+extern "C" unsigned long long kpsb_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" kpsb_status kpsb_gemm_timing(int enable) {
+  clear_error();
+  std::lock_guard<std::mutex> lk(g_tm);
+  g_timing = enable != 0;
+  if (g_timing) {
+    g_next = 0;
+    for (auto& r : g_recs) r.used = false;
+  }
+  return KPSB_OK;
+}
+
+extern "C" kpsb_status kpsb_gemm_stats(unsigned long long* launches, double* ms, double* flops) {
+  clear_error();
+  std::lock_guard<std::mutex> lk(g_tm);
+  unsigned long long L = 0;
+  double T = 0.0, F = 0.0;
+  for (size_t i = 0; i < g_next && i < g_recs.size(); ++i) {
+    TimerRec& r = g_recs[i];
+    if (!r.used) continue;
+    KPSB_TRY_CUDA(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    KPSB_TRY_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    T += t;
+    F += r.flops;
+    L += r.launches;
+  }
+  if (launches) *launches = L;
+  if (ms) *ms = T;
+  if (flops) *flops = F;
+  return KPSB_OK;
+}

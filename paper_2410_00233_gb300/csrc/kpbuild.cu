@@ -414,6 +414,7 @@ static kpsb_status build_egkb(const float* psf_host, int s0, int s1, int n, int 
     if (!s) s = la_matmul_small(w.Q, (int)N, N, nc, dV, nc, kk, h->Ay, (int)N, st);
     if (!s) {
       sign_fix_kernel<<<kk, 256, 0, st>>>(h->Ax, h->Ay, N);
+      count_launch();
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaMemcpyAsync(h->sigma_d, dSg, sizeof(double) * kk, cudaMemcpyDeviceToDevice, st);
       h->sigma.resize(kk);
@@ -505,6 +506,7 @@ static kpsb_status build_rsvd(const float* psf_host, int s0, int s1, int n, int 
     if (!s) s = la_small_svd(G, kp, kp, kp, U, lam, W, nullptr, st);
     if (s) break;
     rsvd_sigma_kernel<<<1, 256, 0, st>>>(lam, W, kp, k, 1e-12, sig, T2);
+    count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_error("rsvd: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
     // effective k: drop directions with zero singular value (rank of R(A) < k)
@@ -526,6 +528,7 @@ static kpsb_status build_rsvd(const float* psf_host, int s0, int s1, int n, int 
     if (!s) s = la_matmul_small(Ht, (int)N, N, kp, T2, kp, kk, h->Ay, (int)N, st);
     if (!s) {
       sign_fix_kernel<<<kk, 256, 0, st>>>(h->Ax, h->Ay, N);
+      count_launch();
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaMemcpyAsync(h->sigma_d, sig, sizeof(double) * kk, cudaMemcpyDeviceToDevice, st);
       h->sigma.assign(hsig.begin(), hsig.begin() + kk);

@@ -204,11 +204,15 @@ extern "C" kpsb_status kp_apply_dev(kpsb_kp_t kp, const double* X, double* Y, in
   if (e != cudaSuccess) {
     set_error("kp_apply_dev: %s", cudaGetErrorString(e));
     s = KPSB_ECUDA;
-  } else if (tc) {
-    kpsb_kp* kps[1] = {kp};
-    s = tc_apply_batch(kps, Jd, &J, 1, n, k, transpose, prec, st);
   } else {
-    s = kp_apply_batch(Jd, 1, n, k, transpose, prec, st);
+    int slot = gemm_timer_begin(st);
+    if (tc) {
+      kpsb_kp* kps[1] = {kp};
+      s = tc_apply_batch(kps, Jd, &J, 1, n, k, transpose, prec, st);
+    } else {
+      s = kp_apply_batch(Jd, 1, n, k, transpose, prec, st);
+    }
+    gemm_timer_end(slot, st, 4.0 * k * (double)n * n * n, tc ? 1 : 2);
   }
   // the descriptor copy is from host stack memory: wait for it before returning
   cudaError_t e2 = cudaStreamSynchronize(st);

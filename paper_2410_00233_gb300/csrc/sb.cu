@@ -329,13 +329,22 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
     if (e != cudaSuccess) { set_error("sb setup: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
     const int blocks = std::max(1, std::min(SB_MAX_BLOCKS, (int)((N + SB_T * 4 - 1) / (SB_T * 4))));
     dim3 gv(blocks, P);
+    double ksum = 0.0;
+    for (auto& j : jobs) ksum += j.kp->k;
+    const double apply_flops = 4.0 * ksum * (double)n * n * n;  // 4 k n^3 per problem (Sec. 4.2)
     auto kp_fwd = [&]() -> kpsb_status {
-      return tc ? tc_apply_batch(kps.data(), dfwd, fwd.data(), P, n, kmax, 0, o.prec, st)
-                : kp_apply_batch(dfwd, P, n, kmax, 0, o.prec, st);
+      int slot = gemm_timer_begin(st);
+      kpsb_status r = tc ? tc_apply_batch(kps.data(), dfwd, fwd.data(), P, n, kmax, 0, o.prec, st)
+                         : kp_apply_batch(dfwd, P, n, kmax, 0, o.prec, st);
+      gemm_timer_end(slot, st, apply_flops, 2);
+      return r;
     };
     auto kp_bwd = [&]() -> kpsb_status {
-      return tc ? tc_apply_batch(kps.data(), dbwd, bwd.data(), P, n, kmax, 1, o.prec, st)
-                : kp_apply_batch(dbwd, P, n, kmax, 1, o.prec, st);
+      int slot = gemm_timer_begin(st);
+      kpsb_status r = tc ? tc_apply_batch(kps.data(), dbwd, bwd.data(), P, n, kmax, 1, o.prec, st)
+                         : kp_apply_batch(dbwd, P, n, kmax, 1, o.prec, st);
+      gemm_timer_end(slot, st, apply_flops, 2);
+      return r;
     };
     sb_setup_kernel<<<gv, SB_T, 0, st>>>(dprobs);
     KPSB_CHECK_LAUNCH();
@@ -347,15 +356,18 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
       KPSB_CHECK_LAUNCH();
       if ((s = kp_bwd())) break;
       sb_cgls_f_kernel<<<gv, SB_T, 0, st>>>(dprobs, 1);
+      KPSB_CHECK_LAUNCH();
       sb_cgls_w_kernel<<<gv, SB_T, 0, st>>>(dprobs);
       KPSB_CHECK_LAUNCH();
       for (int it = 0; it < o.i_max; ++it) {
         if ((s = kp_fwd())) break;
         sb_cgls_zz_kernel<<<gv, SB_T, 0, st>>>(dprobs);
+        KPSB_CHECK_LAUNCH();
         sb_cgls_x_kernel<<<gv, SB_T, 0, st>>>(dprobs);
         KPSB_CHECK_LAUNCH();
         if ((s = kp_bwd())) break;
         sb_cgls_f_kernel<<<gv, SB_T, 0, st>>>(dprobs, 0);
+        KPSB_CHECK_LAUNCH();
         sb_cgls_w_kernel<<<gv, SB_T, 0, st>>>(dprobs);
         KPSB_CHECK_LAUNCH();
         if (!o.fixed_inner && (it + 1) % CHUNK == 0 && it + 1 < o.i_max) {

@@ -89,6 +89,9 @@ _SIGS = {
     "kpsb_small_svd": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "kpsb_last_error": (C.c_char_p, []),
+    "kpsb_kernel_launches": (C.c_ulonglong, []),
+    "kpsb_gemm_timing": (C.c_int, [C.c_int]),
+    "kpsb_gemm_stats": (C.c_int, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 }
 
 
@@ -327,6 +330,21 @@ def kp_ra_apply_dev(psf_ptr: int, s0: int, s1: int, n: int, bc: int, V_ptr: int,
 def kp_ra_materialize_dev(psf_ptr: int, s0: int, s1: int, n: int, bc: int, R_ptr: int, stream=0):
     _check("kp_ra_materialize_dev", lib().kp_ra_materialize_dev(
         C.c_void_p(psf_ptr), s0, s1, n, bc, C.c_void_p(R_ptr), C.c_void_p(int(stream)) if stream else None))
+
+
+def kpsb_kernel_launches() -> int:
+    return int(lib().kpsb_kernel_launches())
+
+
+def kpsb_gemm_timing(enable: bool):
+    _check("kpsb_gemm_timing", lib().kpsb_gemm_timing(int(bool(enable))))
+
+
+def kpsb_gemm_stats():
+    """(launches, milliseconds, algorithmic flops) of the recorded KP GEMM applies."""
+    L, ms, fl = C.c_ulonglong(), C.c_double(), C.c_double()
+    _check("kpsb_gemm_stats", lib().kpsb_gemm_stats(C.byref(L), C.byref(ms), C.byref(fl)))
+    return int(L.value), float(ms.value), float(fl.value)
 
 
 def kpsb_small_svd(A):
