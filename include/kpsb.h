@@ -198,6 +198,21 @@ kpsb_status kp_blur_dev(const double* psf, int s0, int s1, int n, int bc, const 
 kpsb_status kp_ra_apply_dev(const float* psf, int s0, int s1, int n, int bc, const float* V,
                             int ldv, int nb, float* U, int ldu, int transpose, void* stream);
 
+/* kp_ra_apply_dev without any device allocation, for callers that cannot allocate during a
+ * call: a real-time loop that must not pay for (or be synchronised by) cudaMalloc/cudaFree,
+ * or a program that gives all device memory to its own pool up front.  The paper has no
+ * counterpart; it is an integration convenience.  Arguments, layout and result are those of
+ * kp_ra_apply_dev.  Scratch comes from one fixed 4 MiB array in device memory that every
+ * device using the library keeps until the process exits; requests needing more
+ * (n = 1024 with more than 15 vectors, n = 512 with more than 60) fail with KPSB_EINVAL
+ * and a message.  The first call on a device looks up the array's address on that device:
+ * make that first call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents (the call clears what must start at zero), so calls that
+ * overlap on the GPU (different streams, different host threads) race: serialise them. */
+kpsb_status kp_ra_apply_noalloc_dev(const float* psf, int s0, int s1, int n, int bc,
+                                    const float* V, int ldv, int nb, float* U, int ldu,
+                                    int transpose, void* stream);
+
 /* Materialise R(A) densely from the index map (n^2 x n^2 FP32, column-major, device;
  * n <= 128).  Each entry is a sum of PSF taps in a fixed order.  Async. */
 kpsb_status kp_ra_materialize_dev(const float* psf, int s0, int s1, int n, int bc, float* R,

@@ -84,6 +84,8 @@ _SIGS = {
                               C.c_int, C.c_void_p]),
     "kp_ra_apply_dev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                   C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "kp_ra_apply_noalloc_dev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                          C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "kp_ra_materialize_dev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                         C.c_void_p]),
     "kpsb_small_svd": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -325,6 +327,14 @@ def kp_ra_apply_dev(psf_ptr: int, s0: int, s1: int, n: int, bc: int, V_ptr: int,
     _check("kp_ra_apply_dev", lib().kp_ra_apply_dev(C.c_void_p(psf_ptr), s0, s1, n, bc, C.c_void_p(V_ptr),
                                                     ldv, nb, C.c_void_p(U_ptr), ldu, int(transpose),
                                                     C.c_void_p(int(stream)) if stream else None))
+
+
+def kp_ra_apply_noalloc_dev(psf_ptr: int, s0: int, s1: int, n: int, bc: int, V_ptr: int, ldv: int,
+                            nb: int, U_ptr: int, ldu: int, transpose: int = 0, stream=0):
+    """kp_ra_apply_dev with library-owned fixed scratch (no device allocation in the call)."""
+    _check("kp_ra_apply_noalloc_dev", lib().kp_ra_apply_noalloc_dev(
+        C.c_void_p(psf_ptr), s0, s1, n, bc, C.c_void_p(V_ptr), ldv, nb, C.c_void_p(U_ptr), ldu,
+        int(transpose), C.c_void_p(int(stream)) if stream else None))
 
 
 def kp_ra_materialize_dev(psf_ptr: int, s0: int, s1: int, n: int, bc: int, R_ptr: int, stream=0):
