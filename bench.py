@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=32)
-    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "fp32", "tf32x3"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-worker", type=float, default=0.0, help=argparse.SUPPRESS)
@@ -233,7 +233,7 @@ def main():
 
         B.build()
     K.lib()
-    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "bf16x3": K.P_BF16X3}
+    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3}
     prec_name = args.prec
     if prec_name == "auto":
         prec_name = os.environ.get("KPSB_BENCH_PREC", "fp32")
@@ -369,9 +369,6 @@ def main():
         if prec in (K.P_TF32X3,):
             peak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
             roof = {"bound": "tensor", "peak_note": "TF32 = measured sustained bf16 x 1.1/2.25 (of measured)"}
-        elif prec == K.P_BF16X3:
-            peak = peaks.get("bf16_tflops_sustained", 1700.0)
-            roof = {"bound": "tensor", "peak_note": "measured sustained bf16 (of measured)"}
         elif prec == K.P_FP32:
             peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             roof = {"bound": "alu", "peak_note": "FP32 FMA: 152 SM x 128 lanes x 2 x max SM clock"}

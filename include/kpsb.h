@@ -53,9 +53,10 @@ enum { KPSB_ANISO = 0, KPSB_ISO = 1 };
  *  FP64  : FP64 FMA of the FP32 factors (exact in FP64) with FP64 images.
  *  FP32  : FP32 FMA, images rounded to FP32, FP32 accumulation.
  *  TF32X3: tensor cores (tcgen05 kind::tf32), each operand split into two TF32 parts,
- *          three products accumulated in FP32 (error ~ FP32 rounding).
- *  BF16X3: tensor cores (tcgen05 kind::f16, bf16), two bf16 parts, three products. */
-enum { KPSB_P_FP64 = 0, KPSB_P_FP32 = 1, KPSB_P_TF32X3 = 2, KPSB_P_BF16X3 = 3 };
+ *          three products accumulated in FP32 (error ~ FP32 rounding).  Used where the
+ *          tensor-core kernel tiles the image (n a multiple of 128); other sizes run the
+ *          FP32 CUDA-core GEMM. */
+enum { KPSB_P_FP64 = 0, KPSB_P_FP32 = 1, KPSB_P_TF32X3 = 2 };
 /* Shrinkage threshold of the d-subproblem argmin lambda^2||d-c||^2 + beta||d||_1
  * (Sec. 3.2-3.3): EXACT = beta/(2 lambda^2) (its exact minimiser), PAPER = beta/lambda^2
  * (the printed 1/gamma, which minimises with 2*beta). */

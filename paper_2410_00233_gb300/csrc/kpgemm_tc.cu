@@ -1,18 +1,649 @@
-// Tensor-core (tcgen05) Kronecker-sum GEMMs: placeholder until the kernels land.
+// Kronecker-sum GEMMs on the 5th-generation tensor cores (tcgen05, TMEM accumulators,
+// TMA-fed shared memory, mbarrier pipeline), split-precision TF32 ("TF32x3"): every FP32
+// operand a is split into a_hi = tf32(a) and a_lo = tf32(a - a_hi), and a*b is accumulated
+// in FP32 as a_hi b_hi + a_hi b_lo + a_lo b_hi (error ~ FP32 rounding).
+//
+// One KP apply (Sec. 4.2, eq. (4.3)) per problem, forward Y = sum_i sigma_i Ay_i X Ax_i^T:
+//   split : Xt = X^T as two TF32 planes (hi, lo), row-major.
+//   stage1: for every term i,  D1[r][c] = sum_m Xt[r][m] T1_i[c][m]    (= Z_i(r, c))
+//           T1_i[c][m] = sigma_i Ax_i(c, m)       (transpose apply: sigma_i Ax_i(m, c))
+//           epilogue writes Zt[c][i n + r] as hi/lo planes.
+//   stage2: D2[a][c] = sum_{i,r} T2[a][i n + r] Zt[c][i n + r]          (= Y(a, c))
+//           T2[a][i n + r] = Ay_i(a, r)           (transpose apply: Ay_i(r, a))
+//           epilogue writes Y column-major in FP64.
+// Both stages are "C = A B^T" with both operands K-major (rows contiguous in K), which is
+// the canonical tcgen05 operand form; the tables T1, T2 are built once per handle.
+//
+// Kernel anatomy (128 threads, one 128 x BN output tile per CTA): warp 0 allocates BN TMEM
+// columns; lane 0 of warp 0 issues TMA loads of 32-wide K slices (128-byte swizzle) into a
+// ring of shared-memory stages; lane 0 of warp 1 issues tcgen05.mma (kind::tf32, M = 128,
+// N = BN, K = 8) and releases each stage with tcgen05.commit; after the last MMA all four
+// warps read their 32 TMEM lanes with tcgen05.ld and run the epilogue.  Every wait is
+// bounded: on timeout the CTA records an error code, drains and frees TMEM, and returns.
+#include <cuda.h>
+
+#include <mutex>
+
 #include "kpsb_internal.cuh"
 
 namespace kpsb {
 
-struct TCTables {};
+// ------------------------------------------------------------------------------------------
+// Tensor maps (driver entry point fetched through the runtime, no libcuda link needed)
+// ------------------------------------------------------------------------------------------
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                       const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                       const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                       CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-bool tc_supported(int, int) { return false; }
+static PFN_encodeTiled_t encode_fn() {
+  static PFN_encodeTiled_t fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_encodeTiled_t)p;
+  });
+  return fn;
+}
 
-void tc_free(TCTables* t) { delete t; }
+// Row-major FP32 planes: dims (innermost first) {K, rows, planes[, terms]}, box {32, box_rows}.
+static kpsb_status make_map(CUtensorMap* m, const float* base, int rank, const cuuint64_t* dims,
+                            const cuuint64_t* strides_bytes, int box_rows) {
+  PFN_encodeTiled_t enc = encode_fn();
+  KPSB_REQUIRE(enc, "cuTensorMapEncodeTiled unavailable");
+  cuuint32_t box[4] = {32, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, (void*)base, dims,
+                   strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d): rank %d dims %llu x %llu", (int)r, rank,
+              (unsigned long long)dims[0], (unsigned long long)dims[1]);
+    return KPSB_ECUDA;
+  }
+  return KPSB_OK;
+}
 
-kpsb_status tc_apply_batch(kpsb_kp**, const KPJob*, const KPJob*, int, int, int, int, int,
-                           cudaStream_t) {
-  set_error("tensor-core KP GEMM not available in this build");
-  return KPSB_EINVAL;
+// ------------------------------------------------------------------------------------------
+// Device helpers: PTX wrappers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: about a second of SM clock at most.
+static constexpr long long TC_WAIT_CYCLES = 2000000000LL;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y, int z, int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B
+// apart (SBO), version 1 (sm_100 family).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// ------------------------------------------------------------------------------------------
+// Jobs
+// ------------------------------------------------------------------------------------------
+struct alignas(128) TCJob {
+  CUtensorMap m1A;   // Xt planes: {n, n, 2}
+  CUtensorMap m1B;   // T1 planes: {n, n, 2, k}
+  CUtensorMap m2A;   // T2 planes: {k n, n, 2}
+  CUtensorMap m2B;   // Zt planes: {k n, n, 2}
+  const double* X;   // input image (n x n FP64, column-major)
+  double* Y;         // output image
+  float* Xt;         // [2][n][n]
+  float* Zt;         // [2][n][ldz]
+  int n, k, ldz;
+  const int* active;
+};
+
+// Tensor-core tables of one handle: [k][2][n][n] for stage 1, [2][n][k n] for stage 2,
+// forward and transpose.
+struct TCTables {
+  float* T1f = nullptr;
+  float* T1t = nullptr;
+  float* T2f = nullptr;
+  float* T2t = nullptr;
+  int n = 0, k = 0;
+};
+
+void tc_free(TCTables* t) {
+  if (!t) return;
+  if (t->T1f) cudaFree(t->T1f);
+  delete t;
+}
+
+// Full 128-row tiles in both stages (M = 128, BN | 128, K slices of 32).
+bool tc_supported(int n, int prec) { return prec == KPSB_P_TF32X3 && n >= 128 && n % 128 == 0; }
+
+// ---- table build ---------------------------------------------------------------------------
+__global__ void tc_tables_kernel(const float* __restrict__ Ax, const float* __restrict__ Ay,
+                                 const double* __restrict__ sigma, int n, int k, float* T1f,
+                                 float* T1t, float* T2f, float* T2t) {
+  const long long nn = (long long)n * n;
+  const long long total = nn * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / nn);
+    long long rem = e % nn;
+    int row = (int)(rem / n), col = (int)(rem % n);  // row-major position (row, col)
+    const float* ax = Ax + (size_t)i * nn;
+    const float* ay = Ay + (size_t)i * nn;
+    float sg = (float)sigma[i];
+    // stage 1 tables: T1_i[c][m]
+    float f = sg * ax[row + (size_t)col * n];   // forward: sigma Ax_i(c = row, m = col)
+    float t = sg * ax[col + (size_t)row * n];   // transpose: sigma Ax_i(m = col, c = row)
+    size_t o1 = ((size_t)i * 2) * nn + (size_t)row * n + col;
+    float h = tf32_round(f);
+    T1f[o1] = h;
+    T1f[o1 + nn] = tf32_round(f - h);
+    h = tf32_round(t);
+    T1t[o1] = h;
+    T1t[o1 + nn] = tf32_round(t - h);
+    // stage 2 tables: T2[a][i n + r], a = row, r = col
+    float f2 = ay[row + (size_t)col * n];       // forward: Ay_i(a, r)
+    float t2 = ay[col + (size_t)row * n];       // transpose: Ay_i(r, a)
+    size_t plane = (size_t)n * k * n;
+    size_t o2 = (size_t)row * k * n + (size_t)i * n + col;
+    h = tf32_round(f2);
+    T2f[o2] = h;
+    T2f[o2 + plane] = tf32_round(f2 - h);
+    h = tf32_round(t2);
+    T2t[o2] = h;
+    T2t[o2 + plane] = tf32_round(t2 - h);
+  }
+}
+
+static kpsb_status tc_tables(kpsb_kp* kp, cudaStream_t st, TCTables** out) {
+  std::lock_guard<std::mutex> lk(kp->mu);
+  if (!kp->tc) {
+    const size_t per = (size_t)2 * kp->k * kp->n * kp->n;  // floats per table
+    TCTables* t = new TCTables();
+    t->n = kp->n;
+    t->k = kp->k;
+    cudaError_t e = cudaMalloc((void**)&t->T1f, sizeof(float) * per * 4);
+    if (e != cudaSuccess) {
+      delete t;
+      set_error("tensor-core tables (%zu bytes): %s", sizeof(float) * per * 4, cudaGetErrorString(e));
+      return KPSB_ENOMEM;
+    }
+    t->T1t = t->T1f + per;
+    t->T2f = t->T1t + per;
+    t->T2t = t->T2f + per;
+    long long total = (long long)kp->k * kp->n * kp->n;
+    int nb = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+    tc_tables_kernel<<<nb, 256, 0, st>>>(kp->Ax, kp->Ay, kp->sigma_d, kp->n, kp->k, t->T1f, t->T1t,
+                                         t->T2f, t->T2t);
+    count_launch();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      tc_free(t);
+      set_error("tensor-core tables: %s", cudaGetErrorString(e));
+      return KPSB_ECUDA;
+    }
+    kp->tc = t;
+  }
+  *out = kp->tc;
+  return KPSB_OK;
+}
+
+// ---- split + transpose of the input image -----------------------------------------------------
+// Xt[r][m] = X(r, m) as hi/lo TF32 planes.  grid = (tiles of 32x32, problems).
+__global__ void tc_split_kernel(const TCJob* __restrict__ jobs) {
+  const TCJob& J = jobs[blockIdx.y];
+  if (J.active && !*J.active) return;
+  const int n = J.n;
+  const int tiles = n / 32;
+  const int tr = blockIdx.x % tiles, tm = blockIdx.x / tiles;
+  if (tm >= tiles) return;
+  __shared__ float t[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    int r = tr * 32 + tx, m = tm * 32 + j;
+    t[j][tx] = (float)J.X[r + (size_t)m * n];  // coalesced along r
+  }
+  __syncthreads();
+  const size_t nn = (size_t)n * n;
+  for (int j = ty; j < 32; j += 8) {
+    int r = tr * 32 + j, m = tm * 32 + tx;
+    float v = t[tx][j];
+    float h = tf32_round(v);
+    J.Xt[(size_t)r * n + m] = h;  // coalesced along m
+    J.Xt[nn + (size_t)r * n + m] = tf32_round(v - h);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// The GEMM kernel
+// ------------------------------------------------------------------------------------------
+__device__ int g_tc_error = 0;  // set on a timed-out wait (read by the host after a solve)
+
+template <int BN, int STAGES, int STAGE>
+struct TCCfg {
+  static constexpr int A_BYTES = 128 * 128;  // 128 rows x 32 fp32
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // hi + lo planes
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+template <int BN, int STAGES, int STAGE>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict__ jobs, int tiles_m) {
+  using C = TCCfg<BN, STAGES, STAGE>;
+  const TCJob& J = jobs[blockIdx.z];
+  const int term = STAGE == 1 ? (int)blockIdx.y : 0;
+  if (term >= J.k) return;
+  if (J.active && !*J.active) return;
+  const int n = J.n;
+  const int m0 = (blockIdx.x % tiles_m) * 128;
+  const int c0 = (blockIdx.x / tiles_m) * BN;
+  if (m0 >= n || c0 >= n) return;
+  const int KT = STAGE == 1 ? n : J.k * n;  // K extent
+  const int nkb = KT / 32;
+
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    // the tensor maps live in global memory (written before the launch): acquire them for
+    // the tensor-map proxy before the first copy
+    const CUtensorMap* mA = STAGE == 1 ? &J.m1A : &J.m2A;
+    const CUtensorMap* mB = STAGE == 1 ? &J.m1B : &J.m2B;
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)mA) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)mB) : "memory");
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, round = kb / STAGES;
+      if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      unsigned char* st = smem + s * C::STAGE_BYTES;
+      mbar_expect_tx(&full[s], C::STAGE_BYTES);
+      const int kx = kb * 32;
+      if (STAGE == 1) {
+        tma_load_3d(st, &J.m1A, &full[s], kx, m0, 0);
+        tma_load_3d(st + C::A_BYTES, &J.m1A, &full[s], kx, m0, 1);
+        tma_load_4d(st + 2 * C::A_BYTES, &J.m1B, &full[s], kx, c0, 0, term);
+        tma_load_4d(st + 2 * C::A_BYTES + C::B_BYTES, &J.m1B, &full[s], kx, c0, 1, term);
+      } else {
+        tma_load_3d(st, &J.m2A, &full[s], kx, m0, 0);
+        tma_load_3d(st + C::A_BYTES, &J.m2A, &full[s], kx, m0, 1);
+        tma_load_3d(st + 2 * C::A_BYTES, &J.m2B, &full[s], kx, c0, 0);
+        tma_load_3d(st + 2 * C::A_BYTES + C::B_BYTES, &J.m2B, &full[s], kx, c0, 1);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    constexpr uint32_t idesc = idesc_tf32(128, BN);
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, round = kb / STAGES;
+      if (!mbar_wait(&full[s], round & 1)) {
+        s_fail = 1;
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES);
+      const uint32_t a_hi = sa, a_lo = sa + C::A_BYTES;
+      const uint32_t b_hi = sa + 2 * C::A_BYTES, b_lo = b_hi + C::B_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {  // four K = 8 slices of 32 bytes in the 128-byte row
+        const uint32_t off = kk * 32;
+        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+        mma_tf32(tmem, sdesc_sw128(a_lo + off), sdesc_sw128(b_hi + off), idesc, acc0);
+        mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_lo + off), idesc, 1u);
+        mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), idesc, 1u);
+      }
+      mma_commit(&empty[s]);  // stage s free once these MMAs have read it
+    }
+    if (ok) mma_commit(done);
+  }
+  __syncwarp();
+  // ---- epilogue: all four warps ----
+  bool ok = true;
+  if (lane == 0) ok = mbar_wait(done, 0) && !s_fail;
+  ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;  // TMEM lane = output row
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int cc = 0; cc < BN; cc += 16) {
+      float v[16];
+      tmem_ld16(tbase + cc, v);
+      if (row < n) {
+        if (STAGE == 1) {
+          // D1[r][c] = Z_term(r, c) -> Zt[c][term n + r], hi/lo planes
+          const size_t plane = (size_t)n * J.ldz;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = c0 + cc + j;
+            if (c < n) {
+              float h = tf32_round(v[j]);
+              size_t o = (size_t)c * J.ldz + (size_t)term * n + row;
+              J.Zt[o] = h;
+              J.Zt[plane + o] = tf32_round(v[j] - h);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = c0 + cc + j;
+            if (c < n) J.Y[row + (size_t)c * n] = (double)v[j];
+          }
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicExch(&g_tc_error, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (!ok && threadIdx.x == 0) {
+    // drain: wait (bounded) for copies that may still be in flight into shared memory
+    for (int s = 0; s < STAGES; ++s) mbar_wait(&full[s], 0);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Host side: plans (one per batched solve: tensor maps built once) and launches
+// ------------------------------------------------------------------------------------------
+struct TCPlan {
+  TCJob* d_fwd = nullptr;
+  TCJob* d_bwd = nullptr;
+  float* work = nullptr;  // Xt and Zt of every problem
+  int njobs = 0, n = 0, kmax = 0;
+};
+
+static constexpr int S1_BN = 128, S1_STAGES = 3;
+static constexpr int S2_BN = 64, S2_STAGES = 4;
+
+static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int transpose, float* Xt,
+                            float* Zt) {
+  const int n = src.n, k = src.k;
+  J.X = src.X;
+  J.Y = src.Y;
+  J.Xt = Xt;
+  J.Zt = Zt;
+  J.n = n;
+  J.k = k;
+  J.ldz = k * n;
+  J.active = src.active;
+  const cuuint64_t fb = sizeof(float);
+  {  // Xt: {n, n, 2}
+    cuuint64_t d[3] = {(cuuint64_t)n, (cuuint64_t)n, 2};
+    cuuint64_t s[2] = {fb * n, fb * n * n};
+    KPSB_TRY(make_map(&J.m1A, Xt, 3, d, s, 128));
+  }
+  {  // T1: {n, n, 2, k}
+    cuuint64_t d[4] = {(cuuint64_t)n, (cuuint64_t)n, 2, (cuuint64_t)k};
+    cuuint64_t s[3] = {fb * n, fb * n * n, fb * 2 * n * n};
+    KPSB_TRY(make_map(&J.m1B, transpose ? T->T1t : T->T1f, 4, d, s, S1_BN));
+  }
+  {  // T2: {k n, n, 2}
+    cuuint64_t d[3] = {(cuuint64_t)k * n, (cuuint64_t)n, 2};
+    cuuint64_t s[2] = {fb * k * n, fb * (cuuint64_t)k * n * n};
+    KPSB_TRY(make_map(&J.m2A, transpose ? T->T2t : T->T2f, 3, d, s, 128));
+  }
+  {  // Zt: {k n, n, 2}
+    cuuint64_t d[3] = {(cuuint64_t)k * n, (cuuint64_t)n, 2};
+    cuuint64_t s[2] = {fb * k * n, fb * (cuuint64_t)k * n * n};
+    KPSB_TRY(make_map(&J.m2B, Zt, 3, d, s, S2_BN));
+  }
+  return KPSB_OK;
+}
+
+kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h, int njobs, int n,
+                           cudaStream_t st, TCPlan** out) {
+  KPSB_REQUIRE(tc_supported(n, KPSB_P_TF32X3), "tensor-core path needs n %% 128 == 0 (n = %d)", n);
+  TCPlan* P = new TCPlan();
+  P->njobs = njobs;
+  P->n = n;
+  std::vector<TCTables*> tabs(njobs);
+  size_t floats = 0;
+  for (int p = 0; p < njobs; ++p) {
+    kpsb_status s = tc_tables(kps[p], st, &tabs[p]);
+    if (s) {
+      delete P;
+      return s;
+    }
+    P->kmax = std::max(P->kmax, kps[p]->k);
+    floats += (size_t)2 * n * n + (size_t)2 * n * kps[p]->k * n;
+  }
+  cudaError_t e = cudaMallocAsync((void**)&P->work, sizeof(float) * floats + 2 * sizeof(TCJob) * njobs + 256, st);
+  if (e != cudaSuccess) {
+    delete P;
+    set_error("tensor-core workspace: %s", cudaGetErrorString(e));
+    return KPSB_ENOMEM;
+  }
+  std::vector<TCJob> hf(njobs), hb(njobs);
+  float* q = P->work;
+  for (int p = 0; p < njobs; ++p) {
+    float* Xt = q;
+    q += (size_t)2 * n * n;
+    float* Zt = q;
+    q += (size_t)2 * n * kps[p]->k * n;
+    kpsb_status s = fill_job(hf[p], fwd_h[p], tabs[p], 0, Xt, Zt);
+    if (!s) s = fill_job(hb[p], bwd_h[p], tabs[p], 1, Xt, Zt);
+    if (s) {
+      cudaFreeAsync(P->work, st);
+      delete P;
+      return s;
+    }
+  }
+  char* jb = (char*)(((uintptr_t)q + 255) & ~(uintptr_t)255);
+  P->d_fwd = (TCJob*)jb;
+  P->d_bwd = P->d_fwd + njobs;
+  e = cudaMemcpyAsync(P->d_fwd, hf.data(), sizeof(TCJob) * njobs, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(P->d_bwd, hb.data(), sizeof(TCJob) * njobs, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host job arrays go out of scope
+  if (e != cudaSuccess) {
+    cudaFreeAsync(P->work, st);
+    delete P;
+    set_error("tensor-core plan upload: %s", cudaGetErrorString(e));
+    return KPSB_ECUDA;
+  }
+  *out = P;
+  return KPSB_OK;
+}
+
+void tc_plan_free(TCPlan* P, cudaStream_t st) {
+  if (!P) return;
+  if (P->work) cudaFreeAsync(P->work, st);
+  delete P;
+}
+
+template <int BN, int STAGES, int STAGE>
+static kpsb_status launch_gemm(const TCJob* jobs, int njobs, int n, int kmax, cudaStream_t st) {
+  using C = TCCfg<BN, STAGES, STAGE>;
+  static bool attr_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_done[dev]) {
+    KPSB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, STAGE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    attr_done[dev] = true;
+  }
+  const int tiles_m = (n + 127) / 128, tiles_n = (n + BN - 1) / BN;
+  dim3 grid(tiles_m * tiles_n, STAGE == 1 ? kmax : 1, njobs);
+  tc_gemm_kernel<BN, STAGES, STAGE><<<grid, 128, C::SMEM, st>>>(jobs, tiles_m);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
+  const TCJob* jobs = transpose ? P->d_bwd : P->d_fwd;
+  const int n = P->n;
+  dim3 gs((n / 32) * (n / 32), P->njobs);
+  tc_split_kernel<<<gs, 256, 0, st>>>(jobs);
+  KPSB_CHECK_LAUNCH();
+  KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1>(jobs, P->njobs, n, P->kmax, st)));
+  KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2>(jobs, P->njobs, n, P->kmax, st)));
+  return KPSB_OK;
+}
+
+kpsb_status tc_check_error() {
+  int h = 0;
+  KPSB_TRY_CUDA(cudaMemcpyFromSymbol(&h, g_tc_error, sizeof(int)));
+  if (h) {
+    int z = 0;
+    cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int));
+    set_error("tensor-core GEMM: a pipeline wait timed out");
+    return KPSB_ETIMEOUT;
+  }
+  return KPSB_OK;
+}
+
+// Single apply through a temporary plan (kp_apply_dev).
+kpsb_status tc_apply_batch(kpsb_kp** kps, const KPJob* jobs_d, const KPJob* jobs_h, int njobs, int n,
+                           int kmax, int transpose, int prec, cudaStream_t st) {
+  (void)jobs_d;
+  (void)kmax;
+  KPSB_REQUIRE(prec == KPSB_P_TF32X3, "precision %d has no tensor-core kernel in this build", prec);
+  TCPlan* P = nullptr;
+  KPSB_TRY(tc_plan_create(kps, jobs_h, jobs_h, njobs, n, st, &P));
+  kpsb_status s = tc_plan_apply(P, transpose, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  tc_plan_free(P, st);
+  if (s == KPSB_OK && e != cudaSuccess) {
+    set_error("tensor-core apply: %s", cudaGetErrorString(e));
+    s = KPSB_ECUDA;
+  }
+  if (s == KPSB_OK) s = tc_check_error();
+  return s;
 }
 
 }  // namespace kpsb

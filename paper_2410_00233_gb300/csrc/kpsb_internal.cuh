@@ -95,10 +95,17 @@ kpsb_status kp_apply_batch(const KPJob* jobs_d, int njobs, int n, int kmax, int 
                            int prec, cudaStream_t st);
 size_t kp_z_bytes(int n, int k, int prec);
 
-// Tensor-core path (kpgemm_tc.cu).
-kpsb_status tc_apply_batch(kpsb_kp** kps, const KPJob* jobs_d, const KPJob* jobs_h, int njobs,
-                           int n, int kmax, int transpose, int prec, cudaStream_t st);
+// Tensor-core path (kpgemm_tc.cu).  A plan holds the tensor maps and workspaces of one
+// batch (forward and transpose jobs); applies reuse it.
+struct TCPlan;
 bool tc_supported(int n, int prec);
 void tc_free(TCTables* t);
+kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h, int njobs, int n,
+                           cudaStream_t st, TCPlan** out);
+kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st);
+void tc_plan_free(TCPlan* P, cudaStream_t st);
+kpsb_status tc_check_error();
+kpsb_status tc_apply_batch(kpsb_kp** kps, const KPJob* jobs_d, const KPJob* jobs_h, int njobs,
+                           int n, int kmax, int transpose, int prec, cudaStream_t st);
 
 }  // namespace kpsb

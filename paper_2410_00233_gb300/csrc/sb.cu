@@ -265,8 +265,10 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
   const size_t N = (size_t)n * n;
   int kmax = 0;
   for (auto& j : jobs) kmax = std::max(kmax, j.kp->k);
-  const bool tc = o.prec == KPSB_P_TF32X3 || o.prec == KPSB_P_BF16X3;
-  const size_t zbytes = tc ? 0 : a256(kp_z_bytes(n, kmax, o.prec));
+  // tensor-core GEMMs where the kernel tiles the size; other sizes use FP32 CUDA cores
+  const bool tc = tc_supported(n, o.prec);
+  const int gemm_prec = tc ? o.prec : (o.prec == KPSB_P_FP64 ? KPSB_P_FP64 : KPSB_P_FP32);
+  const size_t zbytes = tc ? 0 : a256(kp_z_bytes(n, kmax, gemm_prec));
   const size_t per = a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
                      a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256;
   const size_t total = per * P + a256(sizeof(SBProb) * P) + 2 * a256(sizeof(KPJob) * P);
@@ -319,6 +321,7 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
   kpsb_status s = KPSB_OK;
   cudaError_t e = cudaSuccess;
   SBScal* hsc = nullptr;
+  TCPlan* plan = nullptr;
   do {
     for (int p = 0; p < P && e == cudaSuccess; ++p)
       e = cudaMemsetAsync(hp[p].counter, 0, sizeof(unsigned int), st);
@@ -332,18 +335,18 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
     double ksum = 0.0;
     for (auto& j : jobs) ksum += j.kp->k;
     const double apply_flops = 4.0 * ksum * (double)n * n * n;  // 4 k n^3 per problem (Sec. 4.2)
+    if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, st, &plan))) break;
+    const int apply_launches = tc ? 3 : 2;
     auto kp_fwd = [&]() -> kpsb_status {
       int slot = gemm_timer_begin(st);
-      kpsb_status r = tc ? tc_apply_batch(kps.data(), dfwd, fwd.data(), P, n, kmax, 0, o.prec, st)
-                         : kp_apply_batch(dfwd, P, n, kmax, 0, o.prec, st);
-      gemm_timer_end(slot, st, apply_flops, 2);
+      kpsb_status r = tc ? tc_plan_apply(plan, 0, st) : kp_apply_batch(dfwd, P, n, kmax, 0, gemm_prec, st);
+      gemm_timer_end(slot, st, apply_flops, apply_launches);
       return r;
     };
     auto kp_bwd = [&]() -> kpsb_status {
       int slot = gemm_timer_begin(st);
-      kpsb_status r = tc ? tc_apply_batch(kps.data(), dbwd, bwd.data(), P, n, kmax, 1, o.prec, st)
-                         : kp_apply_batch(dbwd, P, n, kmax, 1, o.prec, st);
-      gemm_timer_end(slot, st, apply_flops, 2);
+      kpsb_status r = tc ? tc_plan_apply(plan, 1, st) : kp_apply_batch(dbwd, P, n, kmax, 1, gemm_prec, st);
+      gemm_timer_end(slot, st, apply_flops, apply_launches);
       return r;
     };
     sb_setup_kernel<<<gv, SB_T, 0, st>>>(dprobs);
@@ -399,6 +402,7 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
       e = cudaMemcpyAsync(hsc + p, hp[p].sc, sizeof(SBScal), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { set_error("sb finish: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+    if (tc && (s = tc_check_error())) break;
     stats_out.resize(P);
     for (int p = 0; p < P; ++p) {
       stats_out[p].l_end = hsc[p].l_end;
@@ -408,6 +412,7 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
     }
   } while (0);
   if (hsc) cudaFreeHost(hsc);
+  if (plan) tc_plan_free(plan, st);
   cudaFreeAsync(base, st);
   return s;
 }
@@ -417,7 +422,7 @@ static kpsb_status sb_defaults(const kpsb_sb_opts* opts, kpsb_sb_opts& o) {
   if (opts) o = *opts;
   if (o.tau_cgls <= 0.0) o.tau_cgls = 1e-4;
   if (o.i_max <= 0) o.i_max = 100;
-  KPSB_REQUIRE(o.prec >= KPSB_P_FP64 && o.prec <= KPSB_P_BF16X3, "unknown precision %d", o.prec);
+  KPSB_REQUIRE(o.prec >= KPSB_P_FP64 && o.prec <= KPSB_P_TF32X3, "unknown precision %d", o.prec);
   KPSB_REQUIRE(o.threshold_rule == KPSB_THR_EXACT || o.threshold_rule == KPSB_THR_PAPER,
                "unknown threshold rule %d", o.threshold_rule);
   return KPSB_OK;

@@ -154,3 +154,43 @@ def test_fp32_gemm_path_isnr_within_0p1_db():
     x32, _ = K.sb_solve(kp, b, 1.0, 0.1, K.ISO, 20, prec=K.P_FP32)
     assert abs(O.isnr(x32, b, x_true) - O.isnr(x64, b, x_true)) < 0.1
     assert abs(O.rel_error(x32, x_true) - O.rel_error(x64, x_true)) < 1e-3
+
+
+@pytest.mark.parametrize("n,k", [(128, 5), (256, 12), (128, 1), (384, 3)])
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_kp_apply_tensor_core_tf32x3(n, k, transpose):
+    """tcgen05 TF32x3 KP GEMM vs the FP64 oracle.  The split removes the TF32 input
+    rounding; what remains is the tensor-core accumulation, which is not IEEE FP32 and
+    grows with K (measured 2.8e-5 relative at K = 12 * 256): bound 1e-4."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    Ax, Ay, sig = _rand_factors(n, k, 3 * n + k)
+    kp = K.kp_from_factors(Ax, Ay, sig)
+    X = I.rng(6).standard_normal((n, n))
+    Kop = _oracle_op(Ax, Ay, sig)
+    ref = O.kp_apply_t(Kop, X) if transpose else O.kp_apply(Kop, X)
+    y = K.kp_apply(kp, X, transpose, K.P_TF32X3)
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert err < 1e-4, err
+    # element-wise too (no tile garbage anywhere)
+    assert np.abs(y - ref).max() <= 5e-4 * np.abs(ref).max()
+
+
+def test_tensor_core_sb_isnr_within_0p1_db():
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    pr = I.problem_medium(0)
+    n = pr.n
+    b_true = O.blur(pr.psf, pr.x_true, pr.bc)
+    b = b_true + I.noise_vector(b_true, pr.eta, pr.zeta)
+    kp = K.kp_build(pr.psf, n, pr.bc, pr.tau, K.EGKB, p=pr.p, start=pr.start.astype(np.float32))
+    x64, s64 = K.sb_solve(kp, b, 1.0, 0.1, K.ISO, 15, prec=K.P_FP64)
+    xtc, stc = K.sb_solve(kp, b, 1.0, 0.1, K.ISO, 15, prec=K.P_TF32X3)
+    d = abs(O.isnr(xtc, b, pr.x_true) - O.isnr(x64, b, pr.x_true))
+    assert d < 0.1, d
+    assert abs(O.rel_error(xtc, pr.x_true) - O.rel_error(x64, pr.x_true)) < 1e-3
+    # the batched tensor-core solve equals the single one
+    outs, st = K.sb_solve_batched([dict(kp=kp, b=b, mu=1.0, lam=0.1, tv=K.ISO, iters=15)] * 2, prec=K.P_TF32X3)
+    assert np.array_equal(outs[0], xtc) and np.array_equal(outs[1], xtc)
