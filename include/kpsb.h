@@ -53,10 +53,14 @@ enum { KPSB_ANISO = 0, KPSB_ISO = 1 };
  *  FP64  : FP64 FMA of the FP32 factors (exact in FP64) with FP64 images.
  *  FP32  : FP32 FMA, images rounded to FP32, FP32 accumulation.
  *  TF32X3: tensor cores (tcgen05 kind::tf32), each operand split into two TF32 parts,
- *          three products accumulated in FP32 (error ~ FP32 rounding).  Used where the
- *          tensor-core kernel tiles the image (n a multiple of 128); other sizes run the
- *          FP32 CUDA-core GEMM. */
-enum { KPSB_P_FP64 = 0, KPSB_P_FP32 = 1, KPSB_P_TF32X3 = 2 };
+ *          three products accumulated in FP32.
+ *  TF32X2: tensor cores; the factors are used rounded once to TF32 (the same rounded
+ *          operator in the forward and transpose applies, so the adjoint stays exact; the
+ *          change of A_k is ~5e-4 relative, far below the KP truncation error) and the
+ *          image is split into two TF32 parts: two products, half the factor traffic.
+ *  The tensor-core modes run where the kernel tiles the image (n a multiple of 128);
+ *  other sizes run the FP32 CUDA-core GEMM. */
+enum { KPSB_P_FP64 = 0, KPSB_P_FP32 = 1, KPSB_P_TF32X3 = 2, KPSB_P_TF32X2 = 3 };
 /* Shrinkage threshold of the d-subproblem argmin lambda^2||d-c||^2 + beta||d||_1
  * (Sec. 3.2-3.3): EXACT = beta/(2 lambda^2) (its exact minimiser), PAPER = beta/lambda^2
  * (the printed 1/gamma, which minimises with 2*beta). */

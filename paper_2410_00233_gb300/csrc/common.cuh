@@ -15,8 +15,12 @@ namespace kpsb {
 // Thread-local last-error message (kpsb_last_error).
 void set_error(const char* fmt, ...);
 void clear_error();
-// Process-wide count of kernels launched by this library (kpsb_kernel_launches).
-void count_launch();
+// Process-wide count of kernels launched by this library (kpsb_kernel_launches).  While
+// this thread captures a CUDA graph, launches are not counted at capture time; the graph's
+// owner counts the kernels that actually ran.
+void count_launch(long long n = 1);
+void set_capture_mode(bool on);
+bool gemm_timing_enabled();
 // CUDA-event timing of the Kronecker-sum GEMM launches (kpsb_gemm_timing / _stats).
 int gemm_timer_begin(cudaStream_t st);
 void gemm_timer_end(int slot, cudaStream_t st, double flops, int launches);

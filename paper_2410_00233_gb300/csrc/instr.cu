@@ -9,8 +9,14 @@
 namespace kpsb {
 
 static std::atomic<unsigned long long> g_launches{0};
+static thread_local bool t_capturing = false;
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch(long long n) {
+  if (t_capturing && n == 1) return;
+  g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+}
+
+void set_capture_mode(bool on) { t_capturing = on; }
 
 namespace {
 struct TimerRec {
@@ -24,6 +30,11 @@ bool g_timing = false;
 std::vector<TimerRec> g_recs;
 size_t g_next = 0;
 }  // namespace
+
+bool gemm_timing_enabled() {
+  std::lock_guard<std::mutex> lk(g_tm);
+  return g_timing;
+}
 
 int gemm_timer_begin(cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_tm);

@@ -211,7 +211,9 @@ void tc_free(TCTables* t) {
 }
 
 // Full 128-row tiles in both stages (M = 128, BN | 128, K slices of 32).
-bool tc_supported(int n, int prec) { return prec == KPSB_P_TF32X3 && n >= 128 && n % 128 == 0; }
+bool tc_supported(int n, int prec) {
+  return (prec == KPSB_P_TF32X3 || prec == KPSB_P_TF32X2) && n >= 128 && n % 128 == 0;
+}
 
 // ---- table build ---------------------------------------------------------------------------
 __global__ void tc_tables_kernel(const float* __restrict__ Ax, const float* __restrict__ Ay,
@@ -316,18 +318,22 @@ __global__ void tc_split_kernel(const TCJob* __restrict__ jobs) {
 // ------------------------------------------------------------------------------------------
 __device__ int g_tc_error = 0;  // set on a timed-out wait (read by the host after a solve)
 
-template <int BN, int STAGES, int STAGE>
+// FPL = planes of the factor operand (2: split factors, three products per K slice;
+// 1: factors rounded once to TF32, two products).  The iterate operand always has two.
+template <int BN, int STAGES, int STAGE, int FPL>
 struct TCCfg {
   static constexpr int A_BYTES = 128 * 128;  // 128 rows x 32 fp32
   static constexpr int B_BYTES = BN * 128;
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // hi + lo planes
+  static constexpr int A_PLANES = STAGE == 1 ? 2 : FPL;  // stage 1: A = iterate, stage 2: A = factors
+  static constexpr int B_PLANES = STAGE == 1 ? FPL : 2;
+  static constexpr int STAGE_BYTES = A_PLANES * A_BYTES + B_PLANES * B_BYTES;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
   static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
 };
 
-template <int BN, int STAGES, int STAGE>
+template <int BN, int STAGES, int STAGE, int FPL>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict__ jobs, int tiles_m) {
-  using C = TCCfg<BN, STAGES, STAGE>;
+  using C = TCCfg<BN, STAGES, STAGE, FPL>;
   const TCJob& J = jobs[blockIdx.z];
   const int term = STAGE == 1 ? (int)blockIdx.y : 0;
   if (term >= J.k) return;
@@ -386,16 +392,17 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
       unsigned char* st = smem + s * C::STAGE_BYTES;
       mbar_expect_tx(&full[s], C::STAGE_BYTES);
       const int kx = kb * 32;
+      unsigned char* sb = st + C::A_PLANES * C::A_BYTES;
       if (STAGE == 1) {
         tma_load_3d(st, &J.m1A, &full[s], kx, m0, 0);
         tma_load_3d(st + C::A_BYTES, &J.m1A, &full[s], kx, m0, 1);
-        tma_load_4d(st + 2 * C::A_BYTES, &J.m1B, &full[s], kx, c0, 0, term);
-        tma_load_4d(st + 2 * C::A_BYTES + C::B_BYTES, &J.m1B, &full[s], kx, c0, 1, term);
+        for (int pl = 0; pl < C::B_PLANES; ++pl)
+          tma_load_4d(sb + pl * C::B_BYTES, &J.m1B, &full[s], kx, c0, pl, term);
       } else {
-        tma_load_3d(st, &J.m2A, &full[s], kx, m0, 0);
-        tma_load_3d(st + C::A_BYTES, &J.m2A, &full[s], kx, m0, 1);
-        tma_load_3d(st + 2 * C::A_BYTES, &J.m2B, &full[s], kx, c0, 0);
-        tma_load_3d(st + 2 * C::A_BYTES + C::B_BYTES, &J.m2B, &full[s], kx, c0, 1);
+        for (int pl = 0; pl < C::A_PLANES; ++pl)
+          tma_load_3d(st + pl * C::A_BYTES, &J.m2A, &full[s], kx, m0, pl);
+        tma_load_3d(sb, &J.m2B, &full[s], kx, c0, 0);
+        tma_load_3d(sb + C::B_BYTES, &J.m2B, &full[s], kx, c0, 1);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -411,14 +418,18 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES);
-      const uint32_t a_hi = sa, a_lo = sa + C::A_BYTES;
-      const uint32_t b_hi = sa + 2 * C::A_BYTES, b_lo = b_hi + C::B_BYTES;
+      const uint32_t a_hi = sa, a_lo = sa + (C::A_PLANES == 2 ? C::A_BYTES : 0);
+      const uint32_t b_hi = sa + C::A_PLANES * C::A_BYTES;
+      const uint32_t b_lo = b_hi + (C::B_PLANES == 2 ? C::B_BYTES : 0);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {  // four K = 8 slices of 32 bytes in the 128-byte row
         const uint32_t off = kk * 32;
         const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-        mma_tf32(tmem, sdesc_sw128(a_lo + off), sdesc_sw128(b_hi + off), idesc, acc0);
-        mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_lo + off), idesc, 1u);
+        // small cross terms first, the hi x hi product last
+        if (C::A_PLANES == 2) mma_tf32(tmem, sdesc_sw128(a_lo + off), sdesc_sw128(b_hi + off), idesc, acc0);
+        if (C::B_PLANES == 2)
+          mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_lo + off), idesc,
+                   C::A_PLANES == 2 ? 1u : acc0);
         mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), idesc, 1u);
       }
       mma_commit(&empty[s]);  // stage s free once these MMAs have read it
@@ -486,10 +497,19 @@ struct TCPlan {
   TCJob* d_bwd = nullptr;
   float* work = nullptr;  // Xt and Zt of every problem
   int njobs = 0, n = 0, kmax = 0;
+  int prec = KPSB_P_TF32X3;
 };
 
 static constexpr int S1_BN = 128, S1_STAGES = 3;
 static constexpr int S2_BN = 64, S2_STAGES = 4;
+
+template <int BN, int STAGES, int STAGE, int FPL>
+static kpsb_status prepare_gemm() {
+  using C = TCCfg<BN, STAGES, STAGE, FPL>;
+  KPSB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, STAGE, FPL>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  return KPSB_OK;
+}
 
 static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int transpose, float* Xt,
                             float* Zt) {
@@ -527,11 +547,17 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
 }
 
 kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h, int njobs, int n,
-                           cudaStream_t st, TCPlan** out) {
-  KPSB_REQUIRE(tc_supported(n, KPSB_P_TF32X3), "tensor-core path needs n %% 128 == 0 (n = %d)", n);
+                           int prec, cudaStream_t st, TCPlan** out) {
+  KPSB_REQUIRE(tc_supported(n, prec), "tensor-core path needs n %% 128 == 0 (n = %d)", n);
+  // kernel attributes are set here, before any graph capture that replays the applies
+  KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 2>()));
+  KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 2>()));
+  KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 1>()));
+  KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 1>()));
   TCPlan* P = new TCPlan();
   P->njobs = njobs;
   P->n = n;
+  P->prec = prec;
   std::vector<TCTables*> tabs(njobs);
   size_t floats = 0;
   for (int p = 0; p < njobs; ++p) {
@@ -586,20 +612,12 @@ void tc_plan_free(TCPlan* P, cudaStream_t st) {
   delete P;
 }
 
-template <int BN, int STAGES, int STAGE>
+template <int BN, int STAGES, int STAGE, int FPL>
 static kpsb_status launch_gemm(const TCJob* jobs, int njobs, int n, int kmax, cudaStream_t st) {
-  using C = TCCfg<BN, STAGES, STAGE>;
-  static bool attr_done[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !attr_done[dev]) {
-    KPSB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, STAGE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    attr_done[dev] = true;
-  }
+  using C = TCCfg<BN, STAGES, STAGE, FPL>;
   const int tiles_m = (n + 127) / 128, tiles_n = (n + BN - 1) / BN;
   dim3 grid(tiles_m * tiles_n, STAGE == 1 ? kmax : 1, njobs);
-  tc_gemm_kernel<BN, STAGES, STAGE><<<grid, 128, C::SMEM, st>>>(jobs, tiles_m);
+  tc_gemm_kernel<BN, STAGES, STAGE, FPL><<<grid, 128, C::SMEM, st>>>(jobs, tiles_m);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
 }
@@ -610,8 +628,13 @@ kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
   dim3 gs((n / 32) * (n / 32), P->njobs);
   tc_split_kernel<<<gs, 256, 0, st>>>(jobs);
   KPSB_CHECK_LAUNCH();
-  KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1>(jobs, P->njobs, n, P->kmax, st)));
-  KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2>(jobs, P->njobs, n, P->kmax, st)));
+  if (P->prec == KPSB_P_TF32X3) {
+    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 2>(jobs, P->njobs, n, P->kmax, st)));
+    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 2>(jobs, P->njobs, n, P->kmax, st)));
+  } else {
+    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 1>(jobs, P->njobs, n, P->kmax, st)));
+    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 1>(jobs, P->njobs, n, P->kmax, st)));
+  }
   return KPSB_OK;
 }
 
@@ -632,9 +655,10 @@ kpsb_status tc_apply_batch(kpsb_kp** kps, const KPJob* jobs_d, const KPJob* jobs
                            int kmax, int transpose, int prec, cudaStream_t st) {
   (void)jobs_d;
   (void)kmax;
-  KPSB_REQUIRE(prec == KPSB_P_TF32X3, "precision %d has no tensor-core kernel in this build", prec);
+  KPSB_REQUIRE(prec == KPSB_P_TF32X3 || prec == KPSB_P_TF32X2,
+               "precision %d has no tensor-core kernel", prec);
   TCPlan* P = nullptr;
-  KPSB_TRY(tc_plan_create(kps, jobs_h, jobs_h, njobs, n, st, &P));
+  KPSB_TRY(tc_plan_create(kps, jobs_h, jobs_h, njobs, n, prec, st, &P));
   kpsb_status s = tc_plan_apply(P, transpose, st);
   cudaError_t e = cudaStreamSynchronize(st);
   tc_plan_free(P, st);

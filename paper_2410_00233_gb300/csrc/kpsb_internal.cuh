@@ -101,7 +101,7 @@ struct TCPlan;
 bool tc_supported(int n, int prec);
 void tc_free(TCTables* t);
 kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h, int njobs, int n,
-                           cudaStream_t st, TCPlan** out);
+                           int prec, cudaStream_t st, TCPlan** out);
 kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st);
 void tc_plan_free(TCPlan* P, cudaStream_t st);
 kpsb_status tc_check_error();

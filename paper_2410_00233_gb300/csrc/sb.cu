@@ -246,6 +246,119 @@ __global__ void __launch_bounds__(SB_T) sb_shrink_kernel(const SBProb* __restric
   }
 }
 
+// Condition of the device-side CGLS loop (a WHILE node of the solve's CUDA graph): keep
+// iterating while any problem of the batch is still active.  The per-node counter bounds
+// the loop at `limit` iterations whatever the flags say.
+__global__ void sb_cond_kernel(cudaGraphConditionalHandle h, const SBProb* __restrict__ probs, int P,
+                               int* __restrict__ counter, int limit, int reset) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x)
+    if (probs[p].sc->active) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int c = reset ? 0 : counter[0] + 1;
+    counter[0] = c;
+    if (!reset) counter[1] += 1;
+    cudaGraphSetConditional(h, (any && c < limit) ? 1u : 0u);
+  }
+}
+
+// Builds and runs the whole batched solve as one CUDA graph: setup, then per outer step the
+// head launches, a WHILE node whose body is one CGLS iteration plus the condition kernel,
+// and the shrinkage.  The graph is captured from the same launch sequences as the
+// host-driven path.  Kernels that run inside the graph are counted after it completes.
+template <class FHead, class FIter, class FShrink>
+static kpsb_status sb_graph_run(cudaStream_t st, dim3 gv, const SBProb* dprobs, int P, int max_iters,
+                                int i_max, int* ctrs, FHead& head, FIter& iter, FShrink& shrink,
+                                int head_launches, int iter_launches) {
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  kpsb_status s = KPSB_OK;
+  cudaError_t e = cudaSuccess;
+  bool capturing = false;
+  set_capture_mode(true);
+  do {
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
+    if ((e = cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking)) != cudaSuccess) break;
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) break;
+    if ((e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+      break;
+    capturing = true;
+    sb_setup_kernel<<<gv, SB_T, 0, cs>>>(dprobs);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    for (int ell = 0; ell < max_iters; ++ell) {
+      if ((s = head(cs))) break;
+      cudaGraphConditionalHandle h;
+      if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+      sb_cond_kernel<<<1, 256, 0, cs>>>(h, dprobs, P, ctrs, i_max + 2, 1);
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+      cudaStreamCaptureStatus cst;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      cudaGraph_t capg = nullptr;
+      if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, nullptr, &nd)) != cudaSuccess) break;
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t wn;
+      if ((e = cudaGraphAddNode(&wn, capg, deps, nullptr, nd, &np)) != cudaSuccess) break;
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      if ((e = cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+          cudaSuccess)
+        break;
+      if ((e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        break;
+      kpsb_status si = iter(cs2);
+      if (si == KPSB_OK) {
+        sb_cond_kernel<<<1, 256, 0, cs2>>>(h, dprobs, P, ctrs, i_max + 2, 0);
+        e = cudaGetLastError();
+      }
+      cudaGraph_t body_out = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(cs2, &body_out);
+      if (si) { s = si; break; }
+      if (e == cudaSuccess) e = e2;
+      if (e != cudaSuccess) break;
+      if ((s = shrink(cs))) break;
+    }
+    cudaGraph_t gout = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &gout);
+    capturing = false;
+    if (s != KPSB_OK || e != cudaSuccess) break;
+    if ((e = e2) != cudaSuccess) break;
+    if ((e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) break;
+    if ((e = cudaGraphLaunch(ge, st)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+  } while (0);
+  if (capturing) {
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(cs, &tmp);
+  }
+  set_capture_mode(false);
+  if (s == KPSB_OK && e == cudaSuccess) {
+    int h[2] = {0, 0};
+    e = cudaMemcpy(h, ctrs, sizeof(h), cudaMemcpyDeviceToHost);
+    // kernels executed: setup, per outer step head + condition + shrink, per body run
+    // one CGLS iteration + condition
+    count_launch(1 + (long long)max_iters * (head_launches + 2) + (long long)h[1] * (iter_launches + 1));
+  }
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  if (cs2) cudaStreamDestroy(cs2);
+  if (s == KPSB_OK && e != cudaSuccess) {
+    set_error("split Bregman graph: %s", cudaGetErrorString(e));
+    s = KPSB_ECUDA;
+  }
+  return s;
+}
+
 // ---- host driver -------------------------------------------------------------------------------
 struct SBJobIn {
   kpsb_kp* kp;
@@ -271,7 +384,7 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
   const size_t zbytes = tc ? 0 : a256(kp_z_bytes(n, kmax, gemm_prec));
   const size_t per = a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
                      a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256;
-  const size_t total = per * P + a256(sizeof(SBProb) * P) + 2 * a256(sizeof(KPJob) * P);
+  const size_t total = per * P + a256(sizeof(SBProb) * P) + 2 * a256(sizeof(KPJob) * P) + 256;
   char* base = nullptr;
   KPSB_TRY_CUDA(cudaMallocAsync((void**)&base, total, st));
   std::vector<SBProb> hp(P);
@@ -318,6 +431,7 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
   SBProb* dprobs = (SBProb*)(base + per * P);
   KPJob* dfwd = (KPJob*)((char*)dprobs + a256(sizeof(SBProb) * P));
   KPJob* dbwd = (KPJob*)((char*)dfwd + a256(sizeof(KPJob) * P));
+  int* ctrs = (int*)((char*)dbwd + a256(sizeof(KPJob) * P));  // [0] loop counter, [1] body runs
   kpsb_status s = KPSB_OK;
   cudaError_t e = cudaSuccess;
   SBScal* hsc = nullptr;
@@ -328,6 +442,7 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
     if (e == cudaSuccess) e = cudaMemcpyAsync(dprobs, hp.data(), sizeof(SBProb) * P, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dfwd, fwd.data(), sizeof(KPJob) * P, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dbwd, bwd.data(), sizeof(KPJob) * P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctrs, 0, 2 * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&hsc, sizeof(SBScal) * P);
     if (e != cudaSuccess) { set_error("sb setup: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
     const int blocks = std::max(1, std::min(SB_MAX_BLOCKS, (int)((N + SB_T * 4 - 1) / (SB_T * 4))));
@@ -335,66 +450,78 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
     double ksum = 0.0;
     for (auto& j : jobs) ksum += j.kp->k;
     const double apply_flops = 4.0 * ksum * (double)n * n * n;  // 4 k n^3 per problem (Sec. 4.2)
-    if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, st, &plan))) break;
+    if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, o.prec, st, &plan))) break;
     const int apply_launches = tc ? 3 : 2;
-    auto kp_fwd = [&]() -> kpsb_status {
-      int slot = gemm_timer_begin(st);
-      kpsb_status r = tc ? tc_plan_apply(plan, 0, st) : kp_apply_batch(dfwd, P, n, kmax, 0, gemm_prec, st);
-      gemm_timer_end(slot, st, apply_flops, apply_launches);
+    const bool timed = gemm_timing_enabled();
+    // One KP apply of the whole batch on stream sx (timed with events in instrumented mode).
+    auto kp_apply_on = [&](int transpose, cudaStream_t sx) -> kpsb_status {
+      int slot = timed ? gemm_timer_begin(sx) : -1;
+      kpsb_status r = tc ? tc_plan_apply(plan, transpose, sx)
+                         : kp_apply_batch(transpose ? dbwd : dfwd, P, n, kmax, transpose, gemm_prec, sx);
+      gemm_timer_end(slot, sx, apply_flops, apply_launches);
       return r;
     };
-    auto kp_bwd = [&]() -> kpsb_status {
-      int slot = gemm_timer_begin(st);
-      kpsb_status r = tc ? tc_plan_apply(plan, 1, st) : kp_apply_batch(dbwd, P, n, kmax, 1, gemm_prec, st);
-      gemm_timer_end(slot, st, apply_flops, apply_launches);
-      return r;
+    // Head of an outer step: x_prev = x, CGLS start r = bhat, f = Ahat^T r, w = f.
+    auto outer_head = [&](cudaStream_t sx) -> kpsb_status {
+      sb_outer_init_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+      KPSB_CHECK_LAUNCH();
+      KPSB_TRY(kp_apply_on(1, sx));
+      sb_cgls_f_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 1);
+      KPSB_CHECK_LAUNCH();
+      sb_cgls_w_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+      KPSB_CHECK_LAUNCH();
+      return KPSB_OK;
     };
-    sb_setup_kernel<<<gv, SB_T, 0, st>>>(dprobs);
-    KPSB_CHECK_LAUNCH();
+    // One CGLS iteration (Alg. 5 steps 3-10) of every active problem.
+    auto cgls_iter = [&](cudaStream_t sx) -> kpsb_status {
+      KPSB_TRY(kp_apply_on(0, sx));
+      sb_cgls_zz_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+      KPSB_CHECK_LAUNCH();
+      sb_cgls_x_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+      KPSB_CHECK_LAUNCH();
+      KPSB_TRY(kp_apply_on(1, sx));
+      sb_cgls_f_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 0);
+      KPSB_CHECK_LAUNCH();
+      sb_cgls_w_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+      KPSB_CHECK_LAUNCH();
+      return KPSB_OK;
+    };
+    auto shrink = [&](cudaStream_t sx) -> kpsb_status {
+      sb_shrink_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+      KPSB_CHECK_LAUNCH();
+      return KPSB_OK;
+    };
     int max_iters = 0;
     for (auto& j : jobs) max_iters = std::max(max_iters, j.iters);
-    const int CHUNK = 4;
-    for (int ell = 0; ell < max_iters && s == KPSB_OK; ++ell) {
-      sb_outer_init_kernel<<<gv, SB_T, 0, st>>>(dprobs);
-      KPSB_CHECK_LAUNCH();
-      if ((s = kp_bwd())) break;
-      sb_cgls_f_kernel<<<gv, SB_T, 0, st>>>(dprobs, 1);
-      KPSB_CHECK_LAUNCH();
-      sb_cgls_w_kernel<<<gv, SB_T, 0, st>>>(dprobs);
-      KPSB_CHECK_LAUNCH();
-      for (int it = 0; it < o.i_max; ++it) {
-        if ((s = kp_fwd())) break;
-        sb_cgls_zz_kernel<<<gv, SB_T, 0, st>>>(dprobs);
-        KPSB_CHECK_LAUNCH();
-        sb_cgls_x_kernel<<<gv, SB_T, 0, st>>>(dprobs);
-        KPSB_CHECK_LAUNCH();
-        if ((s = kp_bwd())) break;
-        sb_cgls_f_kernel<<<gv, SB_T, 0, st>>>(dprobs, 0);
-        KPSB_CHECK_LAUNCH();
-        sb_cgls_w_kernel<<<gv, SB_T, 0, st>>>(dprobs);
-        KPSB_CHECK_LAUNCH();
-        if (!o.fixed_inner && (it + 1) % CHUNK == 0 && it + 1 < o.i_max) {
-          for (int p = 0; p < P && e == cudaSuccess; ++p)
-            e = cudaMemcpyAsync(hsc + p, hp[p].sc, sizeof(SBScal), cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-          if (e != cudaSuccess) break;
-          bool any = false;
-          for (int p = 0; p < P; ++p) any |= hsc[p].active != 0;
-          if (!any) break;
-        }
-      }
+    if (!timed) {
+      // Production path: the whole solve is one CUDA graph; each outer step's CGLS loop is
+      // a device-side WHILE node, so no host round trip happens until the end.
+      s = sb_graph_run(st, gv, dprobs, P, max_iters, o.i_max, ctrs, outer_head, cgls_iter, shrink,
+                       3 + apply_launches, 4 + 2 * apply_launches);
       if (s) break;
-      if (e != cudaSuccess) { set_error("sb loop: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
-      sb_shrink_kernel<<<gv, SB_T, 0, st>>>(dprobs);
+    } else {
+      // Instrumented path: host-driven loop (CUDA events around every KP apply), checking
+      // the device flags every few CGLS iterations.
+      sb_setup_kernel<<<gv, SB_T, 0, st>>>(dprobs);
       KPSB_CHECK_LAUNCH();
-      if (o.tau_sb > 0.0 && (ell + 1) % 2 == 0) {
-        for (int p = 0; p < P && e == cudaSuccess; ++p)
-          e = cudaMemcpyAsync(hsc + p, hp[p].sc, sizeof(SBScal), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      const int CHUNK = 4;
+      for (int ell = 0; ell < max_iters && s == KPSB_OK; ++ell) {
+        if ((s = outer_head(st))) break;
+        for (int it = 0; it < o.i_max; ++it) {
+          if ((s = cgls_iter(st))) break;
+          if (!o.fixed_inner && (it + 1) % CHUNK == 0 && it + 1 < o.i_max) {
+            for (int p = 0; p < P && e == cudaSuccess; ++p)
+              e = cudaMemcpyAsync(hsc + p, hp[p].sc, sizeof(SBScal), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) break;
+            bool any = false;
+            for (int p = 0; p < P; ++p) any |= hsc[p].active != 0;
+            if (!any) break;
+          }
+        }
+        if (s) break;
         if (e != cudaSuccess) { set_error("sb loop: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
-        bool any = false;
-        for (int p = 0; p < P; ++p) any |= hsc[p].sb_active != 0;
-        if (!any) break;
+        if ((s = shrink(st))) break;
       }
     }
     if (s) break;
@@ -422,7 +549,7 @@ static kpsb_status sb_defaults(const kpsb_sb_opts* opts, kpsb_sb_opts& o) {
   if (opts) o = *opts;
   if (o.tau_cgls <= 0.0) o.tau_cgls = 1e-4;
   if (o.i_max <= 0) o.i_max = 100;
-  KPSB_REQUIRE(o.prec >= KPSB_P_FP64 && o.prec <= KPSB_P_TF32X3, "unknown precision %d", o.prec);
+  KPSB_REQUIRE(o.prec >= KPSB_P_FP64 && o.prec <= KPSB_P_TF32X2, "unknown precision %d", o.prec);
   KPSB_REQUIRE(o.threshold_rule == KPSB_THR_EXACT || o.threshold_rule == KPSB_THR_PAPER,
                "unknown threshold rule %d", o.threshold_rule);
   return KPSB_OK;

@@ -177,7 +177,39 @@ def test_kp_apply_tensor_core_tf32x3(n, k, transpose):
     assert np.abs(y - ref).max() <= 5e-4 * np.abs(ref).max()
 
 
-def test_tensor_core_sb_isnr_within_0p1_db():
+def _tf32(a):
+    """Round-to-nearest (ties away) to TF32 (10 mantissa bits), as cvt.rna.tf32.f32."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return u.view(np.float32)
+
+
+@pytest.mark.parametrize("n,k", [(128, 5), (256, 12)])
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_kp_apply_tensor_core_tf32x2(n, k, transpose):
+    """TF32x2: the factors are used rounded once to TF32 (sigma folded into Ax in FP32),
+    the image split in two TF32 parts.  Against the oracle applied with those same
+    rounded factors only the tensor-core accumulation remains (bound 1e-4); against the
+    unrounded factors the TF32 rounding of A_k shows (bound 2e-3)."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    Ax, Ay, sig = _rand_factors(n, k, 5 * n + k)
+    kp = K.kp_from_factors(Ax, Ay, sig)
+    X = I.rng(7).standard_normal((n, n))
+    Axr = np.stack([_tf32(np.float32(sig[i]) * Ax[i]) for i in range(k)]).astype(np.float64)
+    Ayr = _tf32(Ay).astype(np.float64)
+    Kr = O.KPSum(Ax=Axr, Ay=Ayr, sigma=np.ones(k))
+    ref_r = O.kp_apply_t(Kr, X) if transpose else O.kp_apply(Kr, X)
+    Kop = _oracle_op(Ax, Ay, sig)
+    ref = O.kp_apply_t(Kop, X) if transpose else O.kp_apply(Kop, X)
+    y = K.kp_apply(kp, X, transpose, K.P_TF32X2)
+    assert np.linalg.norm(y - ref_r) / np.linalg.norm(ref_r) < 1e-4
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 2e-3
+
+
+@pytest.mark.parametrize("prec_name", ["P_TF32X3", "P_TF32X2"])
+def test_tensor_core_sb_isnr_within_0p1_db(prec_name):
     need_gpu()
     from paper_2410_00233_gb300 import kpsb as K
 
@@ -187,10 +219,11 @@ def test_tensor_core_sb_isnr_within_0p1_db():
     b = b_true + I.noise_vector(b_true, pr.eta, pr.zeta)
     kp = K.kp_build(pr.psf, n, pr.bc, pr.tau, K.EGKB, p=pr.p, start=pr.start.astype(np.float32))
     x64, s64 = K.sb_solve(kp, b, 1.0, 0.1, K.ISO, 15, prec=K.P_FP64)
-    xtc, stc = K.sb_solve(kp, b, 1.0, 0.1, K.ISO, 15, prec=K.P_TF32X3)
+    prec = getattr(K, prec_name)
+    xtc, stc = K.sb_solve(kp, b, 1.0, 0.1, K.ISO, 15, prec=prec)
     d = abs(O.isnr(xtc, b, pr.x_true) - O.isnr(x64, b, pr.x_true))
     assert d < 0.1, d
     assert abs(O.rel_error(xtc, pr.x_true) - O.rel_error(x64, pr.x_true)) < 1e-3
     # the batched tensor-core solve equals the single one
-    outs, st = K.sb_solve_batched([dict(kp=kp, b=b, mu=1.0, lam=0.1, tv=K.ISO, iters=15)] * 2, prec=K.P_TF32X3)
+    outs, st = K.sb_solve_batched([dict(kp=kp, b=b, mu=1.0, lam=0.1, tv=K.ISO, iters=15)] * 2, prec=prec)
     assert np.array_equal(outs[0], xtc) and np.array_equal(outs[1], xtc)
