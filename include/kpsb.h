@@ -230,6 +230,46 @@ kpsb_status kp_ra_materialize_dev(const float* psf, int s0, int s1, int n, int b
 kpsb_status kpsb_small_svd(int m, int nc, const double* A, double* U, double* S, double* V,
                            int* sweeps);
 
+/* ---- Serving: continuous batching of deblur requests (not in the paper) ----------------
+ * A server keeps the split Bregman state of every admitted request resident on the device
+ * and advances all of them together, round_steps outer steps per round; requests that
+ * arrive while others run join at the next round, finished ones leave.  Admission is FIFO
+ * while (a) fewer than max_active requests are resident and (b) their device memory
+ * (state, and factors when the PSF is not cached) fits in budget_bytes; cached factors of
+ * unused PSFs are evicted least-recently-used first when memory is needed.  Factors are
+ * built (kp_build, start vector seeded by the PSF key) on a builder thread, so builds
+ * overlap the running rounds, and cached by PSF key: a repeated PSF skips kp_build.  Each
+ * result equals that of sb_solve on the same factors: per-problem kernels, fixed-order
+ * reductions, and rounds that only regroup whole outer steps. */
+typedef struct kpsb_server* kpsb_server_t;
+typedef struct {
+  const double* psf; int s0, s1;  /* host PSF, column-major, copied at submit */
+  int n; int bc; double rank_or_tol; int method;
+  const double* b;                /* host n x n FP64 data, copied at submit */
+  double mu, lambda, beta;        /* beta <= 0: lambda^2 / 2 */
+  int tv; int iters;              /* KPSB_ANISO / KPSB_ISO, outer steps L_max */
+  int prec;                       /* KPSB_P_* of the KP GEMMs */
+  unsigned long long psf_key;     /* cache key (and EGKB seed); 0: hash of the PSF and sizes */
+} kpsb_request;
+typedef struct {
+  unsigned long long submitted, completed, failed, cache_hits, cache_misses, rounds;
+  size_t bytes_in_use, peak_bytes;  /* device bytes accounted against the budget */
+  int active, queued, cached;
+} kpsb_srv_stats;
+/* Starts the worker and builder threads on the current device. */
+kpsb_status srv_create(size_t budget_bytes, int max_active, int round_steps, kpsb_server_t* out);
+/* Queues a request (inputs copied); *id receives its id.  Requests that can never fit the
+ * budget fail with KPSB_EBUSY (reported by srv_poll). */
+kpsb_status srv_submit(kpsb_server_t s, const kpsb_request* req, unsigned long long* id);
+/* Waits up to timeout_us (< 0: forever) for request id.  KPSB_OK: x_out (n x n host, may be
+ * NULL), stats and latency_s (submit to result on the host, seconds) are filled and the
+ * request is retired; KPSB_ETIMEOUT: still running; other codes: the request failed. */
+kpsb_status srv_poll(kpsb_server_t s, unsigned long long id, long long timeout_us, double* x_out,
+                     kpsb_sb_stats* stats, double* latency_s);
+kpsb_status srv_stats(kpsb_server_t s, kpsb_srv_stats* out);
+/* Stops the threads and frees everything, including requests never polled. */
+void srv_destroy(kpsb_server_t s);
+
 /* ---- Instrumentation ----------------------------------------------------------------- */
 /* Kernels launched by this library in this process (all entry points, all threads). */
 unsigned long long kpsb_kernel_launches(void);

@@ -62,6 +62,38 @@ kpsb_status la_randn(float* out, long long count, unsigned long long seed, cudaS
 // ---- KP operator handle ---------------------------------------------------------------
 struct TCTables;  // tensor-core operand tables (kpgemm_tc.cu)
 
+// ---- split Bregman state (sb.cu), shared with the serving loop -------------------------
+struct SBScal;
+struct SBProb {
+  int n, iters, iso, fixed_inner, i_max;
+  double sqrt_mu, lam, thr, tau_cgls, tau_sb;
+  const double* b;
+  double *x, *xprev, *w, *f, *r1, *r2, *r3, *z1, *f1, *dx, *dy, *gx, *gy;
+  SBScal* sc;
+  double* part;           // reduction partials
+  unsigned int* counter;  // last-block counter
+};
+// Device-resident state of one problem; persists across sb_advance calls.
+struct SBState {
+  kpsb_kp* kp = nullptr;
+  int n = 0, prec = 0, gemm_prec = 0;
+  char* mem = nullptr;
+  size_t bytes = 0;
+  void* Z = nullptr;
+  bool initialized = false;
+  SBProb prob{};
+};
+size_t sb_state_bytes(int n, int k, int prec);
+kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* x_dev, double mu,
+                          double lambda, double beta, int tv, int iters, const kpsb_sb_opts& o,
+                          cudaStream_t st);
+kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kpsb_sb_opts& o,
+                       cudaStream_t st);
+kpsb_status sb_state_read(SBState* const* set, int count, std::vector<kpsb_sb_stats>& out,
+                          std::vector<int>& done, cudaStream_t st);
+void sb_state_free(SBState* S, cudaStream_t st);
+kpsb_status sb_fill_defaults(const kpsb_sb_opts* opts, kpsb_sb_opts& o);
+
 }  // namespace kpsb
 
 struct kpsb_kp {

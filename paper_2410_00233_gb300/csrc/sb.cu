@@ -32,16 +32,6 @@ struct SBScal {
   int pad;
 };
 
-struct SBProb {
-  int n, iters, iso, fixed_inner, i_max;
-  double sqrt_mu, lam, thr, tau_cgls, tau_sb;
-  const double* b;
-  double *x, *xprev, *w, *f, *r1, *r2, *r3, *z1, *f1, *dx, *dy, *gx, *gy;
-  SBScal* sc;
-  double* part;           // SB_MAX_BLOCKS * 2
-  unsigned int* counter;  // 1
-};
-
 __device__ __forceinline__ double dx_at(const double* X, int r, int c, int n) {  // (X L^T)(r,c)
   return c < n - 1 ? 0.5 * (X[r + (size_t)c * n] - X[r + (size_t)(c + 1) * n]) : 0.0;
 }
@@ -265,9 +255,9 @@ __global__ void sb_cond_kernel(cudaGraphConditionalHandle h, const SBProb* __res
   }
 }
 
-// Builds and runs the whole batched solve as one CUDA graph: setup, then per outer step the
+// Builds and runs `max_iters` outer steps of a batch as one CUDA graph: per outer step the
 // head launches, a WHILE node whose body is one CGLS iteration plus the condition kernel,
-// and the shrinkage.  The graph is captured from the same launch sequences as the
+// and the shrinkage (initialisation of new problems happens before, in sb_advance).  The graph is captured from the same launch sequences as the
 // host-driven path.  Kernels that run inside the graph are counted after it completes.
 template <class FHead, class FIter, class FShrink>
 static kpsb_status sb_graph_run(cudaStream_t st, dim3 gv, const SBProb* dprobs, int P, int max_iters,
@@ -288,8 +278,6 @@ static kpsb_status sb_graph_run(cudaStream_t st, dim3 gv, const SBProb* dprobs, 
         cudaSuccess)
       break;
     capturing = true;
-    sb_setup_kernel<<<gv, SB_T, 0, cs>>>(dprobs);
-    if ((e = cudaGetLastError()) != cudaSuccess) break;
     for (int ell = 0; ell < max_iters; ++ell) {
       if ((s = head(cs))) break;
       cudaGraphConditionalHandle h;
@@ -344,9 +332,9 @@ static kpsb_status sb_graph_run(cudaStream_t st, dim3 gv, const SBProb* dprobs, 
   if (s == KPSB_OK && e == cudaSuccess) {
     int h[2] = {0, 0};
     e = cudaMemcpy(h, ctrs, sizeof(h), cudaMemcpyDeviceToHost);
-    // kernels executed: setup, per outer step head + condition + shrink, per body run
-    // one CGLS iteration + condition
-    count_launch(1 + (long long)max_iters * (head_launches + 2) + (long long)h[1] * (iter_launches + 1));
+    // kernels executed: per outer step head + condition + shrink, per body run one CGLS
+    // iteration + condition
+    count_launch((long long)max_iters * (head_launches + 2) + (long long)h[1] * (iter_launches + 1));
   }
   if (ge) cudaGraphExecDestroy(ge);
   if (g) cudaGraphDestroy(g);
@@ -360,76 +348,137 @@ static kpsb_status sb_graph_run(cudaStream_t st, dim3 gv, const SBProb* dprobs, 
 }
 
 // ---- host driver -------------------------------------------------------------------------------
-struct SBJobIn {
-  kpsb_kp* kp;
-  const double* b;  // device
-  double* x;        // device
-  double mu, lambda, beta;
-  int tv, iters;
-};
-
 static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Runs all jobs (same n) to completion on stream st.  stats_out receives one entry per job.
-static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_opts& o,
-                                cudaStream_t st, std::vector<kpsb_sb_stats>& stats_out) {
-  const int P = (int)jobs.size();
-  const int n = jobs[0].kp->n;
+// GEMM arithmetic actually used for a size: tensor cores where the kernel tiles n, else
+// FP32 (or FP64) CUDA cores.
+static int gemm_prec_for(int n, int prec) {
+  if (tc_supported(n, prec)) return prec;
+  return prec == KPSB_P_FP64 ? KPSB_P_FP64 : KPSB_P_FP32;
+}
+
+size_t sb_state_bytes(int n, int k, int prec) {
+  const size_t N = (size_t)n * n;
+  const int gp = gemm_prec_for(n, prec);
+  const size_t zbytes = tc_supported(n, gp) ? 0 : a256(kp_z_bytes(n, k, gp));
+  size_t tc_ws = tc_supported(n, gp) ? a256(sizeof(float) * ((size_t)2 * N + (size_t)2 * n * k * n)) : 0;
+  return a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
+         a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256 + tc_ws;
+}
+
+kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* x_dev, double mu,
+                          double lambda, double beta, int tv, int iters, const kpsb_sb_opts& o,
+                          cudaStream_t st) {
+  const int n = kp->n;
+  const size_t N = (size_t)n * n;
+  S->kp = kp;
+  S->n = n;
+  S->prec = o.prec;
+  S->gemm_prec = gemm_prec_for(n, o.prec);
+  S->initialized = false;
+  const size_t zbytes = tc_supported(n, S->gemm_prec) ? 0 : a256(kp_z_bytes(n, kp->k, S->gemm_prec));
+  S->bytes = a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
+             a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256;
+  KPSB_TRY_CUDA(cudaMallocAsync((void**)&S->mem, S->bytes, st));
+  char* q = S->mem;
+  double* v = (double*)q;
+  SBProb& P = S->prob;
+  P.n = n;
+  P.iters = iters;
+  P.iso = tv == KPSB_ISO;
+  P.fixed_inner = o.fixed_inner;
+  P.i_max = o.i_max;
+  P.sqrt_mu = sqrt(mu);
+  P.lam = lambda;
+  P.thr = o.threshold_rule == KPSB_THR_PAPER ? beta / (lambda * lambda) : beta / (2.0 * lambda * lambda);
+  P.tau_cgls = o.tau_cgls;
+  P.tau_sb = o.tau_sb;
+  P.b = b_dev;
+  P.x = x_dev;
+  P.xprev = v + 0 * N; P.w = v + 1 * N; P.f = v + 2 * N; P.r1 = v + 3 * N; P.r2 = v + 4 * N;
+  P.r3 = v + 5 * N; P.z1 = v + 6 * N; P.f1 = v + 7 * N; P.dx = v + 8 * N; P.dy = v + 9 * N;
+  P.gx = v + 10 * N; P.gy = v + 11 * N;
+  q += a256(13 * N * sizeof(double));
+  S->Z = zbytes ? (void*)q : nullptr;
+  q += zbytes;
+  P.sc = (SBScal*)q;
+  q += a256(sizeof(SBScal));
+  P.part = (double*)q;
+  q += a256(sizeof(double) * SB_MAX_BLOCKS * 2);
+  P.counter = (unsigned int*)q;
+  KPSB_TRY_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned int), st));
+  return KPSB_OK;
+}
+
+void sb_state_free(SBState* S, cudaStream_t st) {
+  if (S && S->mem) {
+    cudaFreeAsync(S->mem, st);
+    S->mem = nullptr;
+  }
+}
+
+kpsb_status sb_state_read(SBState* const* set, int count, std::vector<kpsb_sb_stats>& out,
+                          std::vector<int>& done, cudaStream_t st) {
+  SBScal* hsc = nullptr;
+  KPSB_TRY_CUDA(cudaMallocHost((void**)&hsc, sizeof(SBScal) * std::max(1, count)));
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < count && e == cudaSuccess; ++p)
+    e = cudaMemcpyAsync(hsc + p, set[p]->prob.sc, sizeof(SBScal), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    out.resize(count);
+    done.resize(count);
+    for (int p = 0; p < count; ++p) {
+      out[p].l_end = hsc[p].l_end;
+      out[p].iota_total = hsc[p].iota_total;
+      out[p].rc_sb = hsc[p].rc_sb;
+      out[p].status = KPSB_OK;
+      done[p] = set[p]->initialized && !hsc[p].sb_active;
+    }
+  }
+  cudaFreeHost(hsc);
+  if (e != cudaSuccess) {
+    set_error("reading split Bregman state: %s", cudaGetErrorString(e));
+    return KPSB_ECUDA;
+  }
+  return KPSB_OK;
+}
+
+// Advances every state of `set` (all with the same n) by up to `outer_steps` outer split
+// Bregman steps: states not yet initialised get x = b, d = g = 0 first; finished states
+// do nothing.  Production runs one CUDA graph; with GEMM timing on, a host-driven loop.
+kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kpsb_sb_opts& o,
+                       cudaStream_t st) {
+  if (count <= 0 || outer_steps <= 0) return KPSB_OK;
+  const int P = count;
+  const int n = set[0]->n;
   const size_t N = (size_t)n * n;
   int kmax = 0;
-  for (auto& j : jobs) kmax = std::max(kmax, j.kp->k);
-  // tensor-core GEMMs where the kernel tiles the size; other sizes use FP32 CUDA cores
-  const bool tc = tc_supported(n, o.prec);
-  const int gemm_prec = tc ? o.prec : (o.prec == KPSB_P_FP64 ? KPSB_P_FP64 : KPSB_P_FP32);
-  const size_t zbytes = tc ? 0 : a256(kp_z_bytes(n, kmax, gemm_prec));
-  const size_t per = a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
-                     a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256;
-  const size_t total = per * P + a256(sizeof(SBProb) * P) + 2 * a256(sizeof(KPJob) * P) + 256;
+  for (int p = 0; p < P; ++p) kmax = std::max(kmax, set[p]->kp->k);
+  const int gemm_prec = gemm_prec_for(n, o.prec);
+  const bool tc = tc_supported(n, gemm_prec);
+  const size_t small = a256(sizeof(SBProb) * P) * 2 + 2 * a256(sizeof(KPJob) * P) + 256;
   char* base = nullptr;
-  KPSB_TRY_CUDA(cudaMallocAsync((void**)&base, total, st));
-  std::vector<SBProb> hp(P);
+  KPSB_TRY_CUDA(cudaMallocAsync((void**)&base, small, st));
+  std::vector<SBProb> hp(P), hnew;
   std::vector<KPJob> fwd(P), bwd(P);
   std::vector<kpsb_kp*> kps(P);
   for (int p = 0; p < P; ++p) {
-    char* q = base + per * p;
-    SBProb& S = hp[p];
-    const SBJobIn& J = jobs[p];
-    double* v = (double*)q;
-    S.n = n;
-    S.iters = J.iters;
-    S.iso = J.tv == KPSB_ISO;
-    S.fixed_inner = o.fixed_inner;
-    S.i_max = o.i_max;
-    S.sqrt_mu = sqrt(J.mu);
-    S.lam = J.lambda;
-    S.thr = o.threshold_rule == KPSB_THR_PAPER ? J.beta / (J.lambda * J.lambda)
-                                                : J.beta / (2.0 * J.lambda * J.lambda);
-    S.tau_cgls = o.tau_cgls;
-    S.tau_sb = o.tau_sb;
-    S.b = J.b;
-    S.x = J.x;
-    S.xprev = v + 0 * N; S.w = v + 1 * N; S.f = v + 2 * N; S.r1 = v + 3 * N; S.r2 = v + 4 * N;
-    S.r3 = v + 5 * N; S.z1 = v + 6 * N; S.f1 = v + 7 * N; S.dx = v + 8 * N; S.dy = v + 9 * N;
-    S.gx = v + 10 * N; S.gy = v + 11 * N;
-    q += a256(13 * N * sizeof(double));
-    void* Z = q;
-    q += zbytes;
-    S.sc = (SBScal*)q;
-    q += a256(sizeof(SBScal));
-    S.part = (double*)q;
-    q += a256(sizeof(double) * SB_MAX_BLOCKS * 2);
-    S.counter = (unsigned int*)q;
-    kps[p] = J.kp;
+    const SBState* S = set[p];
+    hp[p] = S->prob;
+    if (!S->initialized) hnew.push_back(S->prob);
+    kps[p] = S->kp;
     KPJob& F = fwd[p];
-    F.Ax = J.kp->Ax; F.Ay = J.kp->Ay; F.sigma = J.kp->sigma_d; F.n = n; F.k = J.kp->k;
-    F.X = S.w; F.Y = S.z1; F.Z = Z;
-    F.active = (const int*)((char*)S.sc + offsetof(SBScal, active));
+    F.Ax = S->kp->Ax; F.Ay = S->kp->Ay; F.sigma = S->kp->sigma_d; F.n = n; F.k = S->kp->k;
+    F.X = S->prob.w; F.Y = S->prob.z1; F.Z = S->Z;
+    F.active = (const int*)((char*)S->prob.sc + offsetof(SBScal, active));
     KPJob& B = bwd[p];
     B = F;
-    B.X = S.r1; B.Y = S.f1;
+    B.X = S->prob.r1; B.Y = S->prob.f1;
   }
-  SBProb* dprobs = (SBProb*)(base + per * P);
-  KPJob* dfwd = (KPJob*)((char*)dprobs + a256(sizeof(SBProb) * P));
+  SBProb* dprobs = (SBProb*)base;
+  SBProb* dnew = (SBProb*)(base + a256(sizeof(SBProb) * P));
+  KPJob* dfwd = (KPJob*)((char*)dnew + a256(sizeof(SBProb) * P));
   KPJob* dbwd = (KPJob*)((char*)dfwd + a256(sizeof(KPJob) * P));
   int* ctrs = (int*)((char*)dbwd + a256(sizeof(KPJob) * P));  // [0] loop counter, [1] body runs
   kpsb_status s = KPSB_OK;
@@ -437,9 +486,9 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
   SBScal* hsc = nullptr;
   TCPlan* plan = nullptr;
   do {
-    for (int p = 0; p < P && e == cudaSuccess; ++p)
-      e = cudaMemsetAsync(hp[p].counter, 0, sizeof(unsigned int), st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dprobs, hp.data(), sizeof(SBProb) * P, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(dprobs, hp.data(), sizeof(SBProb) * P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !hnew.empty())
+      e = cudaMemcpyAsync(dnew, hnew.data(), sizeof(SBProb) * hnew.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dfwd, fwd.data(), sizeof(KPJob) * P, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dbwd, bwd.data(), sizeof(KPJob) * P, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctrs, 0, 2 * sizeof(int), st);
@@ -447,10 +496,15 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
     if (e != cudaSuccess) { set_error("sb setup: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
     const int blocks = std::max(1, std::min(SB_MAX_BLOCKS, (int)((N + SB_T * 4 - 1) / (SB_T * 4))));
     dim3 gv(blocks, P);
+    if (!hnew.empty()) {
+      sb_setup_kernel<<<dim3(blocks, (unsigned)hnew.size()), SB_T, 0, st>>>(dnew);
+      KPSB_CHECK_LAUNCH();
+      for (int p = 0; p < P; ++p) set[p]->initialized = true;
+    }
     double ksum = 0.0;
-    for (auto& j : jobs) ksum += j.kp->k;
+    for (int p = 0; p < P; ++p) ksum += set[p]->kp->k;
     const double apply_flops = 4.0 * ksum * (double)n * n * n;  // 4 k n^3 per problem (Sec. 4.2)
-    if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, o.prec, st, &plan))) break;
+    if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, gemm_prec, st, &plan))) break;
     const int apply_launches = tc ? 3 : 2;
     const bool timed = gemm_timing_enabled();
     // One KP apply of the whole batch on stream sx (timed with events in instrumented mode).
@@ -491,21 +545,17 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
       KPSB_CHECK_LAUNCH();
       return KPSB_OK;
     };
-    int max_iters = 0;
-    for (auto& j : jobs) max_iters = std::max(max_iters, j.iters);
     if (!timed) {
-      // Production path: the whole solve is one CUDA graph; each outer step's CGLS loop is
-      // a device-side WHILE node, so no host round trip happens until the end.
-      s = sb_graph_run(st, gv, dprobs, P, max_iters, o.i_max, ctrs, outer_head, cgls_iter, shrink,
+      // Production path: the whole advance is one CUDA graph; each outer step's CGLS loop
+      // is a device-side WHILE node, so no host round trip happens until the end.
+      s = sb_graph_run(st, gv, dprobs, P, outer_steps, o.i_max, ctrs, outer_head, cgls_iter, shrink,
                        3 + apply_launches, 4 + 2 * apply_launches);
       if (s) break;
     } else {
       // Instrumented path: host-driven loop (CUDA events around every KP apply), checking
       // the device flags every few CGLS iterations.
-      sb_setup_kernel<<<gv, SB_T, 0, st>>>(dprobs);
-      KPSB_CHECK_LAUNCH();
       const int CHUNK = 4;
-      for (int ell = 0; ell < max_iters && s == KPSB_OK; ++ell) {
+      for (int ell = 0; ell < outer_steps && s == KPSB_OK; ++ell) {
         if ((s = outer_head(st))) break;
         for (int it = 0; it < o.i_max; ++it) {
           if ((s = cgls_iter(st))) break;
@@ -523,20 +573,10 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
         if (e != cudaSuccess) { set_error("sb loop: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
         if ((s = shrink(st))) break;
       }
+      if (s) break;
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { set_error("sb loop: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
     }
-    if (s) break;
-    for (int p = 0; p < P && e == cudaSuccess; ++p)
-      e = cudaMemcpyAsync(hsc + p, hp[p].sc, sizeof(SBScal), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) { set_error("sb finish: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
     if (tc && (s = tc_check_error())) break;
-    stats_out.resize(P);
-    for (int p = 0; p < P; ++p) {
-      stats_out[p].l_end = hsc[p].l_end;
-      stats_out[p].iota_total = hsc[p].iota_total;
-      stats_out[p].rc_sb = hsc[p].rc_sb;
-      stats_out[p].status = KPSB_OK;
-    }
   } while (0);
   if (hsc) cudaFreeHost(hsc);
   if (plan) tc_plan_free(plan, st);
@@ -544,7 +584,37 @@ static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_
   return s;
 }
 
-static kpsb_status sb_defaults(const kpsb_sb_opts* opts, kpsb_sb_opts& o) {
+struct SBJobIn {
+  kpsb_kp* kp;
+  const double* b;  // device
+  double* x;        // device
+  double mu, lambda, beta;
+  int tv, iters;
+};
+
+// Runs all jobs (same n) to completion on stream st.  stats_out receives one entry per job.
+static kpsb_status sb_run_group(const std::vector<SBJobIn>& jobs, const kpsb_sb_opts& o,
+                                cudaStream_t st, std::vector<kpsb_sb_stats>& stats_out) {
+  const int P = (int)jobs.size();
+  std::vector<SBState> states(P);
+  std::vector<SBState*> set(P);
+  kpsb_status s = KPSB_OK;
+  int made = 0;
+  for (; made < P && s == KPSB_OK; ++made) {
+    const SBJobIn& J = jobs[made];
+    s = sb_state_init(&states[made], J.kp, J.b, J.x, J.mu, J.lambda, J.beta, J.tv, J.iters, o, st);
+    set[made] = &states[made];
+  }
+  int max_iters = 0;
+  for (auto& j : jobs) max_iters = std::max(max_iters, j.iters);
+  if (s == KPSB_OK) s = sb_advance(set.data(), P, max_iters, o, st);
+  std::vector<int> done;
+  if (s == KPSB_OK) s = sb_state_read(set.data(), P, stats_out, done, st);
+  for (int p = 0; p < made; ++p) sb_state_free(&states[p], st);
+  return s;
+}
+
+kpsb_status sb_fill_defaults(const kpsb_sb_opts* opts, kpsb_sb_opts& o) {
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   if (o.tau_cgls <= 0.0) o.tau_cgls = 1e-4;
@@ -574,7 +644,7 @@ extern "C" kpsb_status sb_solve_dev(kpsb_kp_t kp, const double* b, double mu, do
   KPSB_TRY(sb_check_job(kp, mu, lambda, tv, iters));
   KPSB_REQUIRE(b && x_out && b != x_out, "null or aliased pointer");
   kpsb_sb_opts o;
-  KPSB_TRY(sb_defaults(opts, o));
+  KPSB_TRY(sb_fill_defaults(opts, o));
   double beta = o.beta > 0.0 ? o.beta : lambda * lambda / 2.0;
   std::vector<SBJobIn> jobs(1);
   jobs[0] = SBJobIn{kp, b, x_out, mu, lambda, beta, tv, iters};
@@ -592,7 +662,7 @@ extern "C" kpsb_status sb_solve(kpsb_kp_t kp, const double* b, double mu, double
   KPSB_REQUIRE(b && x_out, "null pointer");
   const size_t bytes = sizeof(double) * (size_t)kp->n * kp->n;
   kpsb_sb_opts o;
-  KPSB_TRY(sb_defaults(opts, o));
+  KPSB_TRY(sb_fill_defaults(opts, o));
   cudaStream_t st = (cudaStream_t)o.stream;
   double* d = nullptr;
   KPSB_TRY_CUDA(cudaMallocAsync((void**)&d, 2 * bytes, st));
@@ -617,7 +687,7 @@ extern "C" kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int 
   KPSB_REQUIRE(count >= 0 && (count == 0 || jobs), "bad batch");
   if (count == 0) return KPSB_OK;
   kpsb_sb_opts o;
-  KPSB_TRY(sb_defaults(opts, o));
+  KPSB_TRY(sb_fill_defaults(opts, o));
   cudaStream_t st = (cudaStream_t)o.stream;
   for (int i = 0; i < count; ++i) {
     KPSB_TRY(sb_check_job(jobs[i].kp, jobs[i].mu, jobs[i].lambda, jobs[i].tv, jobs[i].iters));

@@ -60,6 +60,21 @@ class SBJob(C.Structure):
                 ("stats", C.POINTER(SBStats))]
 
 
+class Request(C.Structure):
+    _fields_ = [("psf", C.POINTER(C.c_double)), ("s0", C.c_int), ("s1", C.c_int), ("n", C.c_int),
+                ("bc", C.c_int), ("rank_or_tol", C.c_double), ("method", C.c_int),
+                ("b", C.POINTER(C.c_double)), ("mu", C.c_double), ("lambda_", C.c_double),
+                ("beta", C.c_double), ("tv", C.c_int), ("iters", C.c_int), ("prec", C.c_int),
+                ("psf_key", C.c_ulonglong)]
+
+
+class SrvStats(C.Structure):
+    _fields_ = [("submitted", C.c_ulonglong), ("completed", C.c_ulonglong), ("failed", C.c_ulonglong),
+                ("cache_hits", C.c_ulonglong), ("cache_misses", C.c_ulonglong), ("rounds", C.c_ulonglong),
+                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t), ("active", C.c_int),
+                ("queued", C.c_int), ("cached", C.c_int)]
+
+
 _lib = None
 
 _SIGS = {
@@ -91,6 +106,12 @@ _SIGS = {
     "kpsb_small_svd": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "kpsb_last_error": (C.c_char_p, []),
+    "srv_create": (C.c_int, [C.c_size_t, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "srv_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_ulonglong)]),
+    "srv_poll": (C.c_int, [C.c_void_p, C.c_ulonglong, C.c_longlong, C.POINTER(C.c_double),
+                           C.POINTER(SBStats), C.POINTER(C.c_double)]),
+    "srv_stats": (C.c_int, [C.c_void_p, C.POINTER(SrvStats)]),
+    "srv_destroy": (None, [C.c_void_p]),
     "kpsb_kernel_launches": (C.c_ulonglong, []),
     "kpsb_gemm_timing": (C.c_int, [C.c_int]),
     "kpsb_gemm_stats": (C.c_int, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -340,6 +361,62 @@ def kp_ra_apply_noalloc_dev(psf_ptr: int, s0: int, s1: int, n: int, bc: int, V_p
 def kp_ra_materialize_dev(psf_ptr: int, s0: int, s1: int, n: int, bc: int, R_ptr: int, stream=0):
     _check("kp_ra_materialize_dev", lib().kp_ra_materialize_dev(
         C.c_void_p(psf_ptr), s0, s1, n, bc, C.c_void_p(R_ptr), C.c_void_p(int(stream)) if stream else None))
+
+
+class Server:
+    """Continuous-batching deblur server (srv_* of include/kpsb.h)."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 64, round_steps: int = 5):
+        out = C.c_void_p()
+        _check("srv_create", lib().srv_create(int(budget_bytes), int(max_active), int(round_steps),
+                                              C.byref(out)))
+        self.ptr = out
+        self._n = {}
+
+    def submit(self, psf, n, bc, rank_or_tol, b, mu, lam, tv, iters, *, method=EGKB, beta=0.0,
+               prec=P_TF32X2, psf_key=0) -> int:
+        ps = _f64(psf)
+        bf = _f64(b)
+        r = Request()
+        r.psf = _pd(ps)
+        r.s0, r.s1 = ps.shape
+        r.n, r.bc, r.rank_or_tol, r.method = int(n), int(bc), float(rank_or_tol), int(method)
+        r.b = _pd(bf)
+        r.mu, r.lambda_, r.beta = float(mu), float(lam), float(beta)
+        r.tv, r.iters, r.prec, r.psf_key = int(tv), int(iters), int(prec), int(psf_key)
+        rid = C.c_ulonglong()
+        _check("srv_submit", lib().srv_submit(self.ptr, C.byref(r), C.byref(rid)))
+        self._n[rid.value] = int(n)
+        return rid.value
+
+    def poll(self, rid: int, timeout_us: int = -1):
+        """(x, Stats, latency_s) when done, None on timeout; raises if the request failed."""
+        n = self._n[rid]
+        x = np.zeros((n, n), order="F")
+        st = SBStats()
+        lat = C.c_double()
+        code = lib().srv_poll(self.ptr, C.c_ulonglong(rid), int(timeout_us), _pd(x), C.byref(st), C.byref(lat))
+        if code == -4:
+            return None
+        self._n.pop(rid, None)
+        _check("srv_poll", code)
+        return x, _stats(st), lat.value
+
+    def stats(self) -> dict:
+        st = SrvStats()
+        _check("srv_stats", lib().srv_stats(self.ptr, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in SrvStats._fields_}
+
+    def close(self):
+        if self.ptr and self.ptr.value:
+            lib().srv_destroy(self.ptr)
+            self.ptr = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kpsb_kernel_launches() -> int:
