@@ -21,6 +21,7 @@
 // warps read their 32 TMEM lanes with tcgen05.ld and run the epilogue.  Every wait is
 // bounded: on timeout the CTA records an error code, drains and frees TMEM, and returns.
 #include <cuda.h>
+#include <stdlib.h>
 
 #include <mutex>
 
@@ -183,7 +184,8 @@ __device__ __forceinline__ float tf32_round(float x) {
 // ------------------------------------------------------------------------------------------
 struct alignas(128) TCJob {
   CUtensorMap m1A;   // Xt planes: {n, n, 2}
-  CUtensorMap m1B;   // T1 planes: {n, n, 2, k}
+  CUtensorMap m1B;   // T1 planes: {n, n, 2, k} (box 128 rows, two-stage kernel)
+  CUtensorMap m1F;   // T1 planes, box FUSED_BN rows (fused kernel)
   CUtensorMap m2A;   // T2 planes: {k n, n, 2}
   CUtensorMap m2B;   // Zt planes: {k n, n, 2}
   const double* X;   // input image (n x n FP64, column-major)
@@ -489,6 +491,252 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
   }
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Fused apply: both stages in one CTA per (problem, BN-column tile); the intermediate
+// Z_i(r, c) of a unit (term i, 128-row chunk rc of r) goes TMEM -> registers -> split TF32
+// planes in shared memory (128-byte-swizzled K-major rows c, K = r) and is consumed there
+// by the stage-2 MMAs, so it never reaches global memory.
+//   units u = (i, rc), i < k, rc < R = n/128
+//   S1(u): D1[u%2][r][c] = sum_m Xt[rc*128 + r][m] T1_i[c0 + c][m]       (K = n)
+//   C(u) : Zs[c][r] = split(D1[u%2][r][c])                                (converter warps)
+//   S2(u): D2[t][a][c] += sum_r T2[t*128 + a][i n + rc*128 + r] Zs[c][r]  (K = 128, every t)
+// Issue order S1(0), S1(1), S2(0), S1(2), S2(1), ...: stage 1 of the next unit overlaps the
+// conversion of the current one (two D1 buffers in TMEM).  Warps: 0 = TMA, 1 = MMA,
+// 2..5 = converter and epilogue (TMEM lane quarters 2, 3, 0, 1).
+// ------------------------------------------------------------------------------------------
+static constexpr int FUSED_BN = 64;
+
+template <int BN, int FPL>
+struct FCfg {
+  static constexpr int XA_BYTES = 128 * 128;         // one plane of a 128-row x 32-K slice
+  static constexpr int TB_BYTES = BN * 128;          // one plane of a BN-row x 32-K slice
+  static constexpr int S1_BYTES = 2 * XA_BYTES + FPL * TB_BYTES;  // Xt hi/lo + T1 planes
+  static constexpr int S2_BYTES = FPL * XA_BYTES;                 // T2 planes
+  static constexpr int SLOT = S1_BYTES > S2_BYTES ? S1_BYTES : S2_BYTES;
+  static constexpr int ZS_PLANE = 4 * TB_BYTES;      // BN rows x 128 K: four 32-K sub-tiles
+  static constexpr int ZS_BYTES = 2 * ZS_PLANE;      // hi, lo
+  static constexpr int STAGES = 3;
+  static constexpr int SMEM = STAGES * SLOT + ZS_BYTES + 1024 + 512;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that gives up at once when the CTA has already failed.
+__device__ __forceinline__ bool fwait(uint64_t* bar, uint32_t parity, volatile int* fail) {
+  if (*fail) return false;
+  if (mbar_wait(bar, parity)) return true;
+  *fail = 1;
+  return false;
+}
+
+template <int BN, int FPL>
+__global__ void __launch_bounds__(192, 1) tc_fused_kernel(const TCJob* __restrict__ jobs) {
+  using C = FCfg<BN, FPL>;
+  constexpr int STAGES = C::STAGES;
+  const TCJob& J = jobs[blockIdx.y];
+  if (J.active && !*J.active) return;
+  const int n = J.n, k = J.k;
+  const int c0 = blockIdx.x * BN;
+  if (c0 >= n) return;
+  const int R = n / 128;
+  const int U = k * R;
+  const int nkb1 = n / 32;
+
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* zs = smem + STAGES * C::SLOT;
+  uint64_t* full = (uint64_t*)(zs + C::ZS_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* d1_full = empty + STAGES;
+  uint64_t* d1_empty = d1_full + 2;
+  uint64_t* zs_full = d1_empty + 2;
+  uint64_t* zs_empty = zs_full + 1;
+  uint64_t* d2_full = zs_empty + 1;
+  uint32_t* tmem_slot = (uint32_t*)(d2_full + 1);
+  __shared__ int s_fail_v;
+  volatile int* s_fail = &s_fail_v;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)((R + 2) * BN)) ncols <<= 1;
+  if (threadIdx.x == 0) {
+    s_fail_v = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&d1_full[b], 1);
+      mbar_init(&d1_empty[b], 4);
+    }
+    mbar_init(zs_full, 4);
+    mbar_init(zs_empty, 1);
+    mbar_init(d2_full, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t idesc = idesc_tf32(128, BN);
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: slots in the MMA's consumption order ----
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m1A) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m1F) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m2A) : "memory");
+    int si = 0;
+    bool ok = true;
+    for (int v = 0; v <= U && ok; ++v) {
+      if (v < U) {
+        const int i = v / R, rc = v % R;
+        for (int kb = 0; kb < nkb1 && ok; ++kb, ++si) {
+          const int s = si % STAGES, round = si / STAGES;
+          if (round > 0 && !fwait(&empty[s], (round - 1) & 1, s_fail)) { ok = false; break; }
+          unsigned char* st = smem + s * C::SLOT;
+          mbar_expect_tx(&full[s], C::S1_BYTES);
+          tma_load_3d(st, &J.m1A, &full[s], kb * 32, rc * 128, 0);
+          tma_load_3d(st + C::XA_BYTES, &J.m1A, &full[s], kb * 32, rc * 128, 1);
+          for (int pl = 0; pl < FPL; ++pl)
+            tma_load_4d(st + 2 * C::XA_BYTES + pl * C::TB_BYTES, &J.m1F, &full[s], kb * 32, c0, pl, i);
+        }
+      }
+      if (v >= 1 && ok) {
+        const int u = v - 1, i = u / R, rc = u % R;
+        for (int t = 0; t < R && ok; ++t)
+          for (int q = 0; q < 4 && ok; ++q, ++si) {
+            const int s = si % STAGES, round = si / STAGES;
+            if (round > 0 && !fwait(&empty[s], (round - 1) & 1, s_fail)) { ok = false; break; }
+            unsigned char* st = smem + s * C::SLOT;
+            mbar_expect_tx(&full[s], C::S2_BYTES);
+            for (int pl = 0; pl < FPL; ++pl)
+              tma_load_3d(st + pl * C::XA_BYTES, &J.m2A, &full[s], i * n + rc * 128 + q * 32, t * 128, pl);
+          }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    int si = 0;
+    bool ok = true;
+    for (int v = 0; v <= U && ok; ++v) {
+      if (v < U) {
+        const uint32_t d1 = tmem + (uint32_t)((R + (v & 1)) * BN);
+        if (v >= 2 && !fwait(&d1_empty[v & 1], ((v >> 1) - 1) & 1, s_fail)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kb = 0; kb < nkb1; ++kb, ++si) {
+          const int s = si % STAGES, round = si / STAGES;
+          if (!fwait(&full[s], round & 1, s_fail)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(smem + s * C::SLOT);
+          const uint32_t a_hi = sa, a_lo = sa + C::XA_BYTES;
+          const uint32_t b_hi = sa + 2 * C::XA_BYTES, b_lo = b_hi + (FPL == 2 ? C::TB_BYTES : 0);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t off = kk * 32, acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+            mma_tf32(d1, sdesc_sw128(a_lo + off), sdesc_sw128(b_hi + off), idesc, acc0);
+            if (FPL == 2) mma_tf32(d1, sdesc_sw128(a_hi + off), sdesc_sw128(b_lo + off), idesc, 1u);
+            mma_tf32(d1, sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), idesc, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&d1_full[v & 1]);
+      }
+      if (v >= 1) {
+        const int u = v - 1;
+        if (!fwait(zs_full, u & 1, s_fail)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t z_hi = smem_u32(zs), z_lo = z_hi + C::ZS_PLANE;
+        for (int t = 0; t < R && ok; ++t) {
+          const uint32_t d2 = tmem + (uint32_t)(t * BN);
+          for (int q = 0; q < 4; ++q, ++si) {
+            const int s = si % STAGES, round = si / STAGES;
+            if (!fwait(&full[s], round & 1, s_fail)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(smem + s * C::SLOT);
+            const uint32_t a_hi = sa, a_lo = sa + (FPL == 2 ? C::XA_BYTES : 0);
+            const uint32_t zq = q * C::TB_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t off = kk * 32;
+              const uint32_t acc0 = (u > 0 || q > 0 || kk > 0) ? 1u : 0u;
+              mma_tf32(d2, sdesc_sw128(a_hi + off), sdesc_sw128(z_lo + zq + off), idesc, acc0);
+              if (FPL == 2) mma_tf32(d2, sdesc_sw128(a_lo + off), sdesc_sw128(z_hi + zq + off), idesc, 1u);
+              mma_tf32(d2, sdesc_sw128(a_hi + off), sdesc_sw128(z_hi + zq + off), idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+          }
+        }
+        if (!ok) break;
+        mma_commit(zs_empty);
+      }
+    }
+    if (ok) mma_commit(d2_full);
+  } else if (warp >= 2) {
+    // ---- converter, then epilogue ----
+    const int quarter = warp & 3;
+    const int rl = quarter * 32 + lane;  // TMEM lane = row of the 128-row chunk
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    bool ok = true;
+    for (int u = 0; u < U && ok; ++u) {
+      if (!fwait(&d1_full[u & 1], (u >> 1) & 1, s_fail)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float v[BN];
+#pragma unroll
+      for (int c = 0; c < BN; c += 16) tmem_ld16(tmem + lane_base + (uint32_t)((R + (u & 1)) * BN + c), v + c);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d1_empty[u & 1]);
+      if (u >= 1 && !fwait(zs_empty, (u - 1) & 1, s_fail)) { ok = false; break; }
+      // Zs[c][r]: sub-tile q = r / 32, 128-byte row c, 16-byte chunk ((r % 32) / 4) ^ (c % 8)
+      unsigned char* zrow = zs + (rl >> 5) * C::TB_BYTES;
+      const int ch = (rl & 31) >> 2, w4 = (rl & 3) * 4;
+#pragma unroll
+      for (int c = 0; c < BN; ++c) {
+        const float h = tf32_round(v[c]);
+        const int off = c * 128 + ((ch ^ (c & 7)) << 4) + w4;
+        *(float*)(zrow + off) = h;
+        *(float*)(zrow + C::ZS_PLANE + off) = tf32_round(v[c] - h);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(zs_full);
+    }
+    if (ok && fwait(d2_full, 0, s_fail)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int t = 0; t < R; ++t) {
+        float v[BN];
+#pragma unroll
+        for (int c = 0; c < BN; c += 16) tmem_ld16(tmem + lane_base + (uint32_t)(t * BN + c), v + c);
+        const int a = t * 128 + rl;
+#pragma unroll
+        for (int c = 0; c < BN; ++c) J.Y[a + (size_t)(c0 + c) * n] = (double)v[c];
+      }
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*s_fail && threadIdx.x == 0) {
+    atomicExch(&g_tc_error, 1);
+    for (int s = 0; s < STAGES; ++s) mbar_wait(&full[s], 0);  // bounded drain of copies in flight
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Host side: plans (one per batched solve: tensor maps built once) and launches
 // ------------------------------------------------------------------------------------------
@@ -498,10 +746,29 @@ struct TCPlan {
   float* work = nullptr;  // Xt and Zt of every problem
   int njobs = 0, n = 0, kmax = 0;
   int prec = KPSB_P_TF32X3;
+  bool fused = false;
 };
 
 static constexpr int S1_BN = 128, S1_STAGES = 3;
 static constexpr int S2_BN = 64, S2_STAGES = 4;
+
+template <int BN, int FPL>
+static kpsb_status prepare_fused() {
+  KPSB_TRY_CUDA(cudaFuncSetAttribute(tc_fused_kernel<BN, FPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     FCfg<BN, FPL>::SMEM));
+  return KPSB_OK;
+}
+
+template <int BN, int FPL>
+static kpsb_status launch_fused(const TCJob* jobs, int njobs, int n, cudaStream_t st) {
+  dim3 grid((n + BN - 1) / BN, njobs);
+  tc_fused_kernel<BN, FPL><<<grid, 192, FCfg<BN, FPL>::SMEM, st>>>(jobs);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+// Fused kernel where its TMEM fits (R + 2) x BN columns: n <= 768 with BN = 64.
+static bool fused_ok(int n) { return n % 128 == 0 && (n / 128 + 2) * FUSED_BN <= 512 && !getenv("KPSB_TWO_STAGE"); }
 
 template <int BN, int STAGES, int STAGE, int FPL>
 static kpsb_status prepare_gemm() {
@@ -533,6 +800,11 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
     cuuint64_t s[3] = {fb * n, fb * n * n, fb * 2 * n * n};
     KPSB_TRY(make_map(&J.m1B, transpose ? T->T1t : T->T1f, 4, d, s, S1_BN));
   }
+  {  // T1 again with FUSED_BN-row boxes (fused kernel)
+    cuuint64_t d[4] = {(cuuint64_t)n, (cuuint64_t)n, 2, (cuuint64_t)k};
+    cuuint64_t s[3] = {fb * n, fb * n * n, fb * 2 * n * n};
+    KPSB_TRY(make_map(&J.m1F, transpose ? T->T1t : T->T1f, 4, d, s, FUSED_BN));
+  }
   {  // T2: {k n, n, 2}
     cuuint64_t d[3] = {(cuuint64_t)k * n, (cuuint64_t)n, 2};
     cuuint64_t s[2] = {fb * k * n, fb * (cuuint64_t)k * n * n};
@@ -554,10 +826,13 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
   KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 2>()));
   KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 1>()));
   KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 1>()));
+  KPSB_TRY((prepare_fused<FUSED_BN, 1>()));
+  KPSB_TRY((prepare_fused<FUSED_BN, 2>()));
   TCPlan* P = new TCPlan();
   P->njobs = njobs;
   P->n = n;
   P->prec = prec;
+  P->fused = fused_ok(n);
   std::vector<TCTables*> tabs(njobs);
   size_t floats = 0;
   for (int p = 0; p < njobs; ++p) {
@@ -628,6 +903,10 @@ kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
   dim3 gs((n / 32) * (n / 32), P->njobs);
   tc_split_kernel<<<gs, 256, 0, st>>>(jobs);
   KPSB_CHECK_LAUNCH();
+  if (P->fused) {
+    if (P->prec == KPSB_P_TF32X3) return launch_fused<FUSED_BN, 2>(jobs, P->njobs, n, st);
+    return launch_fused<FUSED_BN, 1>(jobs, P->njobs, n, st);
+  }
   if (P->prec == KPSB_P_TF32X3) {
     KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 2>(jobs, P->njobs, n, P->kmax, st)));
     KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 2>(jobs, P->njobs, n, P->kmax, st)));

@@ -227,3 +227,28 @@ def test_tensor_core_sb_isnr_within_0p1_db(prec_name):
     # the batched tensor-core solve equals the single one
     outs, st = K.sb_solve_batched([dict(kp=kp, b=b, mu=1.0, lam=0.1, tv=K.ISO, iters=15)] * 2, prec=prec)
     assert np.array_equal(outs[0], xtc) and np.array_equal(outs[1], xtc)
+
+
+@pytest.mark.parametrize("prec_name", ["P_TF32X3", "P_TF32X2"])
+def test_fused_and_two_stage_tensor_core_paths_agree(prec_name, monkeypatch):
+    """n <= 768 runs the fused kernel (Z kept in shared memory), larger n the two-stage
+    kernels; both compute the same split products, so they agree to accumulation-order
+    rounding, and both match the oracle."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    prec = getattr(K, prec_name)
+    for n, k in ((128, 7), (256, 3)):
+        Ax, Ay, sig = _rand_factors(n, k, 11 * n + k)
+        kp = K.kp_from_factors(Ax, Ay, sig)
+        X = I.rng(8).standard_normal((n, n))
+        ref = O.kp_apply(_oracle_op(Ax, Ay, sig), X)
+        yf = K.kp_apply(kp, X, 0, prec)
+        monkeypatch.setenv("KPSB_TWO_STAGE", "1")
+        kp2 = K.kp_from_factors(Ax, Ay, sig)
+        y2 = K.kp_apply(kp2, X, 0, prec)
+        monkeypatch.delenv("KPSB_TWO_STAGE")
+        tol = 1e-4 if prec == K.P_TF32X3 else 2e-3
+        assert np.linalg.norm(yf - ref) / np.linalg.norm(ref) < tol
+        assert np.linalg.norm(y2 - ref) / np.linalg.norm(ref) < tol
+        assert np.linalg.norm(yf - y2) / np.linalg.norm(ref) < 1e-4
