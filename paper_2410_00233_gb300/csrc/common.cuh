@@ -108,6 +108,32 @@ __device__ __forceinline__ bool last_block_arrive(unsigned int* counter, unsigne
   return s_last;
 }
 
+// Round to TF32 (10 explicit mantissa bits), to nearest with ties away from zero.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// The 1/2 forward-difference operators of the TV term on an n x n column-major image
+// (L with a zero last row): Dx = (L (x) I) acts along columns, Dy = (I (x) L) along rows.
+__device__ __forceinline__ double tv_dx(const double* X, int r, int c, int n) {  // (X L^T)(r,c)
+  return c < n - 1 ? 0.5 * (X[r + (size_t)c * n] - X[r + (size_t)(c + 1) * n]) : 0.0;
+}
+__device__ __forceinline__ double tv_dy(const double* X, int r, int c, int n) {  // (L X)(r,c)
+  return r < n - 1 ? 0.5 * (X[r + (size_t)c * n] - X[r + 1 + (size_t)c * n]) : 0.0;
+}
+__device__ __forceinline__ double tv_dxt(const double* Y, int r, int c, int n) {  // (Y L)(r,c)
+  double v = c < n - 1 ? 0.5 * Y[r + (size_t)c * n] : 0.0;
+  if (c >= 1) v -= 0.5 * Y[r + (size_t)(c - 1) * n];
+  return v;
+}
+__device__ __forceinline__ double tv_dyt(const double* Y, int r, int c, int n) {  // (L^T Y)(r,c)
+  double v = r < n - 1 ? 0.5 * Y[r + (size_t)c * n] : 0.0;
+  if (r >= 1) v -= 0.5 * Y[r - 1 + (size_t)c * n];
+  return v;
+}
+
 __device__ __forceinline__ int ext_index(int q, int n, int bc) {
   // Boundary extension: zero -> -1 for out-of-range; reflexive half-sample mirror.
   if (q >= 0 && q < n) return q;

@@ -189,7 +189,7 @@ extern "C" kpsb_status kp_apply_dev(kpsb_kp_t kp, const double* X, double* Y, in
   size_t zb = tc ? 0 : kp_z_bytes(n, k, prec);
   char* buf = nullptr;
   KPSB_TRY_CUDA(cudaMallocAsync((void**)&buf, zb + 256, st));
-  KPJob J;
+  KPJob J{};
   J.Ax = kp->Ax;
   J.Ay = kp->Ay;
   J.sigma = kp->sigma_d;

@@ -194,6 +194,7 @@ struct alignas(128) TCJob {
   float* Zt;         // [2][n][ldz]
   int n, k, ldz;
   const int* active;
+  float* Yf;         // when set (fused kernel): FP32 output instead of Y
 };
 
 // Tensor-core tables of one handle: [k][2][n][n] for stage 1, [2][n][k n] for stage 2,
@@ -719,8 +720,13 @@ __global__ void __launch_bounds__(192, 1) tc_fused_kernel(const TCJob* __restric
 #pragma unroll
         for (int c = 0; c < BN; c += 16) tmem_ld16(tmem + lane_base + (uint32_t)(t * BN + c), v + c);
         const int a = t * 128 + rl;
+        if (J.Yf) {  // FP32 result (the accumulation is FP32): no FP64 work in this kernel
 #pragma unroll
-        for (int c = 0; c < BN; ++c) J.Y[a + (size_t)(c0 + c) * n] = (double)v[c];
+          for (int c = 0; c < BN; ++c) J.Yf[a + (size_t)(c0 + c) * n] = v[c];
+        } else {
+#pragma unroll
+          for (int c = 0; c < BN; ++c) J.Y[a + (size_t)(c0 + c) * n] = (double)v[c];
+        }
       }
     }
   }
@@ -747,7 +753,10 @@ struct TCPlan {
   int njobs = 0, n = 0, kmax = 0;
   int prec = KPSB_P_TF32X3;
   bool fused = false;
+  bool ext_split = false;  // the caller writes the split planes (xt_ext)
 };
+
+bool tc_plan_fused(const TCPlan* P) { return P && P->fused; }
 
 static constexpr int S1_BN = 128, S1_STAGES = 3;
 static constexpr int S2_BN = 64, S2_STAGES = 4;
@@ -770,6 +779,8 @@ static kpsb_status launch_fused(const TCJob* jobs, int njobs, int n, cudaStream_
 // Fused kernel where its TMEM fits (R + 2) x BN columns: n <= 768 with BN = 64.
 static bool fused_ok(int n) { return n % 128 == 0 && (n / 128 + 2) * FUSED_BN <= 512 && !getenv("KPSB_TWO_STAGE"); }
 
+int tc_fused_tiles(int n, int prec) { return (tc_supported(n, prec) && fused_ok(n)) ? n / FUSED_BN : 0; }
+
 template <int BN, int STAGES, int STAGE, int FPL>
 static kpsb_status prepare_gemm() {
   using C = TCCfg<BN, STAGES, STAGE, FPL>;
@@ -789,6 +800,7 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
   J.k = k;
   J.ldz = k * n;
   J.active = src.active;
+  J.Yf = src.yf;
   const cuuint64_t fb = sizeof(float);
   {  // Xt: {n, n, 2}
     cuuint64_t d[3] = {(cuuint64_t)n, (cuuint64_t)n, 2};
@@ -842,7 +854,7 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
       return s;
     }
     P->kmax = std::max(P->kmax, kps[p]->k);
-    floats += (size_t)2 * n * n + (size_t)2 * n * kps[p]->k * n;
+    floats += (fwd_h[p].xt_ext ? 0 : (size_t)2 * n * n) + (size_t)2 * n * kps[p]->k * n;
   }
   cudaError_t e = cudaMallocAsync((void**)&P->work, sizeof(float) * floats + 2 * sizeof(TCJob) * njobs + 256, st);
   if (e != cudaSuccess) {
@@ -852,9 +864,13 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
   }
   std::vector<TCJob> hf(njobs), hb(njobs);
   float* q = P->work;
+  P->ext_split = njobs > 0 && fwd_h[0].xt_ext != nullptr;
   for (int p = 0; p < njobs; ++p) {
-    float* Xt = q;
-    q += (size_t)2 * n * n;
+    float* Xt = fwd_h[p].xt_ext;
+    if (!Xt) {
+      Xt = q;
+      q += (size_t)2 * n * n;
+    }
     float* Zt = q;
     q += (size_t)2 * n * kps[p]->k * n;
     kpsb_status s = fill_job(hf[p], fwd_h[p], tabs[p], 0, Xt, Zt);
@@ -900,9 +916,11 @@ static kpsb_status launch_gemm(const TCJob* jobs, int njobs, int n, int kmax, cu
 kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
   const TCJob* jobs = transpose ? P->d_bwd : P->d_fwd;
   const int n = P->n;
-  dim3 gs((n / 32) * (n / 32), P->njobs);
-  tc_split_kernel<<<gs, 256, 0, st>>>(jobs);
-  KPSB_CHECK_LAUNCH();
+  if (!P->ext_split) {
+    dim3 gs((n / 32) * (n / 32), P->njobs);
+    tc_split_kernel<<<gs, 256, 0, st>>>(jobs);
+    KPSB_CHECK_LAUNCH();
+  }
   if (P->fused) {
     if (P->prec == KPSB_P_TF32X3) return launch_fused<FUSED_BN, 2>(jobs, P->njobs, n, st);
     return launch_fused<FUSED_BN, 1>(jobs, P->njobs, n, st);

@@ -72,6 +72,9 @@ struct SBProb {
   SBScal* sc;
   double* part;           // reduction partials
   unsigned int* counter;  // last-block counter
+  float* xt;              // split TF32 planes of the next KP apply's input (tensor-core path)
+  float* z1f;             // FP32 KP-apply results (fused tensor-core path), else null
+  float* f1f;
 };
 // Device-resident state of one problem; persists across sb_advance calls.
 struct SBState {
@@ -120,6 +123,9 @@ struct KPJob {
   double* Y;           // output n x n FP64
   void* Z;             // intermediate: k x n x n (FP64 or FP32 by precision)
   const int* active;   // skip when *active == 0 (may be null)
+  // Tensor-core path only (zero for a plain apply):
+  float* xt_ext;       // caller-maintained split planes of X ([2][n][n] row-major), or null
+  float* yf;           // fused kernel: write the result in FP32 here instead of Y
 };
 // Y = sum sigma_i Ay_i X Ax_i^T (transpose 0) / sum sigma_i Ay_i^T X Ax_i (transpose 1)
 // for every job (all with the same n).  jobs_d: device copy of the descriptors.
@@ -135,6 +141,10 @@ void tc_free(TCTables* t);
 kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h, int njobs, int n,
                            int prec, cudaStream_t st, TCPlan** out);
 kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st);
+// True when the plan runs the fused kernel with CGLS epilogues (inputs split by the caller).
+bool tc_plan_fused(const TCPlan* P);
+// Column tiles of the fused kernel for size n, 0 if n is not handled by it.
+int tc_fused_tiles(int n, int prec);
 void tc_plan_free(TCPlan* P, cudaStream_t st);
 kpsb_status tc_check_error();
 kpsb_status tc_apply_batch(kpsb_kp** kps, const KPJob* jobs_d, const KPJob* jobs_h, int njobs,

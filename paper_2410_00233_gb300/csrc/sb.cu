@@ -32,22 +32,10 @@ struct SBScal {
   int pad;
 };
 
-__device__ __forceinline__ double dx_at(const double* X, int r, int c, int n) {  // (X L^T)(r,c)
-  return c < n - 1 ? 0.5 * (X[r + (size_t)c * n] - X[r + (size_t)(c + 1) * n]) : 0.0;
-}
-__device__ __forceinline__ double dy_at(const double* X, int r, int c, int n) {  // (L X)(r,c)
-  return r < n - 1 ? 0.5 * (X[r + (size_t)c * n] - X[r + 1 + (size_t)c * n]) : 0.0;
-}
-__device__ __forceinline__ double dxt_at(const double* Y, int r, int c, int n) {  // (Y L)(r,c)
-  double v = c < n - 1 ? 0.5 * Y[r + (size_t)c * n] : 0.0;
-  if (c >= 1) v -= 0.5 * Y[r + (size_t)(c - 1) * n];
-  return v;
-}
-__device__ __forceinline__ double dyt_at(const double* Y, int r, int c, int n) {  // (L^T Y)(r,c)
-  double v = r < n - 1 ? 0.5 * Y[r + (size_t)c * n] : 0.0;
-  if (r >= 1) v -= 0.5 * Y[r - 1 + (size_t)c * n];
-  return v;
-}
+#define dx_at tv_dx
+#define dy_at tv_dy
+#define dxt_at tv_dxt
+#define dyt_at tv_dyt
 
 __device__ __forceinline__ int sb_blocks(int n) {
   int b = ((n * n) + SB_T * 4 - 1) / (SB_T * 4);
@@ -122,7 +110,8 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_f_kernel(const SBProb* __restric
   double ss = 0.0;
   for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
     int r = (int)(e % n), c = (int)(e / n);
-    double v = P.sqrt_mu * P.f1[e] + P.lam * (dxt_at(P.r2, r, c, n) + dyt_at(P.r3, r, c, n));
+    const double f1 = P.f1f ? (double)P.f1f[e] : P.f1[e];
+    double v = P.sqrt_mu * f1 + P.lam * (dxt_at(P.r2, r, c, n) + dyt_at(P.r3, r, c, n));
     P.f[e] = v;
     ss = fma(v, v, ss);
   }
@@ -141,12 +130,13 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_f_kernel(const SBProb* __restric
   }
 }
 
-// w = f + delta w (step 10).
-__global__ void __launch_bounds__(SB_T) sb_cgls_w_kernel(const SBProb* __restrict__ probs) {
+// w = f + delta w (step 10); init: w = f (step 2).  The start does not read w, which holds
+// no value yet: 0 * w would turn leftover non-finite bytes into NaN.
+__global__ void __launch_bounds__(SB_T) sb_cgls_w_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
   const double dl = P.sc->delta;
   for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride)
-    P.w[e] = fma(dl, P.w[e], P.f[e]);
+    P.w[e] = init ? P.f[e] : fma(dl, P.w[e], P.f[e]);
 }
 
 // ||z||^2 with z = Ahat w = [sqrt(mu) z1; lam Dx w; lam Dy w] (steps 3-4).
@@ -155,7 +145,8 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_zz_kernel(const SBProb* __restri
   double ss = 0.0;
   for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
     int r = (int)(e % n), c = (int)(e / n);
-    double a = P.sqrt_mu * P.z1[e], bx = P.lam * dx_at(P.w, r, c, n), by = P.lam * dy_at(P.w, r, c, n);
+    const double z = P.z1f ? (double)P.z1f[e] : P.z1[e];
+    double a = P.sqrt_mu * z, bx = P.lam * dx_at(P.w, r, c, n), by = P.lam * dy_at(P.w, r, c, n);
     ss = fma(a, a, fma(bx, bx, fma(by, by, ss)));
   }
   double tot[2];
@@ -233,6 +224,125 @@ __global__ void __launch_bounds__(SB_T) sb_shrink_kernel(const SBProb* __restric
     s->rc_sb = tot[1] > 0.0 ? sqrt(tot[0]) / sqrt(tot[1]) : INFINITY;
     s->l_end += 1;
     if (s->l_end >= P.iters || s->rc_sb < P.tau_sb) s->sb_active = 0;
+  }
+}
+
+
+// ---- tensor-core variant of the CGLS vector steps ---------------------------------------------
+// With the fused tensor-core KP apply the GEMM epilogues already produce z1 and the pieces
+// of |z|^2 (forward) and f with |f|^2 (transpose).  The kernels below finish each step and
+// write the split TF32 planes Xt (row-major, Xt[r][m] = X(r, m), hi then lo) of the next
+// apply's input themselves, working on 32 x 32 tiles so both the column-major vectors and
+// the transposed planes are written coalesced.
+#define SB_TILES_BEGIN                                                   \
+  const int tn = n >> 5, ntile = tn * tn, nblk = sb_blocks(n);           \
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;                \
+  for (int t = blockIdx.x; t < ntile; t += nblk) {                       \
+    const int tr = t % tn, tcol = t / tn;
+#define SB_TILES_END }
+
+// Store the tile held in th/tl (th[col][row] of the tile) as rows of the Xt planes.
+__device__ __forceinline__ void store_xt_tile(float* __restrict__ xt, int n, int tr, int tcol,
+                                              float (*th)[33], float (*tl)[33], int lx, int ly) {
+  __syncthreads();
+  const size_t nn = (size_t)n * n;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = tr * 32 + ly + 8 * j, m = tcol * 32 + lx;
+    xt[(size_t)r * n + m] = th[lx][ly + 8 * j];
+    xt[nn + (size_t)r * n + m] = tl[lx][ly + 8 * j];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void put_split(float (*th)[33], float (*tl)[33], int a, int b, double v) {
+  const float f = (float)v;
+  const float h = tf32_rna(f);
+  th[a][b] = h;
+  tl[a][b] = tf32_rna(f - h);
+}
+
+// Outer step start (as sb_outer_init_kernel) plus the split planes of r1 = sqrt(mu) b.
+__global__ void __launch_bounds__(SB_T) sb_outer_init_tc_kernel(const SBProb* __restrict__ probs) {
+  SB_PROLOGUE(P.sc->sb_active)
+  (void)N; (void)stride;
+  __shared__ float th[32][33], tl[32][33];
+  SB_TILES_BEGIN
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = tr * 32 + lx, c = tcol * 32 + ly + 8 * j;
+    const size_t e = r + (size_t)c * n;
+    P.xprev[e] = P.x[e];
+    P.x[e] = 0.0;
+    const double r1 = P.sqrt_mu * P.b[e];
+    P.r1[e] = r1;
+    P.r2[e] = P.lam * (P.dx[e] - P.gx[e]);
+    P.r3[e] = P.lam * (P.dy[e] - P.gy[e]);
+    put_split(th, tl, ly + 8 * j, lx, r1);
+  }
+  store_xt_tile(P.xt, n, tr, tcol, th, tl, lx, ly);
+  SB_TILES_END
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.sc->active = 1;
+    P.sc->it = 0;
+  }
+}
+
+// w = f + delta w (step 10; delta from the f kernel), init: w = f (step 2, w not read), and
+// the planes of w for the next forward apply.
+__global__ void __launch_bounds__(SB_T) sb_w_tc_kernel(const SBProb* __restrict__ probs, int init) {
+  SB_PROLOGUE(P.sc->active)
+  (void)N; (void)stride;
+  __shared__ float th[32][33], tl[32][33];
+  const double dl = P.sc->delta;
+  SB_TILES_BEGIN
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = tr * 32 + lx, c = tcol * 32 + ly + 8 * j;
+    const size_t e = r + (size_t)c * n;
+    const double w = init ? P.f[e] : fma(dl, P.w[e], P.f[e]);
+    P.w[e] = w;
+    put_split(th, tl, ly + 8 * j, lx, w);
+  }
+  store_xt_tile(P.xt, n, tr, tcol, th, tl, lx, ly);
+  SB_TILES_END
+}
+
+// x += mu w, r -= mu z (steps 5-6, mu from the zz kernel); RC_CGLS (5.1) and the stop
+// test; the planes of r1 for the transpose apply.
+__global__ void __launch_bounds__(SB_T) sb_x_tc_kernel(const SBProb* __restrict__ probs) {
+  SB_PROLOGUE(P.sc->active)
+  (void)N; (void)stride;
+  __shared__ float th[32][33], tl[32][33];
+  const double mu = P.sc->step;
+  double sx = 0.0, sw = 0.0;
+  SB_TILES_BEGIN
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = tr * 32 + lx, c = tcol * 32 + ly + 8 * j;
+    const size_t e = r + (size_t)c * n;
+    const double w = P.w[e];
+    const double xn = fma(mu, w, P.x[e]);
+    P.x[e] = xn;
+    const double r1 = P.r1[e] - mu * (P.sqrt_mu * (double)P.z1f[e]);
+    P.r1[e] = r1;
+    P.r2[e] -= mu * (P.lam * dx_at(P.w, r, c, n));
+    P.r3[e] -= mu * (P.lam * dy_at(P.w, r, c, n));
+    sx = fma(xn, xn, sx);
+    sw = fma(w, w, sw);
+    put_split(th, tl, ly + 8 * j, lx, r1);
+  }
+  store_xt_tile(P.xt, n, tr, tcol, th, tl, lx, ly);
+  SB_TILES_END
+  double tot[2];
+  if (!prob_reduce2(P, sx, sw, tot)) return;
+  if (threadIdx.x == 0) {
+    SBScal* s = P.sc;
+    const double xn = sqrt(tot[0]);
+    s->rc_cgls = xn > 0.0 ? mu * sqrt(tot[1]) / xn : INFINITY;
+    s->it += 1;
+    s->iota_total += 1;
+    if (s->it >= P.i_max || (!P.fixed_inner && s->rc_cgls < P.tau_cgls)) s->active = 0;
   }
 }
 
@@ -363,7 +473,7 @@ size_t sb_state_bytes(int n, int k, int prec) {
   const size_t zbytes = tc_supported(n, gp) ? 0 : a256(kp_z_bytes(n, k, gp));
   size_t tc_ws = tc_supported(n, gp) ? a256(sizeof(float) * ((size_t)2 * N + (size_t)2 * n * k * n)) : 0;
   return a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
-         a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256 + tc_ws;
+         a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256 + tc_ws + a256(sizeof(float) * 4 * N) + 256;
 }
 
 kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* x_dev, double mu,
@@ -377,8 +487,10 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   S->gemm_prec = gemm_prec_for(n, o.prec);
   S->initialized = false;
   const size_t zbytes = tc_supported(n, S->gemm_prec) ? 0 : a256(kp_z_bytes(n, kp->k, S->gemm_prec));
+  const bool fused = tc_fused_tiles(n, S->gemm_prec) > 0;
+  const size_t xtbytes = fused ? a256(sizeof(float) * 4 * N) : 0;  // Xt planes + z1f + f1f
   S->bytes = a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
-             a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256;
+             a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256 + xtbytes;
   KPSB_TRY_CUDA(cudaMallocAsync((void**)&S->mem, S->bytes, st));
   char* q = S->mem;
   double* v = (double*)q;
@@ -406,7 +518,13 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   P.part = (double*)q;
   q += a256(sizeof(double) * SB_MAX_BLOCKS * 2);
   P.counter = (unsigned int*)q;
-  KPSB_TRY_CUDA(cudaMemsetAsync(P.counter, 0, sizeof(unsigned int), st));
+  q += 256;
+  P.xt = fused ? (float*)q : nullptr;
+  P.z1f = fused ? P.xt + 2 * N : nullptr;
+  P.f1f = fused ? P.xt + 3 * N : nullptr;
+  // the block comes from the stream-ordered pool with whatever its last user left: clear it
+  // all, so that no read of a not-yet-written vector can depend on that history
+  KPSB_TRY_CUDA(cudaMemsetAsync(S->mem, 0, S->bytes, st));
   return KPSB_OK;
 }
 
@@ -457,6 +575,9 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
   for (int p = 0; p < P; ++p) kmax = std::max(kmax, set[p]->kp->k);
   const int gemm_prec = gemm_prec_for(n, o.prec);
   const bool tc = tc_supported(n, gemm_prec);
+  // fused CGLS variant: every state carries split planes and epilogue partials
+  bool fz = tc && tc_fused_tiles(n, gemm_prec) > 0;
+  for (int p = 0; p < count; ++p) fz = fz && set[p]->prob.xt != nullptr;
   const size_t small = a256(sizeof(SBProb) * P) * 2 + 2 * a256(sizeof(KPJob) * P) + 256;
   char* base = nullptr;
   KPSB_TRY_CUDA(cudaMallocAsync((void**)&base, small, st));
@@ -475,6 +596,11 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     KPJob& B = bwd[p];
     B = F;
     B.X = S->prob.r1; B.Y = S->prob.f1;
+    if (fz) {  // fused kernel: inputs split by the vector kernels, FP32 results
+      F.xt_ext = B.xt_ext = S->prob.xt;
+      F.yf = S->prob.z1f;
+      B.yf = S->prob.f1f;
+    }
   }
   SBProb* dprobs = (SBProb*)base;
   SBProb* dnew = (SBProb*)(base + a256(sizeof(SBProb) * P));
@@ -505,7 +631,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     for (int p = 0; p < P; ++p) ksum += set[p]->kp->k;
     const double apply_flops = 4.0 * ksum * (double)n * n * n;  // 4 k n^3 per problem (Sec. 4.2)
     if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, gemm_prec, st, &plan))) break;
-    const int apply_launches = tc ? 3 : 2;
+    const int apply_launches = tc ? (fz ? 1 : 3) - (tc && !fz && tc_plan_fused(plan) ? 1 : 0) : 2;
     const bool timed = gemm_timing_enabled();
     // One KP apply of the whole batch on stream sx (timed with events in instrumented mode).
     auto kp_apply_on = [&](int transpose, cudaStream_t sx) -> kpsb_status {
@@ -517,17 +643,40 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     };
     // Head of an outer step: x_prev = x, CGLS start r = bhat, f = Ahat^T r, w = f.
     auto outer_head = [&](cudaStream_t sx) -> kpsb_status {
+      if (fz) {
+        sb_outer_init_tc_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+        KPSB_CHECK_LAUNCH();
+        KPSB_TRY(kp_apply_on(1, sx));
+        sb_cgls_f_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 1);
+        KPSB_CHECK_LAUNCH();
+        sb_w_tc_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 1);
+        KPSB_CHECK_LAUNCH();
+        return KPSB_OK;
+      }
       sb_outer_init_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
       KPSB_CHECK_LAUNCH();
       KPSB_TRY(kp_apply_on(1, sx));
       sb_cgls_f_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 1);
       KPSB_CHECK_LAUNCH();
-      sb_cgls_w_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+      sb_cgls_w_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 1);
       KPSB_CHECK_LAUNCH();
       return KPSB_OK;
     };
     // One CGLS iteration (Alg. 5 steps 3-10) of every active problem.
     auto cgls_iter = [&](cudaStream_t sx) -> kpsb_status {
+      if (fz) {
+        KPSB_TRY(kp_apply_on(0, sx));
+        sb_cgls_zz_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+        KPSB_CHECK_LAUNCH();
+        sb_x_tc_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+        KPSB_CHECK_LAUNCH();
+        KPSB_TRY(kp_apply_on(1, sx));
+        sb_cgls_f_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 0);
+        KPSB_CHECK_LAUNCH();
+        sb_w_tc_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 0);
+        KPSB_CHECK_LAUNCH();
+        return KPSB_OK;
+      }
       KPSB_TRY(kp_apply_on(0, sx));
       sb_cgls_zz_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
       KPSB_CHECK_LAUNCH();
@@ -536,7 +685,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
       KPSB_TRY(kp_apply_on(1, sx));
       sb_cgls_f_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 0);
       KPSB_CHECK_LAUNCH();
-      sb_cgls_w_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
+      sb_cgls_w_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 0);
       KPSB_CHECK_LAUNCH();
       return KPSB_OK;
     };
@@ -549,7 +698,8 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
       // Production path: the whole advance is one CUDA graph; each outer step's CGLS loop
       // is a device-side WHILE node, so no host round trip happens until the end.
       s = sb_graph_run(st, gv, dprobs, P, outer_steps, o.i_max, ctrs, outer_head, cgls_iter, shrink,
-                       3 + apply_launches, 4 + 2 * apply_launches);
+                       fz ? 3 + apply_launches : 3 + apply_launches,
+                       fz ? 4 + 2 * apply_launches : 4 + 2 * apply_launches);
       if (s) break;
     } else {
       // Instrumented path: host-driven loop (CUDA events around every KP apply), checking

@@ -252,3 +252,66 @@ def test_fused_and_two_stage_tensor_core_paths_agree(prec_name, monkeypatch):
         assert np.linalg.norm(yf - ref) / np.linalg.norm(ref) < tol
         assert np.linalg.norm(y2 - ref) / np.linalg.norm(ref) < tol
         assert np.linalg.norm(yf - y2) / np.linalg.norm(ref) < 1e-4
+
+
+def test_lambda_sweep_on_shared_factors_equals_single_solves():
+    """Parameter sweep (Sec. 5.3.1): many lambda values (beta = lambda^2 / gamma, gamma = 2)
+    solved together on one set of KP factors; each equals its own solve."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    x_true, b, Ax, Ay, sig = _problem(32, seed=21)
+    kp = K.kp_from_factors(Ax, Ay, sig)
+    lams = np.logspace(-2, 1, 6)
+    jobs = [dict(kp=kp, b=b, mu=1.0, lam=float(l), tv=K.ANISO, iters=4) for l in lams]
+    outs, stats = K.sb_solve_batched(jobs)
+    for l, x, st in zip(lams, outs, stats):
+        xa, sa = K.sb_solve(kp, b, 1.0, float(l), K.ANISO, 4)
+        assert np.array_equal(x, xa) and st.iota_total == sa.iota_total
+
+
+def test_uneven_batch_equals_alone():
+    """Problems of several sizes (and GEMM paths: n = 64 on CUDA cores, n = 128 / 256 on the
+    tensor cores) in one batched call, each equal to its solve alone."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    jobs, alone = [], []
+    for i, n in enumerate((64, 128, 256, 128, 64)):
+        pr = I.problem_batched(i * 4 + (0 if n == 64 else 1 if n == 128 else 2))
+        assert pr.n == n
+        bt = O.blur(pr.psf, pr.x_true, pr.bc)
+        b = bt + I.noise_vector(bt, pr.eta, pr.zeta)
+        kp = K.kp_build(pr.psf, n, pr.bc, pr.k, K.EGKB, p=pr.p, seed=pr.seed)
+        tv = K.ISO if pr.iso else K.ANISO
+        x, st = K.sb_solve(kp, b, 1.0, 0.1, tv, 3, prec=K.P_TF32X2)
+        alone.append((x, st))
+        jobs.append(dict(kp=kp, b=b, mu=1.0, lam=0.1, tv=tv, iters=3))
+    outs, stats = K.sb_solve_batched(jobs, prec=K.P_TF32X2)
+    report = [(x.shape[0], float(np.linalg.norm(x)), st.iota_total, float(np.linalg.norm(xb)),
+               sb.iota_total, sb.l_end) for (x, st), xb, sb in zip(alone, outs, stats)]
+    for (x, st), xb, sb in zip(alone, outs, stats):
+        assert np.array_equal(x, xb) and st.iota_total == sb.iota_total, report
+
+
+def test_solve_independent_of_allocator_history():
+    """A solve whose state reuses device memory that held NaNs (left by a KP apply of a NaN
+    image) returns the same result as the first solve: no step reads a vector before it is
+    written (Alg. 5 starts from w = f, not from f + 0 w)."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    for n, prec in ((64, K.P_FP32), (128, K.P_TF32X2), (48, K.P_FP64)):
+        x_true, b, Ax, Ay, sig = _problem(n, seed=5 + n)
+        kp = K.kp_from_factors(Ax, Ay, sig)
+        x1, s1 = K.sb_solve(kp, b, 1.0, 0.1, K.ISO, 3, prec=prec)
+        nan = np.full((n, n), np.nan)
+        for _ in range(3):
+            K.kp_apply(kp, nan, 0, K.P_FP64)
+            K.kp_apply(kp, nan, 1, prec)
+        outs, st = K.sb_solve_batched([dict(kp=kp, b=b, mu=1.0, lam=0.1, tv=K.ISO, iters=3)] * 3, prec=prec)
+        x2, s2 = K.sb_solve(kp, b, 1.0, 0.1, K.ISO, 3, prec=prec)
+        assert np.all(np.isfinite(x1)) and s1.iota_total > 0
+        assert np.array_equal(x1, x2) and s1.iota_total == s2.iota_total
+        for xb, sb in zip(outs, st):
+            assert np.array_equal(x1, xb) and sb.iota_total == s1.iota_total
