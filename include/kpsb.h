@@ -275,11 +275,19 @@ void srv_destroy(kpsb_server_t s);
 unsigned long long kpsb_kernel_launches(void);
 /* enable = 1: clear the totals and record a CUDA event pair, on the launching stream,
  * around every Kronecker-sum GEMM apply (two kernel launches on the CUDA-core path, one
- * on the tensor-core path) until called with enable = 0. */
+ * on the tensor-core path) and every split Bregman vector kernel, until called with
+ * enable = 0.  While enabled, split Bregman runs its host-driven loop instead of one
+ * CUDA graph (same kernels, same results). */
 kpsb_status kpsb_gemm_timing(int enable);
 /* Totals of the recorded applies (waits for their events): kernel launches, summed
  * device milliseconds, and algorithmic flops (4 k n^3 per problem per apply, Sec. 4.2). */
 kpsb_status kpsb_gemm_stats(unsigned long long* launches, double* ms, double* flops);
+/* Totals of one timer category (same meaning as kpsb_gemm_stats; flops 0 for the vector
+ * kernels): 0 KP applies, 1 CGLS ||z||^2 (Alg. 5 steps 3-4), 2 x and r updates with
+ * RC_CGLS (steps 5-6), 3 f = Ahat^T r and tau (steps 7-9), 4 w = f + delta w (step 10),
+ * 5 outer-step kernels (CGLS start, shrinkage of Alg. 3/4).  KPSB_EINVAL for another
+ * category. */
+kpsb_status kpsb_timer_stats(int category, unsigned long long* launches, double* ms, double* flops);
 
 /* Thread-local message for the last error of this thread ("" if none). */
 const char* kpsb_last_error(void);

@@ -21,7 +21,19 @@ void clear_error();
 void count_launch(long long n = 1);
 void set_capture_mode(bool on);
 bool gemm_timing_enabled();
-// CUDA-event timing of the Kronecker-sum GEMM launches (kpsb_gemm_timing / _stats).
+// CUDA-event timing (kpsb_gemm_timing / kpsb_timer_stats) by category: the
+// Kronecker-sum GEMM applies and the split Bregman vector kernels.
+enum TimerCategory {
+  TIMER_KP_APPLY = 0,  // one KP apply of a batch
+  TIMER_SB_ZZ = 1,     // ||z||^2 (CGLS steps 3-4)
+  TIMER_SB_X = 2,      // x, r updates and RC_CGLS (steps 5-6)
+  TIMER_SB_F = 3,      // f = Ahat^T r and its norm (steps 7-9)
+  TIMER_SB_W = 4,      // w = f + delta w (step 10)
+  TIMER_SB_OUTER = 5,  // outer-step kernels: start of an outer step, shrinkage
+  TIMER_CATEGORIES = 6
+};
+int timer_begin(cudaStream_t st);
+void timer_end(int slot, cudaStream_t st, int cat, double flops, int launches);
 int gemm_timer_begin(cudaStream_t st);
 void gemm_timer_end(int slot, cudaStream_t st, double flops, int launches);
 

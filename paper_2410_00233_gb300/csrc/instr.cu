@@ -1,5 +1,6 @@
 // Instrumentation: process-wide kernel-launch counter and CUDA-event timing of the
-// Kronecker-sum GEMM launches (recorded on the stream each apply runs on).
+// Kronecker-sum GEMM applies and of the split Bregman vector kernels (recorded on the
+// stream each one runs on, by category).
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -23,6 +24,7 @@ struct TimerRec {
   cudaEvent_t a = nullptr, b = nullptr;
   double flops = 0.0;
   int launches = 0;
+  int cat = 0;
   bool used = false;
 };
 std::mutex g_tm;
@@ -36,7 +38,7 @@ bool gemm_timing_enabled() {
   return g_timing;
 }
 
-int gemm_timer_begin(cudaStream_t st) {
+int timer_begin(cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_tm);
   if (!g_timing) return -1;
   if (g_next == g_recs.size()) {
@@ -49,7 +51,9 @@ int gemm_timer_begin(cudaStream_t st) {
   return slot;
 }
 
-void gemm_timer_end(int slot, cudaStream_t st, double flops, int launches) {
+int gemm_timer_begin(cudaStream_t st) { return timer_begin(st); }
+
+void timer_end(int slot, cudaStream_t st, int cat, double flops, int launches) {
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_tm);
   if (slot >= (int)g_recs.size()) return;
@@ -57,7 +61,12 @@ void gemm_timer_end(int slot, cudaStream_t st, double flops, int launches) {
   cudaEventRecord(r.b, st);
   r.flops = flops;
   r.launches = launches;
+  r.cat = cat;
   r.used = true;
+}
+
+void gemm_timer_end(int slot, cudaStream_t st, double flops, int launches) {
+  timer_end(slot, st, TIMER_KP_APPLY, flops, launches);
 }
 
 }  // namespace kpsb
@@ -77,14 +86,16 @@ extern "C" kpsb_status kpsb_gemm_timing(int enable) {
   return KPSB_OK;
 }
 
-extern "C" kpsb_status kpsb_gemm_stats(unsigned long long* launches, double* ms, double* flops) {
+extern "C" kpsb_status kpsb_timer_stats(int category, unsigned long long* launches, double* ms,
+                                        double* flops) {
   clear_error();
+  KPSB_REQUIRE(category >= 0 && category < TIMER_CATEGORIES, "unknown timer category %d", category);
   std::lock_guard<std::mutex> lk(g_tm);
   unsigned long long L = 0;
   double T = 0.0, F = 0.0;
   for (size_t i = 0; i < g_next && i < g_recs.size(); ++i) {
     TimerRec& r = g_recs[i];
-    if (!r.used) continue;
+    if (!r.used || r.cat != category) continue;
     KPSB_TRY_CUDA(cudaEventSynchronize(r.b));
     float t = 0.f;
     KPSB_TRY_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
@@ -96,4 +107,8 @@ extern "C" kpsb_status kpsb_gemm_stats(unsigned long long* launches, double* ms,
   if (ms) *ms = T;
   if (flops) *flops = F;
   return KPSB_OK;
+}
+
+extern "C" kpsb_status kpsb_gemm_stats(unsigned long long* launches, double* ms, double* flops) {
+  return kpsb_timer_stats(TIMER_KP_APPLY, launches, ms, flops);
 }

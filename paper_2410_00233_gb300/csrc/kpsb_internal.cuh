@@ -66,7 +66,7 @@ struct TCTables;  // tensor-core operand tables (kpgemm_tc.cu)
 struct SBScal;
 struct SBProb {
   int n, iters, iso, fixed_inner, i_max;
-  double sqrt_mu, lam, thr, tau_cgls, tau_sb;
+  double mu, sqrt_mu, lam, thr, tau_cgls, tau_sb;
   const double* b;
   double *x, *xprev, *w, *f, *r1, *r2, *r3, *z1, *f1, *dx, *dy, *gx, *gy;
   SBScal* sc;

@@ -16,7 +16,12 @@
 namespace kpsb {
 
 static constexpr int SB_T = 256;
-static constexpr int SB_MAX_BLOCKS = 64;  // blocks per problem in the vector kernels
+// Each block of a vector kernel handles one fixed chunk of SB_CHUNK elements (SB_EPT per
+// thread) and writes one reduction partial: the summation order depends on n only, so a
+// problem gives the same bits alone, in any batch, and in the serving loop.
+static constexpr int SB_EPT = 16;
+static constexpr int SB_CHUNK = SB_T * SB_EPT;
+static constexpr int SB_TILES_PER_CHUNK = SB_CHUNK / 1024;  // 32 x 32 tiles
 
 struct SBScal {
   double tau;      // ||f||^2 of the current direction
@@ -34,12 +39,9 @@ struct SBScal {
 
 #define dx_at tv_dx
 #define dy_at tv_dy
-#define dxt_at tv_dxt
-#define dyt_at tv_dyt
 
-__device__ __forceinline__ int sb_blocks(int n) {
-  int b = ((n * n) + SB_T * 4 - 1) / (SB_T * 4);
-  return b < SB_MAX_BLOCKS ? (b < 1 ? 1 : b) : SB_MAX_BLOCKS;
+__host__ __device__ __forceinline__ int sb_blocks(int n) {
+  return (int)(((long long)n * n + SB_CHUNK - 1) / SB_CHUNK);
 }
 
 // Two-value fixed-order grid reduction inside one problem; returns true in the last block
@@ -66,18 +68,21 @@ __device__ __forceinline__ bool prob_reduce2(const SBProb& P, double a, double b
   return true;
 }
 
-#define SB_PROLOGUE(cond)                                      \
-  const SBProb P = probs[blockIdx.y];                          \
-  if ((int)blockIdx.x >= sb_blocks(P.n)) return;               \
-  if (!(cond)) return;                                         \
-  const int n = P.n;                                           \
-  const long long N = (long long)n * n;                        \
-  const long long stride = (long long)sb_blocks(n) * SB_T;
+#define SB_PROLOGUE(cond)                                            \
+  const SBProb P = probs[blockIdx.y];                                \
+  if ((int)blockIdx.x >= sb_blocks(P.n)) return;                     \
+  if (!(cond)) return;                                               \
+  const int n = P.n;                                                 \
+  const long long N = (long long)n * n;                              \
+  const long long e_lo = (long long)blockIdx.x * SB_CHUNK;           \
+  const long long e_hi = e_lo + SB_CHUNK < N ? e_lo + SB_CHUNK : N;
+// The elements of this block's chunk, SB_T apart.
+#define SB_FOR_E for (long long e = e_lo + threadIdx.x; e < e_hi; e += SB_T)
 
 // x^(0) = b, d = g = 0, flags set (Alg. 3/4 initialisation).
 __global__ void __launch_bounds__(SB_T) sb_setup_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(true)
-  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
+  SB_FOR_E {
     P.x[e] = P.b[e];
     P.dx[e] = P.dy[e] = P.gx[e] = P.gy[e] = 0.0;
   }
@@ -90,7 +95,7 @@ __global__ void __launch_bounds__(SB_T) sb_setup_kernel(const SBProb* __restrict
 // Outer step start: xprev = x; CGLS from x = 0 with r = bhat = [sqrt(mu) b; lam(dx-gx); lam(dy-gy)].
 __global__ void __launch_bounds__(SB_T) sb_outer_init_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->sb_active)
-  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
+  SB_FOR_E {
     P.xprev[e] = P.x[e];
     P.x[e] = 0.0;
     P.r1[e] = P.sqrt_mu * P.b[e];
@@ -107,11 +112,17 @@ __global__ void __launch_bounds__(SB_T) sb_outer_init_kernel(const SBProb* __res
 // tau' = ||f||^2 (step 8); delta = tau'/tau (step 9).  init: tau = tau', delta = 0.
 __global__ void __launch_bounds__(SB_T) sb_cgls_f_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
+  // Dx^T r2 + Dy^T r3 = (lambda/2) t with t the raw differences (L = half forward difference,
+  // zero last row); one coefficient per term keeps the FP64 operation count low.
+  const double hl = 0.5 * P.lam;
   double ss = 0.0;
-  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
-    int r = (int)(e % n), c = (int)(e / n);
+  SB_FOR_E {
+    const int r = (int)(e % n), c = (int)(e / n);
     const double f1 = P.f1f ? (double)P.f1f[e] : P.f1[e];
-    double v = P.sqrt_mu * f1 + P.lam * (dxt_at(P.r2, r, c, n) + dyt_at(P.r3, r, c, n));
+    double t = (c < n - 1 ? P.r2[e] : 0.0) + (r < n - 1 ? P.r3[e] : 0.0);
+    if (c >= 1) t -= P.r2[e - n];
+    if (r >= 1) t -= P.r3[e - 1];
+    const double v = fma(hl, t, P.sqrt_mu * f1);
     P.f[e] = v;
     ss = fma(v, v, ss);
   }
@@ -135,26 +146,37 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_f_kernel(const SBProb* __restric
 __global__ void __launch_bounds__(SB_T) sb_cgls_w_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
   const double dl = P.sc->delta;
-  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride)
+  SB_FOR_E
     P.w[e] = init ? P.f[e] : fma(dl, P.w[e], P.f[e]);
 }
 
 // ||z||^2 with z = Ahat w = [sqrt(mu) z1; lam Dx w; lam Dy w] (steps 3-4).
 __global__ void __launch_bounds__(SB_T) sb_cgls_zz_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
-  double ss = 0.0;
-  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
-    int r = (int)(e % n), c = (int)(e / n);
+  // |z|^2 = mu |z1|^2 + (lambda/2)^2 (|raw Dx w|^2 + |raw Dy w|^2), two sums
+  double sz = 0.0, sd = 0.0;
+  SB_FOR_E {
+    const int r = (int)(e % n), c = (int)(e / n);
     const double z = P.z1f ? (double)P.z1f[e] : P.z1[e];
-    double a = P.sqrt_mu * z, bx = P.lam * dx_at(P.w, r, c, n), by = P.lam * dy_at(P.w, r, c, n);
-    ss = fma(a, a, fma(bx, bx, fma(by, by, ss)));
+    sz = fma(z, z, sz);
+    const double w = P.w[e];
+    if (c < n - 1) {
+      const double d = w - P.w[e + n];
+      sd = fma(d, d, sd);
+    }
+    if (r < n - 1) {
+      const double d = w - P.w[e + 1];
+      sd = fma(d, d, sd);
+    }
   }
   double tot[2];
-  if (!prob_reduce2(P, ss, 0.0, tot)) return;
+  if (!prob_reduce2(P, sz, sd, tot)) return;
   if (threadIdx.x == 0) {
     SBScal* s = P.sc;
-    if (tot[0] > 0.0) {
-      s->step = s->tau / tot[0];
+    const double hl = 0.5 * P.lam;
+    const double zz = fma(hl * hl, tot[1], P.mu * tot[0]);
+    if (zz > 0.0) {
+      s->step = s->tau / zz;
     } else {
       s->step = 0.0;
       s->active = 0;
@@ -166,15 +188,16 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_zz_kernel(const SBProb* __restri
 __global__ void __launch_bounds__(SB_T) sb_cgls_x_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
   const double mu = P.sc->step;
+  const double c1 = -mu * P.sqrt_mu, c2 = -mu * (0.5 * P.lam);  // r -= mu z, one FMA each
   double sx = 0.0, sw = 0.0;
-  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
-    int r = (int)(e % n), c = (int)(e / n);
-    double w = P.w[e];
-    double xn = fma(mu, w, P.x[e]);
+  SB_FOR_E {
+    const int r = (int)(e % n), c = (int)(e / n);
+    const double w = P.w[e];
+    const double xn = fma(mu, w, P.x[e]);
     P.x[e] = xn;
-    P.r1[e] -= mu * (P.sqrt_mu * P.z1[e]);
-    P.r2[e] -= mu * (P.lam * dx_at(P.w, r, c, n));
-    P.r3[e] -= mu * (P.lam * dy_at(P.w, r, c, n));
+    P.r1[e] = fma(c1, P.z1[e], P.r1[e]);
+    if (c < n - 1) P.r2[e] = fma(c2, w - P.w[e + n], P.r2[e]);  // last column: Dx w = 0
+    if (r < n - 1) P.r3[e] = fma(c2, w - P.w[e + 1], P.r3[e]);  // last row: Dy w = 0
     sx = fma(xn, xn, sx);
     sw = fma(w, w, sw);
   }
@@ -195,7 +218,7 @@ __global__ void __launch_bounds__(SB_T) sb_shrink_kernel(const SBProb* __restric
   SB_PROLOGUE(P.sc->sb_active)
   double sd = 0.0, sp = 0.0;
   const double thr = P.thr;
-  for (long long e = blockIdx.x * (long long)SB_T + threadIdx.x; e < N; e += stride) {
+  SB_FOR_E {
     int r = (int)(e % n), c = (int)(e / n);
     double cx = dx_at(P.x, r, c, n) + P.gx[e];
     double cy = dy_at(P.x, r, c, n) + P.gy[e];
@@ -234,10 +257,11 @@ __global__ void __launch_bounds__(SB_T) sb_shrink_kernel(const SBProb* __restric
 // write the split TF32 planes Xt (row-major, Xt[r][m] = X(r, m), hi then lo) of the next
 // apply's input themselves, working on 32 x 32 tiles so both the column-major vectors and
 // the transposed planes are written coalesced.
-#define SB_TILES_BEGIN                                                   \
-  const int tn = n >> 5, ntile = tn * tn, nblk = sb_blocks(n);           \
-  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;                \
-  for (int t = blockIdx.x; t < ntile; t += nblk) {                       \
+#define SB_TILES_BEGIN                                                              \
+  const int tn = n >> 5, ntile = tn * tn;                                           \
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;                           \
+  const int t_hi = min(ntile, ((int)blockIdx.x + 1) * SB_TILES_PER_CHUNK);          \
+  for (int t = (int)blockIdx.x * SB_TILES_PER_CHUNK; t < t_hi; ++t) {              \
     const int tr = t % tn, tcol = t / tn;
 #define SB_TILES_END }
 
@@ -265,7 +289,7 @@ __device__ __forceinline__ void put_split(float (*th)[33], float (*tl)[33], int 
 // Outer step start (as sb_outer_init_kernel) plus the split planes of r1 = sqrt(mu) b.
 __global__ void __launch_bounds__(SB_T) sb_outer_init_tc_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->sb_active)
-  (void)N; (void)stride;
+  (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
   SB_TILES_BEGIN
 #pragma unroll
@@ -292,7 +316,7 @@ __global__ void __launch_bounds__(SB_T) sb_outer_init_tc_kernel(const SBProb* __
 // the planes of w for the next forward apply.
 __global__ void __launch_bounds__(SB_T) sb_w_tc_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
-  (void)N; (void)stride;
+  (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
   const double dl = P.sc->delta;
   SB_TILES_BEGIN
@@ -312,9 +336,10 @@ __global__ void __launch_bounds__(SB_T) sb_w_tc_kernel(const SBProb* __restrict_
 // test; the planes of r1 for the transpose apply.
 __global__ void __launch_bounds__(SB_T) sb_x_tc_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
-  (void)N; (void)stride;
+  (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
   const double mu = P.sc->step;
+  const double c1 = -mu * P.sqrt_mu, c2 = -mu * (0.5 * P.lam);  // r -= mu z, one FMA each
   double sx = 0.0, sw = 0.0;
   SB_TILES_BEGIN
 #pragma unroll
@@ -324,10 +349,10 @@ __global__ void __launch_bounds__(SB_T) sb_x_tc_kernel(const SBProb* __restrict_
     const double w = P.w[e];
     const double xn = fma(mu, w, P.x[e]);
     P.x[e] = xn;
-    const double r1 = P.r1[e] - mu * (P.sqrt_mu * (double)P.z1f[e]);
+    const double r1 = fma(c1, (double)P.z1f[e], P.r1[e]);
     P.r1[e] = r1;
-    P.r2[e] -= mu * (P.lam * dx_at(P.w, r, c, n));
-    P.r3[e] -= mu * (P.lam * dy_at(P.w, r, c, n));
+    if (c < n - 1) P.r2[e] = fma(c2, w - P.w[e + n], P.r2[e]);
+    if (r < n - 1) P.r3[e] = fma(c2, w - P.w[e + 1], P.r3[e]);
     sx = fma(xn, xn, sx);
     sw = fma(w, w, sw);
     put_split(th, tl, ly + 8 * j, lx, r1);
@@ -473,7 +498,7 @@ size_t sb_state_bytes(int n, int k, int prec) {
   const size_t zbytes = tc_supported(n, gp) ? 0 : a256(kp_z_bytes(n, k, gp));
   size_t tc_ws = tc_supported(n, gp) ? a256(sizeof(float) * ((size_t)2 * N + (size_t)2 * n * k * n)) : 0;
   return a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
-         a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256 + tc_ws + a256(sizeof(float) * 4 * N) + 256;
+         a256(sizeof(double) * sb_blocks(n) * 2) + 256 + tc_ws + a256(sizeof(float) * 4 * N) + 256;
 }
 
 kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* x_dev, double mu,
@@ -490,7 +515,7 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   const bool fused = tc_fused_tiles(n, S->gemm_prec) > 0;
   const size_t xtbytes = fused ? a256(sizeof(float) * 4 * N) : 0;  // Xt planes + z1f + f1f
   S->bytes = a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
-             a256(sizeof(double) * SB_MAX_BLOCKS * 2) + 256 + xtbytes;
+             a256(sizeof(double) * sb_blocks(n) * 2) + 256 + xtbytes;
   KPSB_TRY_CUDA(cudaMallocAsync((void**)&S->mem, S->bytes, st));
   char* q = S->mem;
   double* v = (double*)q;
@@ -500,6 +525,7 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   P.iso = tv == KPSB_ISO;
   P.fixed_inner = o.fixed_inner;
   P.i_max = o.i_max;
+  P.mu = mu;
   P.sqrt_mu = sqrt(mu);
   P.lam = lambda;
   P.thr = o.threshold_rule == KPSB_THR_PAPER ? beta / (lambda * lambda) : beta / (2.0 * lambda * lambda);
@@ -516,7 +542,7 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   P.sc = (SBScal*)q;
   q += a256(sizeof(SBScal));
   P.part = (double*)q;
-  q += a256(sizeof(double) * SB_MAX_BLOCKS * 2);
+  q += a256(sizeof(double) * sb_blocks(n) * 2);
   P.counter = (unsigned int*)q;
   q += 256;
   P.xt = fused ? (float*)q : nullptr;
@@ -620,7 +646,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     if (e == cudaSuccess) e = cudaMemsetAsync(ctrs, 0, 2 * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&hsc, sizeof(SBScal) * P);
     if (e != cudaSuccess) { set_error("sb setup: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
-    const int blocks = std::max(1, std::min(SB_MAX_BLOCKS, (int)((N + SB_T * 4 - 1) / (SB_T * 4))));
+    const int blocks = sb_blocks(n);
     dim3 gv(blocks, P);
     if (!hnew.empty()) {
       sb_setup_kernel<<<dim3(blocks, (unsigned)hnew.size()), SB_T, 0, st>>>(dnew);
@@ -641,59 +667,54 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
       gemm_timer_end(slot, sx, apply_flops, apply_launches);
       return r;
     };
+    // Vector kernels: in the instrumented mode each launch is bracketed by an event pair
+    // of its category.
+#define SB_LAUNCH(cat, kernel, ...)                                    \
+  do {                                                                 \
+    const int slot_ = timed ? timer_begin(sx) : -1;                    \
+    kernel<<<gv, SB_T, 0, sx>>>(__VA_ARGS__);                          \
+    KPSB_CHECK_LAUNCH();                                               \
+    timer_end(slot_, sx, cat, 0.0, 1);                                 \
+  } while (0)
     // Head of an outer step: x_prev = x, CGLS start r = bhat, f = Ahat^T r, w = f.
     auto outer_head = [&](cudaStream_t sx) -> kpsb_status {
       if (fz) {
-        sb_outer_init_tc_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
-        KPSB_CHECK_LAUNCH();
+        SB_LAUNCH(TIMER_SB_OUTER, sb_outer_init_tc_kernel, dprobs);
         KPSB_TRY(kp_apply_on(1, sx));
-        sb_cgls_f_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 1);
-        KPSB_CHECK_LAUNCH();
-        sb_w_tc_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 1);
-        KPSB_CHECK_LAUNCH();
+        SB_LAUNCH(TIMER_SB_F, sb_cgls_f_kernel, dprobs, 1);
+        SB_LAUNCH(TIMER_SB_W, sb_w_tc_kernel, dprobs, 1);
         return KPSB_OK;
       }
-      sb_outer_init_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
-      KPSB_CHECK_LAUNCH();
+      SB_LAUNCH(TIMER_SB_OUTER, sb_outer_init_kernel, dprobs);
       KPSB_TRY(kp_apply_on(1, sx));
-      sb_cgls_f_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 1);
-      KPSB_CHECK_LAUNCH();
-      sb_cgls_w_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 1);
-      KPSB_CHECK_LAUNCH();
+      SB_LAUNCH(TIMER_SB_F, sb_cgls_f_kernel, dprobs, 1);
+      SB_LAUNCH(TIMER_SB_W, sb_cgls_w_kernel, dprobs, 1);
       return KPSB_OK;
     };
     // One CGLS iteration (Alg. 5 steps 3-10) of every active problem.
     auto cgls_iter = [&](cudaStream_t sx) -> kpsb_status {
       if (fz) {
         KPSB_TRY(kp_apply_on(0, sx));
-        sb_cgls_zz_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
-        KPSB_CHECK_LAUNCH();
-        sb_x_tc_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
-        KPSB_CHECK_LAUNCH();
+        SB_LAUNCH(TIMER_SB_ZZ, sb_cgls_zz_kernel, dprobs);
+        SB_LAUNCH(TIMER_SB_X, sb_x_tc_kernel, dprobs);
         KPSB_TRY(kp_apply_on(1, sx));
-        sb_cgls_f_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 0);
-        KPSB_CHECK_LAUNCH();
-        sb_w_tc_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 0);
-        KPSB_CHECK_LAUNCH();
+        SB_LAUNCH(TIMER_SB_F, sb_cgls_f_kernel, dprobs, 0);
+        SB_LAUNCH(TIMER_SB_W, sb_w_tc_kernel, dprobs, 0);
         return KPSB_OK;
       }
       KPSB_TRY(kp_apply_on(0, sx));
-      sb_cgls_zz_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
-      KPSB_CHECK_LAUNCH();
-      sb_cgls_x_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
-      KPSB_CHECK_LAUNCH();
+      SB_LAUNCH(TIMER_SB_ZZ, sb_cgls_zz_kernel, dprobs);
+      SB_LAUNCH(TIMER_SB_X, sb_cgls_x_kernel, dprobs);
       KPSB_TRY(kp_apply_on(1, sx));
-      sb_cgls_f_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 0);
-      KPSB_CHECK_LAUNCH();
-      sb_cgls_w_kernel<<<gv, SB_T, 0, sx>>>(dprobs, 0);
-      KPSB_CHECK_LAUNCH();
+      SB_LAUNCH(TIMER_SB_F, sb_cgls_f_kernel, dprobs, 0);
+      SB_LAUNCH(TIMER_SB_W, sb_cgls_w_kernel, dprobs, 0);
       return KPSB_OK;
     };
     auto shrink = [&](cudaStream_t sx) -> kpsb_status {
-      sb_shrink_kernel<<<gv, SB_T, 0, sx>>>(dprobs);
-      KPSB_CHECK_LAUNCH();
+      SB_LAUNCH(TIMER_SB_OUTER, sb_shrink_kernel, dprobs);
       return KPSB_OK;
     };
+#undef SB_LAUNCH
     if (!timed) {
       // Production path: the whole advance is one CUDA graph; each outer step's CGLS loop
       // is a device-side WHILE node, so no host round trip happens until the end.

@@ -115,6 +115,7 @@ _SIGS = {
     "kpsb_kernel_launches": (C.c_ulonglong, []),
     "kpsb_gemm_timing": (C.c_int, [C.c_int]),
     "kpsb_gemm_stats": (C.c_int, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "kpsb_timer_stats": (C.c_int, [C.c_int, C.POINTER(C.c_ulonglong), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 }
 
 
@@ -431,6 +432,16 @@ def kpsb_gemm_stats():
     """(launches, milliseconds, algorithmic flops) of the recorded KP GEMM applies."""
     L, ms, fl = C.c_ulonglong(), C.c_double(), C.c_double()
     _check("kpsb_gemm_stats", lib().kpsb_gemm_stats(C.byref(L), C.byref(ms), C.byref(fl)))
+    return int(L.value), float(ms.value), float(fl.value)
+
+
+TIMER_NAMES = ("kp_apply", "cgls_zz", "cgls_x", "cgls_f", "cgls_w", "sb_outer")
+
+
+def kpsb_timer_stats(category: int):
+    """(launches, milliseconds, flops) of one timer category (index into TIMER_NAMES)."""
+    L, ms, fl = C.c_ulonglong(), C.c_double(), C.c_double()
+    _check("kpsb_timer_stats", lib().kpsb_timer_stats(int(category), C.byref(L), C.byref(ms), C.byref(fl)))
     return int(L.value), float(ms.value), float(fl.value)
 
 

@@ -61,3 +61,6 @@ def test_invalid_arguments_fail_without_touching_the_gpu():
     assert "RSVD" in str(e.value)
     with pytest.raises(K.KpsbError):
         K.kp_build(np.ones((40, 40)), 8, K.BC_REFLEXIVE, 2, K.EGKB)  # overhang > image
+    with pytest.raises(K.KpsbError) as e:
+        K.kpsb_timer_stats(len(K.TIMER_NAMES))  # unknown timer category
+    assert e.value.code == -1
