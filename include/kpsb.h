@@ -45,6 +45,8 @@ typedef enum {
   KPSB_ENOTFOUND = -8   /* unknown request id */
 } kpsb_status;
 
+/* Largest image side n accepted (n x n images; n^2 pixel indices fit 32 bits). */
+#define KPSB_MAX_N 16384
 enum { KPSB_BC_ZERO = 0, KPSB_BC_REFLEXIVE = 1 };
 enum { KPSB_EGKB = 0, KPSB_RSVD = 1 };
 enum { KPSB_ANISO = 0, KPSB_ISO = 1 };

@@ -606,7 +606,7 @@ extern "C" kpsb_status kp_from_factors(int n, int k, const float* Ax, const floa
                                        const double* sigma, kpsb_kp_t* out) {
   clear_error();
   KPSB_REQUIRE(Ax && Ay && sigma && out, "null pointer");
-  KPSB_REQUIRE(n >= 2 && k >= 1 && k <= KP_MAX, "bad sizes n=%d k=%d", n, k);
+  KPSB_REQUIRE(n >= 2 && n <= KPSB_MAX_N && k >= 1 && k <= KP_MAX, "bad sizes n=%d k=%d", n, k);
   kpsb_kp* h = nullptr;
   KPSB_TRY(handle_alloc(&h, n, k, k));
   size_t bytes = sizeof(float) * (size_t)n * n * k;

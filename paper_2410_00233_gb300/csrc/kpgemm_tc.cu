@@ -173,6 +173,47 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// D += A B with A read from tensor memory (M rows = TMEM lanes, K along columns) and B
+// from shared memory.
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                            uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+// 32 consecutive columns of this thread's TMEM lane (no wait: call tmem_ld_wait before use).
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+      "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+      "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -186,6 +227,7 @@ struct alignas(128) TCJob {
   CUtensorMap m1A;   // Xt planes: {n, n, 2}
   CUtensorMap m1B;   // T1 planes: {n, n, 2, k} (box 128 rows, two-stage kernel)
   CUtensorMap m1F;   // T1 planes, box FUSED_BN rows (fused kernel)
+  CUtensorMap m1R;   // T1 planes, box 128 rows (resident kernel, n = 128)
   CUtensorMap m2A;   // T2 planes: {k n, n, 2}
   CUtensorMap m2B;   // Zt planes: {k n, n, 2}
   const double* X;   // input image (n x n FP64, column-major)
@@ -744,6 +786,244 @@ __global__ void __launch_bounds__(192, 1) tc_fused_kernel(const TCJob* __restric
 }
 
 // ------------------------------------------------------------------------------------------
+// Resident apply for n = 128: one CTA per problem, the iterate kept in shared memory and the
+// intermediate kept in tensor memory.  Both stages are computed transposed so that the
+// intermediate can be the A operand of stage 2 straight from TMEM:
+//   S1(i): D1[c][r]  = sum_m T1_i[c][m] Xt[r][m]         (= Z_i(r, c); A = T1_i, B = Xt)
+//   C(i) : Zh/Zl[c][r] = split(D1[c][r])                   (TMEM -> registers -> TMEM)
+//   S2(i): D2[c][a] += sum_r Z[c][r] T2[a][i n + r]       (A = Z in TMEM, B = T2)
+// and Y(a, c) = D2[c][a].  TMEM columns: D1 [0, 128), Zh [128, 256), Zl [256, 384),
+// D2 [384, 512).  Shared memory: Xt hi/lo (128 KB, loaded once) and a ring of 32-wide K
+// slices of T1 / T2 (16 KB per plane) in the order the MMAs consume them:
+// S1(0), S1(1), S2(0), S1(2), S2(1), ...  The converter releases D1 as soon as it has read
+// it, so S1(i + 1) runs while Z(i) is written, and S2(i) while D1(i + 1) is read.
+// Warps: 0 = TMA, 1 = MMA, 2..5 = converter and epilogue (TMEM lane quarters 2, 3, 0, 1).
+// ------------------------------------------------------------------------------------------
+template <int FPL>
+struct RCfg {
+  static constexpr int TILE = 128 * 128;                 // 128 rows x 32 K x 4 bytes
+  static constexpr int X_BYTES = 2 * 4 * TILE;           // hi, lo planes; 4 K slices each
+  static constexpr int SLOT = FPL * TILE;
+  static constexpr int STAGES = 96 * 1024 / SLOT;        // 6 (FPL 1) or 3 (FPL 2)
+  static constexpr int SMEM = X_BYTES + STAGES * SLOT + 1024 + 512;
+  static constexpr int STAGE_LD = 128 + 1;               // epilogue transpose row stride (floats)
+};
+
+template <int FPL>
+__global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __restrict__ jobs) {
+  using C = RCfg<FPL>;
+  constexpr int STAGES = C::STAGES;
+  const TCJob& J = jobs[blockIdx.x];
+  if (J.active && !*J.active) return;
+  const int n = J.n, k = J.k;  // n == 128
+  if (n != 128) return;
+
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* xs = smem;                       // Xt planes
+  unsigned char* ring = smem + C::X_BYTES;
+  uint64_t* full = (uint64_t*)(ring + STAGES * C::SLOT);
+  uint64_t* empty = full + STAGES;
+  uint64_t* x_full = empty + STAGES;
+  uint64_t* d1_full = x_full + 1;
+  uint64_t* d1_free = d1_full + 1;
+  uint64_t* z_full = d1_free + 1;
+  uint64_t* z_free = z_full + 1;
+  uint64_t* d2_full = z_free + 1;
+  uint32_t* tmem_slot = (uint32_t*)(d2_full + 1);
+  __shared__ int s_fail_v;
+  volatile int* s_fail = &s_fail_v;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    s_fail_v = 0;
+    for (int q = 0; q < STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    mbar_init(x_full, 1);
+    mbar_init(d1_full, 1);
+    mbar_init(d1_free, 4);
+    mbar_init(z_full, 4);
+    mbar_init(z_free, 1);
+    mbar_init(d2_full, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t t_d1 = tmem, t_zh = tmem + 128, t_zl = tmem + 256, t_d2 = tmem + 384;
+  constexpr uint32_t idesc = idesc_tf32(128, 128);
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m1A) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m1R) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m2A) : "memory");
+    mbar_expect_tx(x_full, C::X_BYTES);
+    for (int pl = 0; pl < 2; ++pl)
+      for (int kb = 0; kb < 4; ++kb) tma_load_3d(xs + (pl * 4 + kb) * C::TILE, &J.m1A, x_full, kb * 32, 0, pl);
+    int si = 0;
+    bool ok = true;
+    // slots in consumption order: S1(0), then S1(i + 1), S2(i) for every i
+    for (int v = -1; v < k && ok; ++v) {
+      const int i1 = v + 1;  // stage-1 term of this round (if < k)
+      for (int part = 0; part < 2 && ok; ++part) {
+        const bool s1 = part == 0;
+        if (s1 && i1 >= k) continue;
+        if (!s1 && v < 0) continue;
+        for (int kb = 0; kb < 4; ++kb, ++si) {
+          const int q = si % STAGES, round = si / STAGES;
+          if (round > 0 && !fwait(&empty[q], (round - 1) & 1, s_fail)) { ok = false; break; }
+          unsigned char* st = ring + q * C::SLOT;
+          mbar_expect_tx(&full[q], C::SLOT);
+          for (int pl = 0; pl < FPL; ++pl) {
+            if (s1) tma_load_4d(st + pl * C::TILE, &J.m1R, &full[q], kb * 32, 0, pl, i1);
+            else    tma_load_3d(st + pl * C::TILE, &J.m2A, &full[q], v * n + kb * 32, 0, pl);
+          }
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    int si = 0;
+    bool ok = fwait(x_full, 0, s_fail);
+    const uint32_t x_hi = smem_u32(xs), x_lo = x_hi + 4 * C::TILE;
+    // S1(i): D1 = T1_i Xt^T, products (small first) T1lo*Xhi, T1hi*Xlo, T1hi*Xhi
+    auto stage1 = [&](int i) -> bool {
+      if (i >= 1) {
+        if (!fwait(d1_free, (i - 1) & 1, s_fail)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+      for (int kb = 0; kb < 4; ++kb, ++si) {
+        const int q = si % STAGES, round = si / STAGES;
+        if (!fwait(&full[q], round & 1, s_fail)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t t_hi = smem_u32(ring + q * C::SLOT), t_lo = t_hi + (FPL == 2 ? C::TILE : 0);
+        const uint32_t xh = x_hi + kb * C::TILE, xl = x_lo + kb * C::TILE;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t off = kk * 32, acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+          if (FPL == 2) mma_tf32(t_d1, sdesc_sw128(t_lo + off), sdesc_sw128(xh + off), idesc, acc0);
+          mma_tf32(t_d1, sdesc_sw128(t_hi + off), sdesc_sw128(xl + off), idesc, FPL == 2 ? 1u : acc0);
+          mma_tf32(t_d1, sdesc_sw128(t_hi + off), sdesc_sw128(xh + off), idesc, 1u);
+        }
+        mma_commit(&empty[q]);
+      }
+      mma_commit(d1_full);
+      return true;
+    };
+    // S2(i): D2 += Z T2^T, products Zlo*T2hi, Zhi*T2lo, Zhi*T2hi (A from TMEM)
+    auto stage2 = [&](int i) -> bool {
+      if (!fwait(z_full, i & 1, s_fail)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int kb = 0; kb < 4; ++kb, ++si) {
+        const int q = si % STAGES, round = si / STAGES;
+        if (!fwait(&full[q], round & 1, s_fail)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t b_hi = smem_u32(ring + q * C::SLOT), b_lo = b_hi + (FPL == 2 ? C::TILE : 0);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t off = kk * 32, col = (uint32_t)(kb * 32 + kk * 8);
+          const uint32_t acc0 = (i > 0 || kb > 0 || kk > 0) ? 1u : 0u;
+          mma_tf32_ta(t_d2, t_zl + col, sdesc_sw128(b_hi + off), idesc, acc0);
+          if (FPL == 2) mma_tf32_ta(t_d2, t_zh + col, sdesc_sw128(b_lo + off), idesc, 1u);
+          mma_tf32_ta(t_d2, t_zh + col, sdesc_sw128(b_hi + off), idesc, 1u);
+        }
+        mma_commit(&empty[q]);
+      }
+      mma_commit(z_free);
+      return true;
+    };
+    if (ok) ok = stage1(0);
+    for (int i = 0; i < k && ok; ++i) {
+      if (i + 1 < k) ok = stage1(i + 1);
+      if (ok) ok = stage2(i);
+    }
+    if (ok) mma_commit(d2_full);
+  } else if (warp >= 2) {
+    // ---- converter, then epilogue ----
+    const int quarter = warp & 3;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    bool ok = true;
+    for (int i = 0; i < k && ok; ++i) {
+      if (!fwait(d1_full, i & 1, s_fail)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t v[128];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tmem_ld32_nowait(t_d1 + lane_base + c * 32, v + 32 * c);
+      tmem_ld_wait();
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(d1_free);  // S1(i + 1) may overwrite D1
+      if (i >= 1) {
+        if (!fwait(z_free, (i - 1) & 1, s_fail)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint32_t h[32];  // hi plane, then (after its store has issued) the lo plane
+#pragma unroll
+        for (int j = 0; j < 32; ++j) h[j] = __float_as_uint(tf32_round(__uint_as_float(v[32 * c + j])));
+        tmem_st32(t_zh + lane_base + c * 32, h);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          h[j] = __float_as_uint(tf32_round(__uint_as_float(v[32 * c + j]) - __uint_as_float(h[j])));
+        tmem_st32(t_zl + lane_base + c * 32, h);
+      }
+      tmem_st_wait();
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(z_full);
+    }
+    ok = ok && fwait(d2_full, 0, s_fail);
+    // epilogue: D2[c][a] -> staging (the Xt region is free once every MMA has completed)
+    float* stg = (float*)xs;
+    const int c = quarter * 32 + lane;
+    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t v[32];
+        tmem_ld32_nowait(t_d2 + lane_base + q * 32, v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stg[c * C::STAGE_LD + q * 32 + j] = __uint_as_float(v[j]);
+      }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // the four converter warps
+    if (ok && !*s_fail) {
+      const int a = threadIdx.x - 64;  // 0..127: output row, coalesced along a
+      if (J.Yf) {
+        for (int cc = 0; cc < 128; ++cc) J.Yf[a + (size_t)cc * n] = stg[cc * C::STAGE_LD + a];
+      } else {
+        for (int cc = 0; cc < 128; ++cc) J.Y[a + (size_t)cc * n] = (double)stg[cc * C::STAGE_LD + a];
+      }
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*s_fail && threadIdx.x == 0) {
+    atomicExch(&g_tc_error, 1);
+    mbar_wait(x_full, 0);  // bounded drain of copies in flight
+    for (int q = 0; q < STAGES; ++q) mbar_wait(&full[q], 0);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Host side: plans (one per batched solve: tensor maps built once) and launches
 // ------------------------------------------------------------------------------------------
 struct TCPlan {
@@ -775,6 +1055,23 @@ static kpsb_status launch_fused(const TCJob* jobs, int njobs, int n, cudaStream_
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
 }
+
+template <int FPL>
+static kpsb_status prepare_resident() {
+  KPSB_TRY_CUDA(cudaFuncSetAttribute(tc_resident_kernel<FPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     RCfg<FPL>::SMEM));
+  return KPSB_OK;
+}
+
+template <int FPL>
+static kpsb_status launch_resident(const TCJob* jobs, int njobs, cudaStream_t st) {
+  tc_resident_kernel<FPL><<<njobs, 192, RCfg<FPL>::SMEM, st>>>(jobs);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+// n = 128 runs the resident kernel (KPSB_FUSED_TILED=1 selects the tiled fused kernel).
+static bool resident_ok(int n) { return n == 128 && !getenv("KPSB_FUSED_TILED"); }
 
 // Fused kernel where its TMEM fits (R + 2) x BN columns: n <= 768 with BN = 64.
 static bool fused_ok(int n) { return n % 128 == 0 && (n / 128 + 2) * FUSED_BN <= 512 && !getenv("KPSB_TWO_STAGE"); }
@@ -817,6 +1114,11 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
     cuuint64_t s[3] = {fb * n, fb * n * n, fb * 2 * n * n};
     KPSB_TRY(make_map(&J.m1F, transpose ? T->T1t : T->T1f, 4, d, s, FUSED_BN));
   }
+  {  // T1 with 128-row boxes (resident kernel)
+    cuuint64_t d[4] = {(cuuint64_t)n, (cuuint64_t)n, 2, (cuuint64_t)k};
+    cuuint64_t s[3] = {fb * n, fb * n * n, fb * 2 * n * n};
+    KPSB_TRY(make_map(&J.m1R, transpose ? T->T1t : T->T1f, 4, d, s, 128));
+  }
   {  // T2: {k n, n, 2}
     cuuint64_t d[3] = {(cuuint64_t)k * n, (cuuint64_t)n, 2};
     cuuint64_t s[2] = {fb * k * n, fb * (cuuint64_t)k * n * n};
@@ -840,6 +1142,8 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
   KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 1>()));
   KPSB_TRY((prepare_fused<FUSED_BN, 1>()));
   KPSB_TRY((prepare_fused<FUSED_BN, 2>()));
+  KPSB_TRY(prepare_resident<1>());
+  KPSB_TRY(prepare_resident<2>());
   TCPlan* P = new TCPlan();
   P->njobs = njobs;
   P->n = n;
@@ -920,6 +1224,10 @@ kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
     dim3 gs((n / 32) * (n / 32), P->njobs);
     tc_split_kernel<<<gs, 256, 0, st>>>(jobs);
     KPSB_CHECK_LAUNCH();
+  }
+  if (P->fused && resident_ok(n)) {
+    if (P->prec == KPSB_P_TF32X3) return launch_resident<2>(jobs, P->njobs, st);
+    return launch_resident<1>(jobs, P->njobs, st);
   }
   if (P->fused) {
     if (P->prec == KPSB_P_TF32X3) return launch_fused<FUSED_BN, 2>(jobs, P->njobs, n, st);

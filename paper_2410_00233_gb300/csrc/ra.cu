@@ -176,7 +176,7 @@ RAScratch ra_scratch_carve(void* base, int n, int nb, int s_exp) {
 }
 
 kpsb_status ra_check(int s0, int s1, int n, int bc) {
-  KPSB_REQUIRE(n >= 2, "n must be >= 2 (got %d)", n);
+  KPSB_REQUIRE(n >= 2 && n <= KPSB_MAX_N, "n must be in [2, %d] (got %d)", KPSB_MAX_N, n);
   KPSB_REQUIRE(s0 >= 1 && s1 >= 1 && s0 <= RA_MAX_S && s1 <= RA_MAX_S,
                "PSF size %dx%d outside [1, %d]", s0, s1, RA_MAX_S);
   KPSB_REQUIRE(bc == KPSB_BC_ZERO || bc == KPSB_BC_REFLEXIVE, "unknown boundary condition %d", bc);

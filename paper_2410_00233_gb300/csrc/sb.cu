@@ -78,6 +78,14 @@ __device__ __forceinline__ bool prob_reduce2(const SBProb& P, double a, double b
   const long long e_hi = e_lo + SB_CHUNK < N ? e_lo + SB_CHUNK : N;
 // The elements of this block's chunk, SB_T apart.
 #define SB_FOR_E for (long long e = e_lo + threadIdx.x; e < e_hi; e += SB_T)
+// The same with the element's row r_ and column c_, advanced without a division per
+// element (n * n < 2^32; r_ + SB_T % n < 2 n, so one wrap suffices).
+#define SB_FOR_RC                                                                        \
+  const unsigned e0_ = (unsigned)(e_lo + threadIdx.x), un_ = (unsigned)n;                \
+  int r_ = (int)(e0_ % un_), c_ = (int)(e0_ / un_);                                      \
+  const int dr_ = SB_T % n, dc_ = SB_T / n;                                              \
+  for (long long e = e0_; e < e_hi;                                                      \
+       e += SB_T, r_ += dr_, c_ += dc_, r_ >= n ? (r_ -= n, ++c_) : 0)
 
 // x^(0) = b, d = g = 0, flags set (Alg. 3/4 initialisation).
 __global__ void __launch_bounds__(SB_T) sb_setup_kernel(const SBProb* __restrict__ probs) {
@@ -116,8 +124,8 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_f_kernel(const SBProb* __restric
   // zero last row); one coefficient per term keeps the FP64 operation count low.
   const double hl = 0.5 * P.lam;
   double ss = 0.0;
-  SB_FOR_E {
-    const int r = (int)(e % n), c = (int)(e / n);
+  SB_FOR_RC {
+    const int r = r_, c = c_;
     const double f1 = P.f1f ? (double)P.f1f[e] : P.f1[e];
     double t = (c < n - 1 ? P.r2[e] : 0.0) + (r < n - 1 ? P.r3[e] : 0.0);
     if (c >= 1) t -= P.r2[e - n];
@@ -155,8 +163,8 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_zz_kernel(const SBProb* __restri
   SB_PROLOGUE(P.sc->active)
   // |z|^2 = mu |z1|^2 + (lambda/2)^2 (|raw Dx w|^2 + |raw Dy w|^2), two sums
   double sz = 0.0, sd = 0.0;
-  SB_FOR_E {
-    const int r = (int)(e % n), c = (int)(e / n);
+  SB_FOR_RC {
+    const int r = r_, c = c_;
     const double z = P.z1f ? (double)P.z1f[e] : P.z1[e];
     sz = fma(z, z, sz);
     const double w = P.w[e];
@@ -190,8 +198,8 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_x_kernel(const SBProb* __restric
   const double mu = P.sc->step;
   const double c1 = -mu * P.sqrt_mu, c2 = -mu * (0.5 * P.lam);  // r -= mu z, one FMA each
   double sx = 0.0, sw = 0.0;
-  SB_FOR_E {
-    const int r = (int)(e % n), c = (int)(e / n);
+  SB_FOR_RC {
+    const int r = r_, c = c_;
     const double w = P.w[e];
     const double xn = fma(mu, w, P.x[e]);
     P.x[e] = xn;
@@ -218,8 +226,8 @@ __global__ void __launch_bounds__(SB_T) sb_shrink_kernel(const SBProb* __restric
   SB_PROLOGUE(P.sc->sb_active)
   double sd = 0.0, sp = 0.0;
   const double thr = P.thr;
-  SB_FOR_E {
-    int r = (int)(e % n), c = (int)(e / n);
+  SB_FOR_RC {
+    const int r = r_, c = c_;
     double cx = dx_at(P.x, r, c, n) + P.gx[e];
     double cy = dy_at(P.x, r, c, n) + P.gy[e];
     double dxv, dyv;

@@ -230,28 +230,32 @@ def test_tensor_core_sb_isnr_within_0p1_db(prec_name):
 
 
 @pytest.mark.parametrize("prec_name", ["P_TF32X3", "P_TF32X2"])
-def test_fused_and_two_stage_tensor_core_paths_agree(prec_name, monkeypatch):
-    """n <= 768 runs the fused kernel (Z kept in shared memory), larger n the two-stage
-    kernels; both compute the same split products, so they agree to accumulation-order
-    rounding, and both match the oracle."""
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_resident_fused_and_two_stage_tensor_core_paths_agree(prec_name, transpose, monkeypatch):
+    """n = 128 runs the resident kernel (iterate in shared memory, intermediate in tensor
+    memory), n <= 768 the tiled fused kernel, larger n the two-stage kernels; all compute the
+    same split products, so they agree to accumulation-order rounding and match the oracle."""
     need_gpu()
     from paper_2410_00233_gb300 import kpsb as K
 
     prec = getattr(K, prec_name)
-    for n, k in ((128, 7), (256, 3)):
+    tol = 1e-4 if prec == K.P_TF32X3 else 2e-3
+    for n, k in ((128, 7), (128, 1), (128, 30), (256, 3)):
         Ax, Ay, sig = _rand_factors(n, k, 11 * n + k)
-        kp = K.kp_from_factors(Ax, Ay, sig)
-        X = I.rng(8).standard_normal((n, n))
-        ref = O.kp_apply(_oracle_op(Ax, Ay, sig), X)
-        yf = K.kp_apply(kp, X, 0, prec)
-        monkeypatch.setenv("KPSB_TWO_STAGE", "1")
-        kp2 = K.kp_from_factors(Ax, Ay, sig)
-        y2 = K.kp_apply(kp2, X, 0, prec)
-        monkeypatch.delenv("KPSB_TWO_STAGE")
-        tol = 1e-4 if prec == K.P_TF32X3 else 2e-3
-        assert np.linalg.norm(yf - ref) / np.linalg.norm(ref) < tol
-        assert np.linalg.norm(y2 - ref) / np.linalg.norm(ref) < tol
-        assert np.linalg.norm(yf - y2) / np.linalg.norm(ref) < 1e-4
+        X = I.rng(8 + k).standard_normal((n, n))
+        op = _oracle_op(Ax, Ay, sig)
+        ref = O.kp_apply_t(op, X) if transpose else O.kp_apply(op, X)
+        ys = {}
+        for name, env in (("default", None), ("tiled", "KPSB_FUSED_TILED"), ("two_stage", "KPSB_TWO_STAGE")):
+            if env:
+                monkeypatch.setenv(env, "1")
+            kp = K.kp_from_factors(Ax, Ay, sig)  # fresh handle: the path is chosen per plan
+            ys[name] = K.kp_apply(kp, X, transpose, prec)
+            if env:
+                monkeypatch.delenv(env)
+        for name, y in ys.items():
+            assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < tol, (n, k, name)
+            assert np.linalg.norm(y - ys["two_stage"]) / np.linalg.norm(ref) < 1e-4, (n, k, name)
 
 
 def test_lambda_sweep_on_shared_factors_equals_single_solves():
