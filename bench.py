@@ -517,6 +517,8 @@ def main():
     # every forward apply is followed by one ||z||^2 kernel, every transpose apply by one f kernel
     phases["cgls_iterations_batch"] = phases["cgls_zz_launches"]
     gapplies = phases["cgls_zz_launches"] + phases["cgls_f_launches"]
+    pa, _ = K.kpsb_apply_counts()  # problem-applies actually performed (active problems)
+    phases["active_problems_per_apply"] = pa / gapplies if gapplies else None
     K.kpsb_gemm_timing(False)
     # ISNR of the mixed path on the first timed step
     reqs = steps_in[W]

@@ -282,8 +282,13 @@ unsigned long long kpsb_kernel_launches(void);
  * CUDA graph (same kernels, same results). */
 kpsb_status kpsb_gemm_timing(int enable);
 /* Totals of the recorded applies (waits for their events): kernel launches, summed
- * device milliseconds, and algorithmic flops (4 k n^3 per problem per apply, Sec. 4.2). */
+ * device milliseconds, and algorithmic flops actually performed (4 k n^3 per problem per
+ * apply, Sec. 4.2, counted on the device for problems still active, since the last
+ * kpsb_gemm_timing(1)). */
 kpsb_status kpsb_gemm_stats(unsigned long long* launches, double* ms, double* flops);
+/* Device counters of the applies since the last kpsb_gemm_timing(1) (they run whether or
+ * not timing is on): problem-applies performed and the sum of k n^3 over them. */
+kpsb_status kpsb_apply_counts(unsigned long long* problem_applies, unsigned long long* kn3);
 /* Totals of one timer category (same meaning as kpsb_gemm_stats; flops 0 for the vector
  * kernels): 0 KP applies, 1 CGLS ||z||^2 (Alg. 5 steps 3-4), 2 x and r updates with
  * RC_CGLS (steps 5-6), 3 f = Ahat^T r and tau (steps 7-9), 4 w = f + delta w (step 10),

@@ -82,7 +82,19 @@ extern "C" kpsb_status kpsb_gemm_timing(int enable) {
   if (g_timing) {
     g_next = 0;
     for (auto& r : g_recs) r.used = false;
+    KPSB_TRY(simt_work(nullptr, true));
+    KPSB_TRY(tc_work(nullptr, true));
   }
+  return KPSB_OK;
+}
+
+extern "C" kpsb_status kpsb_apply_counts(unsigned long long* problem_applies, unsigned long long* kn3) {
+  clear_error();
+  unsigned long long a[2] = {0, 0}, b[2] = {0, 0};
+  KPSB_TRY(simt_work(a, false));
+  KPSB_TRY(tc_work(b, false));
+  if (kn3) *kn3 = a[0] + b[0];
+  if (problem_applies) *problem_applies = a[1] + b[1];
   return KPSB_OK;
 }
 
@@ -102,6 +114,14 @@ extern "C" kpsb_status kpsb_timer_stats(int category, unsigned long long* launch
     T += t;
     F += r.flops;
     L += r.launches;
+  }
+  if (category == TIMER_KP_APPLY) {
+    // flops the applies performed: 4 k n^3 per active problem (device counters), so
+    // problems whose CGLS has stopped count nothing
+    unsigned long long a[2] = {0, 0}, b[2] = {0, 0};
+    KPSB_TRY(simt_work(a, false));
+    KPSB_TRY(tc_work(b, false));
+    F = 4.0 * (double)(a[0] + b[0]);
   }
   if (launches) *launches = L;
   if (ms) *ms = T;

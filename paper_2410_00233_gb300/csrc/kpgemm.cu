@@ -10,6 +10,10 @@ namespace kpsb {
 
 static constexpr int GB_M = 64, GB_N = 64, GB_K = 16, GB_T = 256;
 
+// Work actually performed by the applies of this file (as in the tensor-core file):
+// [0] sum of k n^3 over active problems, [1] active problem-applies.
+__device__ unsigned long long g_simt_work[2] = {0, 0};
+
 template <typename T>
 struct TileOps;
 
@@ -98,6 +102,10 @@ __global__ void __launch_bounds__(GB_T) kp_stage2_kernel(const KPJob* __restrict
   const KPJob J = jobs[blockIdx.z];
   if (J.active && !*J.active) return;
   const int n = J.n;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(&g_simt_work[0], (unsigned long long)J.k * n * n * n);
+    atomicAdd(&g_simt_work[1], 1ull);
+  }
   const int tiles_m = (n + GB_M - 1) / GB_M;
   const int m0 = (blockIdx.x % tiles_m) * GB_M, n0 = (blockIdx.x / tiles_m) * GB_N;
   if (n0 >= n) return;
@@ -145,6 +153,15 @@ __global__ void __launch_bounds__(GB_T) kp_stage2_kernel(const KPJob* __restrict
       if (r < n) J.Y[r + (size_t)c * n] = (double)acc[x][y];
     }
   }
+}
+
+kpsb_status simt_work(unsigned long long* out, bool reset) {
+  if (reset) {
+    const unsigned long long z[2] = {0, 0};
+    KPSB_TRY_CUDA(cudaMemcpyToSymbol(g_simt_work, z, sizeof(z)));
+  }
+  if (out) KPSB_TRY_CUDA(cudaMemcpyFromSymbol(out, g_simt_work, 2 * sizeof(unsigned long long)));
+  return KPSB_OK;
 }
 
 size_t kp_z_bytes(int n, int k, int prec) {

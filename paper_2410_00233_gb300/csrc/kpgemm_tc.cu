@@ -362,6 +362,14 @@ __global__ void tc_split_kernel(const TCJob* __restrict__ jobs) {
 // The GEMM kernel
 // ------------------------------------------------------------------------------------------
 __device__ int g_tc_error = 0;  // set on a timed-out wait (read by the host after a solve)
+// Work actually performed by the applies of this file: [0] sum of k n^3 over active
+// problems, [1] active problem-applies (one increment per problem per apply).
+__device__ unsigned long long g_tc_work[2] = {0, 0};
+
+__device__ __forceinline__ void count_apply_work(int k, int n) {
+  atomicAdd(&g_tc_work[0], (unsigned long long)k * n * n * n);
+  atomicAdd(&g_tc_work[1], 1ull);
+}
 
 // FPL = planes of the factor operand (2: split factors, three products per K slice;
 // 1: factors rounded once to TF32, two products).  The iterate operand always has two.
@@ -383,6 +391,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
   const int term = STAGE == 1 ? (int)blockIdx.y : 0;
   if (term >= J.k) return;
   if (J.active && !*J.active) return;
+  if (STAGE == 2 && blockIdx.x == 0 && threadIdx.x == 0) count_apply_work(J.k, J.n);
   const int n = J.n;
   const int m0 = (blockIdx.x % tiles_m) * 128;
   const int c0 = (blockIdx.x / tiles_m) * BN;
@@ -584,6 +593,7 @@ __global__ void __launch_bounds__(192, 1) tc_fused_kernel(const TCJob* __restric
   const int n = J.n, k = J.k;
   const int c0 = blockIdx.x * BN;
   if (c0 >= n) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) count_apply_work(k, n);
   const int R = n / 128;
   const int U = k * R;
   const int nkb1 = n / 32;
@@ -817,6 +827,7 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
   if (J.active && !*J.active) return;
   const int n = J.n, k = J.k;  // n == 128
   if (n != 128) return;
+  if (threadIdx.x == 0) count_apply_work(k, n);
 
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -1240,6 +1251,15 @@ kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
     KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 1>(jobs, P->njobs, n, P->kmax, st)));
     KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 1>(jobs, P->njobs, n, P->kmax, st)));
   }
+  return KPSB_OK;
+}
+
+kpsb_status tc_work(unsigned long long* out, bool reset) {
+  if (reset) {
+    const unsigned long long z[2] = {0, 0};
+    KPSB_TRY_CUDA(cudaMemcpyToSymbol(g_tc_work, z, sizeof(z)));
+  }
+  if (out) KPSB_TRY_CUDA(cudaMemcpyFromSymbol(out, g_tc_work, 2 * sizeof(unsigned long long)));
   return KPSB_OK;
 }
 

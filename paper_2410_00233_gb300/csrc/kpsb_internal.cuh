@@ -132,6 +132,10 @@ struct KPJob {
 kpsb_status kp_apply_batch(const KPJob* jobs_d, int njobs, int n, int kmax, int transpose,
                            int prec, cudaStream_t st);
 size_t kp_z_bytes(int n, int k, int prec);
+// Work counters of the applies (sum of k n^3 and problem-applies over active problems),
+// optionally reset; out may be null.
+kpsb_status simt_work(unsigned long long* out, bool reset);
+kpsb_status tc_work(unsigned long long* out, bool reset);
 
 // Tensor-core path (kpgemm_tc.cu).  A plan holds the tensor maps and workspaces of one
 // batch (forward and transpose jobs); applies reuse it.

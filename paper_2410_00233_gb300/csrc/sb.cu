@@ -16,6 +16,12 @@
 namespace kpsb {
 
 static constexpr int SB_T = 256;
+// Minimum resident blocks per SM requested from the compiler for the vector kernels
+// (register cap 65536 / (SB_T * KPSB_SB_MIN_BLOCKS)).
+#ifndef KPSB_SB_MIN_BLOCKS
+#define KPSB_SB_MIN_BLOCKS 4
+#endif
+#define SB_BOUNDS __launch_bounds__(SB_T, KPSB_SB_MIN_BLOCKS)
 // Each block of a vector kernel handles one fixed chunk of SB_CHUNK elements (SB_EPT per
 // thread) and writes one reduction partial: the summation order depends on n only, so a
 // problem gives the same bits alone, in any batch, and in the serving loop.
@@ -29,6 +35,7 @@ struct SBScal {
   double delta;    // tau_{iota+1} / tau_iota
   double rc_cgls;
   double rc_sb;
+  double ww;       // ||w||^2 of the current direction (tensor-core path: from the w kernel)
   int active;      // CGLS of the current outer step still running
   int sb_active;   // outer loop still running
   int it;          // CGLS steps in the current outer step
@@ -47,12 +54,28 @@ __host__ __device__ __forceinline__ int sb_blocks(int n) {
 // Two-value fixed-order grid reduction inside one problem; returns true in the last block
 // with the totals in out[0..1].
 __device__ __forceinline__ bool prob_reduce2(const SBProb& P, double a, double b, double* out) {
-  __shared__ double sh[32];
-  double ta = block_sum<double>(a, sh);
-  double tb = block_sum<double>(b, sh);
-  if (threadIdx.x == 0) {
-    P.part[2 * blockIdx.x] = ta;
-    P.part[2 * blockIdx.x + 1] = tb;
+  // block totals: partials through shared memory, added by one warp in a fixed order
+  // (far fewer FP64 instructions than a shuffle tree in every warp)
+  __shared__ double sa[SB_T], sb[SB_T];
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double ta = 0.0, tb = 0.0;
+#pragma unroll
+    for (int i = 0; i < SB_T / 32; ++i) {
+      ta += sa[threadIdx.x + 32 * i];
+      tb += sb[threadIdx.x + 32 * i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ta += __shfl_down_sync(0xffffffffu, ta, o);
+      tb += __shfl_down_sync(0xffffffffu, tb, o);
+    }
+    if (threadIdx.x == 0) {
+      P.part[2 * blockIdx.x] = ta;
+      P.part[2 * blockIdx.x + 1] = tb;
+    }
   }
   const unsigned nb = (unsigned)sb_blocks(P.n);
   if (!last_block_arrive(P.counter, nb)) return false;
@@ -68,8 +91,13 @@ __device__ __forceinline__ bool prob_reduce2(const SBProb& P, double a, double b
   return true;
 }
 
+#ifdef KPSB_SB_PROB_REF
+#define SB_PROB_DECL const SBProb& P = probs[blockIdx.y];
+#else
+#define SB_PROB_DECL const SBProb P = probs[blockIdx.y];
+#endif
 #define SB_PROLOGUE(cond)                                            \
-  const SBProb P = probs[blockIdx.y];                                \
+  SB_PROB_DECL                                                       \
   if ((int)blockIdx.x >= sb_blocks(P.n)) return;                     \
   if (!(cond)) return;                                               \
   const int n = P.n;                                                 \
@@ -88,7 +116,7 @@ __device__ __forceinline__ bool prob_reduce2(const SBProb& P, double a, double b
        e += SB_T, r_ += dr_, c_ += dc_, r_ >= n ? (r_ -= n, ++c_) : 0)
 
 // x^(0) = b, d = g = 0, flags set (Alg. 3/4 initialisation).
-__global__ void __launch_bounds__(SB_T) sb_setup_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS sb_setup_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(true)
   SB_FOR_E {
     P.x[e] = P.b[e];
@@ -101,7 +129,7 @@ __global__ void __launch_bounds__(SB_T) sb_setup_kernel(const SBProb* __restrict
 }
 
 // Outer step start: xprev = x; CGLS from x = 0 with r = bhat = [sqrt(mu) b; lam(dx-gx); lam(dy-gy)].
-__global__ void __launch_bounds__(SB_T) sb_outer_init_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS sb_outer_init_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->sb_active)
   SB_FOR_E {
     P.xprev[e] = P.x[e];
@@ -118,7 +146,7 @@ __global__ void __launch_bounds__(SB_T) sb_outer_init_kernel(const SBProb* __res
 
 // f = Ahat^T r = sqrt(mu) f1 + lam Dx^T r2 + lam Dy^T r3 (Alg. 5 step 7 / init) and
 // tau' = ||f||^2 (step 8); delta = tau'/tau (step 9).  init: tau = tau', delta = 0.
-__global__ void __launch_bounds__(SB_T) sb_cgls_f_kernel(const SBProb* __restrict__ probs, int init) {
+__global__ void SB_BOUNDS sb_cgls_f_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
   // Dx^T r2 + Dy^T r3 = (lambda/2) t with t the raw differences (L = half forward difference,
   // zero last row); one coefficient per term keeps the FP64 operation count low.
@@ -151,7 +179,7 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_f_kernel(const SBProb* __restric
 
 // w = f + delta w (step 10); init: w = f (step 2).  The start does not read w, which holds
 // no value yet: 0 * w would turn leftover non-finite bytes into NaN.
-__global__ void __launch_bounds__(SB_T) sb_cgls_w_kernel(const SBProb* __restrict__ probs, int init) {
+__global__ void SB_BOUNDS sb_cgls_w_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
   const double dl = P.sc->delta;
   SB_FOR_E
@@ -159,14 +187,22 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_w_kernel(const SBProb* __restric
 }
 
 // ||z||^2 with z = Ahat w = [sqrt(mu) z1; lam Dx w; lam Dy w] (steps 3-4).
-__global__ void __launch_bounds__(SB_T) sb_cgls_zz_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS sb_cgls_zz_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
-  // |z|^2 = mu |z1|^2 + (lambda/2)^2 (|raw Dx w|^2 + |raw Dy w|^2), two sums
+  // |z|^2 = mu |z1|^2 + (lambda/2)^2 (|raw Dx w|^2 + |raw Dy w|^2), two sums.  z1 from the
+  // tensor-core apply is FP32: its squares are summed in FP32 per thread (16 terms), the
+  // partials in FP64.
   double sz = 0.0, sd = 0.0;
+  float szf = 0.0f;
   SB_FOR_RC {
     const int r = r_, c = c_;
-    const double z = P.z1f ? (double)P.z1f[e] : P.z1[e];
-    sz = fma(z, z, sz);
+    if (P.z1f) {
+      const float z = P.z1f[e];
+      szf = fmaf(z, z, szf);
+    } else {
+      const double z = P.z1[e];
+      sz = fma(z, z, sz);
+    }
     const double w = P.w[e];
     if (c < n - 1) {
       const double d = w - P.w[e + n];
@@ -178,7 +214,7 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_zz_kernel(const SBProb* __restri
     }
   }
   double tot[2];
-  if (!prob_reduce2(P, sz, sd, tot)) return;
+  if (!prob_reduce2(P, sz + (double)szf, sd, tot)) return;
   if (threadIdx.x == 0) {
     SBScal* s = P.sc;
     const double hl = 0.5 * P.lam;
@@ -193,7 +229,7 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_zz_kernel(const SBProb* __restri
 }
 
 // x += mu w; r -= mu z (steps 5-6); RC_CGLS = ||mu w|| / ||x|| (eq. (5.1)) and the stop test.
-__global__ void __launch_bounds__(SB_T) sb_cgls_x_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS sb_cgls_x_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
   const double mu = P.sc->step;
   const double c1 = -mu * P.sqrt_mu, c2 = -mu * (0.5 * P.lam);  // r -= mu z, one FMA each
@@ -222,7 +258,7 @@ __global__ void __launch_bounds__(SB_T) sb_cgls_x_kernel(const SBProb* __restric
 }
 
 // Shrinkage (3.10) / (3.13) and Bregman updates (3.8)-(3.9); RC_SB (5.2).
-__global__ void __launch_bounds__(SB_T) sb_shrink_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS sb_shrink_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->sb_active)
   double sd = 0.0, sp = 0.0;
   const double thr = P.thr;
@@ -287,15 +323,17 @@ __device__ __forceinline__ void store_xt_tile(float* __restrict__ xt, int n, int
   __syncthreads();
 }
 
-__device__ __forceinline__ void put_split(float (*th)[33], float (*tl)[33], int a, int b, double v) {
+// Writes the TF32 hi / lo split of v into the tile; returns v rounded to FP32.
+__device__ __forceinline__ float put_split(float (*th)[33], float (*tl)[33], int a, int b, double v) {
   const float f = (float)v;
   const float h = tf32_rna(f);
   th[a][b] = h;
   tl[a][b] = tf32_rna(f - h);
+  return f;
 }
 
 // Outer step start (as sb_outer_init_kernel) plus the split planes of r1 = sqrt(mu) b.
-__global__ void __launch_bounds__(SB_T) sb_outer_init_tc_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS sb_outer_init_tc_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->sb_active)
   (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
@@ -322,11 +360,12 @@ __global__ void __launch_bounds__(SB_T) sb_outer_init_tc_kernel(const SBProb* __
 
 // w = f + delta w (step 10; delta from the f kernel), init: w = f (step 2, w not read), and
 // the planes of w for the next forward apply.
-__global__ void __launch_bounds__(SB_T) sb_w_tc_kernel(const SBProb* __restrict__ probs, int init) {
+__global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
   (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
   const double dl = P.sc->delta;
+  float wwf = 0.0f;  // ||w||^2 for RC_CGLS, from the FP32 value split below (16 terms per thread)
   SB_TILES_BEGIN
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -334,21 +373,25 @@ __global__ void __launch_bounds__(SB_T) sb_w_tc_kernel(const SBProb* __restrict_
     const size_t e = r + (size_t)c * n;
     const double w = init ? P.f[e] : fma(dl, P.w[e], P.f[e]);
     P.w[e] = w;
-    put_split(th, tl, ly + 8 * j, lx, w);
+    const float wf = put_split(th, tl, ly + 8 * j, lx, w);
+    wwf = fmaf(wf, wf, wwf);
   }
   store_xt_tile(P.xt, n, tr, tcol, th, tl, lx, ly);
   SB_TILES_END
+  double tot[2];
+  if (!prob_reduce2(P, (double)wwf, 0.0, tot)) return;
+  if (threadIdx.x == 0) P.sc->ww = tot[0];
 }
 
 // x += mu w, r -= mu z (steps 5-6, mu from the zz kernel); RC_CGLS (5.1) and the stop
 // test; the planes of r1 for the transpose apply.
-__global__ void __launch_bounds__(SB_T) sb_x_tc_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS sb_x_tc_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
   (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
   const double mu = P.sc->step;
   const double c1 = -mu * P.sqrt_mu, c2 = -mu * (0.5 * P.lam);  // r -= mu z, one FMA each
-  double sx = 0.0, sw = 0.0;
+  double sx = 0.0;  // ||w||^2 for RC_CGLS comes from the w kernel (sc->ww)
   SB_TILES_BEGIN
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -362,17 +405,16 @@ __global__ void __launch_bounds__(SB_T) sb_x_tc_kernel(const SBProb* __restrict_
     if (c < n - 1) P.r2[e] = fma(c2, w - P.w[e + n], P.r2[e]);
     if (r < n - 1) P.r3[e] = fma(c2, w - P.w[e + 1], P.r3[e]);
     sx = fma(xn, xn, sx);
-    sw = fma(w, w, sw);
     put_split(th, tl, ly + 8 * j, lx, r1);
   }
   store_xt_tile(P.xt, n, tr, tcol, th, tl, lx, ly);
   SB_TILES_END
   double tot[2];
-  if (!prob_reduce2(P, sx, sw, tot)) return;
+  if (!prob_reduce2(P, sx, 0.0, tot)) return;
   if (threadIdx.x == 0) {
     SBScal* s = P.sc;
     const double xn = sqrt(tot[0]);
-    s->rc_cgls = xn > 0.0 ? mu * sqrt(tot[1]) / xn : INFINITY;
+    s->rc_cgls = xn > 0.0 ? mu * sqrt(s->ww) / xn : INFINITY;
     s->it += 1;
     s->iota_total += 1;
     if (s->it >= P.i_max || (!P.fixed_inner && s->rc_cgls < P.tau_cgls)) s->active = 0;

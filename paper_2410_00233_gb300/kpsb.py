@@ -116,6 +116,7 @@ _SIGS = {
     "kpsb_gemm_timing": (C.c_int, [C.c_int]),
     "kpsb_gemm_stats": (C.c_int, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "kpsb_timer_stats": (C.c_int, [C.c_int, C.POINTER(C.c_ulonglong), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "kpsb_apply_counts": (C.c_int, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
 }
 
 
@@ -443,6 +444,13 @@ def kpsb_timer_stats(category: int):
     L, ms, fl = C.c_ulonglong(), C.c_double(), C.c_double()
     _check("kpsb_timer_stats", lib().kpsb_timer_stats(int(category), C.byref(L), C.byref(ms), C.byref(fl)))
     return int(L.value), float(ms.value), float(fl.value)
+
+
+def kpsb_apply_counts():
+    """(problem-applies, sum of k n^3) performed since the last kpsb_gemm_timing(True)."""
+    pa, kn3 = C.c_ulonglong(), C.c_ulonglong()
+    _check("kpsb_apply_counts", lib().kpsb_apply_counts(C.byref(pa), C.byref(kn3)))
+    return int(pa.value), int(kn3.value)
 
 
 def kpsb_small_svd(A):

@@ -319,3 +319,24 @@ def test_solve_independent_of_allocator_history():
         assert np.array_equal(x1, x2) and s1.iota_total == s2.iota_total
         for xb, sb in zip(outs, st):
             assert np.array_equal(x1, xb) and sb.iota_total == s1.iota_total
+
+
+def test_apply_work_counters_count_performed_work():
+    """The device counters behind the roofline count 4 k n^3 flops per active problem per
+    apply (Sec. 4.2): one apply of one operator adds exactly (1, k n^3)."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    for n, k, prec in ((128, 7, K.P_TF32X2), (64, 5, K.P_FP32), (256, 3, K.P_TF32X3)):
+        Ax, Ay, sig = _rand_factors(n, k, 3 * n + k)
+        kp = K.kp_from_factors(Ax, Ay, sig)
+        X = I.rng(2).standard_normal((n, n))
+        K.kpsb_gemm_timing(True)
+        try:
+            K.kp_apply(kp, X, 0, prec)
+            K.kp_apply(kp, X, 1, prec)
+            assert K.kpsb_apply_counts() == (2, 2 * k * n ** 3)
+            _, _, flops = K.kpsb_gemm_stats()
+            assert flops == 8.0 * k * n ** 3
+        finally:
+            K.kpsb_gemm_timing(False)
