@@ -796,18 +796,24 @@ __global__ void __launch_bounds__(192, 1) tc_fused_kernel(const TCJob* __restric
 }
 
 // ------------------------------------------------------------------------------------------
-// Resident apply for n = 128: one CTA per problem, the iterate kept in shared memory and the
-// intermediate kept in tensor memory.  Both stages are computed transposed so that the
+// Resident apply for n = 128: a persistent grid (one CTA per SM) takes problems from a
+// global counter (the TMA thread claims the next one and hands its index to the MMA and
+// converter warps through a 4-slot ring in shared memory; -1 ends the walk; the last CTA
+// to finish resets the counter for the next launch).  Per problem the iterate is kept in shared memory
+// and the intermediate in tensor memory.  Both stages are computed transposed so that the
 // intermediate can be the A operand of stage 2 straight from TMEM:
 //   S1(i): D1[c][r]  = sum_m T1_i[c][m] Xt[r][m]         (= Z_i(r, c); A = T1_i, B = Xt)
 //   C(i) : Zh/Zl[c][r] = split(D1[c][r])                   (TMEM -> registers -> TMEM)
 //   S2(i): D2[c][a] += sum_r Z[c][r] T2[a][i n + r]       (A = Z in TMEM, B = T2)
-// and Y(a, c) = D2[c][a].  TMEM columns: D1 [0, 128), Zh [128, 256), Zl [256, 384),
-// D2 [384, 512).  Shared memory: Xt hi/lo (128 KB, loaded once) and a ring of 32-wide K
-// slices of T1 / T2 (16 KB per plane) in the order the MMAs consume them:
-// S1(0), S1(1), S2(0), S1(2), S2(1), ...  The converter releases D1 as soon as it has read
-// it, so S1(i + 1) runs while Z(i) is written, and S2(i) while D1(i + 1) is read.
+// and Y(a, c) = D2[c][a]: TMEM lane c holds column c of Y, which the epilogue stores as 128
+// contiguous floats.  TMEM columns: D1 [0, 128), Zh [128, 256), Zl [256, 384), D2 [384, 512).
+// Shared memory: Xt hi/lo (128 KB) and a ring of 32-wide K slices of T1 / T2 (16 KB per
+// plane) in the order the MMAs consume them: S1(0), S1(1), S2(0), S1(2), S2(1), ...
+// Overlap: the converter releases D1 as soon as it has read it (S1(i + 1) runs while Z(i)
+// is written); the next problem's iterate loads once the last stage-1 MMAs of the current
+// one have completed, and its first MMAs run while the converter stores the current result.
 // Warps: 0 = TMA, 1 = MMA, 2..5 = converter and epilogue (TMEM lane quarters 2, 3, 0, 1).
+// Barrier phases follow a CTA-wide term counter g and problem counter j.
 // ------------------------------------------------------------------------------------------
 template <int FPL>
 struct RCfg {
@@ -816,18 +822,14 @@ struct RCfg {
   static constexpr int SLOT = FPL * TILE;
   static constexpr int STAGES = 96 * 1024 / SLOT;        // 6 (FPL 1) or 3 (FPL 2)
   static constexpr int SMEM = X_BYTES + STAGES * SLOT + 1024 + 512;
-  static constexpr int STAGE_LD = 128 + 1;               // epilogue transpose row stride (floats)
 };
 
 template <int FPL>
-__global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __restrict__ jobs, int njobs,
+                                                             int* __restrict__ queue) {
   using C = RCfg<FPL>;
   constexpr int STAGES = C::STAGES;
-  const TCJob& J = jobs[blockIdx.x];
-  if (J.active && !*J.active) return;
-  const int n = J.n, k = J.k;  // n == 128
-  if (n != 128) return;
-  if (threadIdx.x == 0) count_apply_work(k, n);
+  constexpr int n = 128;
 
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -836,13 +838,17 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
   uint64_t* full = (uint64_t*)(ring + STAGES * C::SLOT);
   uint64_t* empty = full + STAGES;
   uint64_t* x_full = empty + STAGES;
-  uint64_t* d1_full = x_full + 1;
+  uint64_t* x_free = x_full + 1;
+  uint64_t* d1_full = x_free + 1;
   uint64_t* d1_free = d1_full + 1;
   uint64_t* z_full = d1_free + 1;
   uint64_t* z_free = z_full + 1;
   uint64_t* d2_full = z_free + 1;
-  uint32_t* tmem_slot = (uint32_t*)(d2_full + 1);
+  uint64_t* d2_free = d2_full + 1;
+  uint64_t* pq = d2_free + 1;  // [4]: problem index published
+  uint32_t* tmem_slot = (uint32_t*)(pq + 4);
   __shared__ int s_fail_v;
+  __shared__ int s_idx[4];
   volatile int* s_fail = &s_fail_v;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -852,12 +858,15 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
       mbar_init(&full[q], 1);
       mbar_init(&empty[q], 1);
     }
+    for (int q = 0; q < 4; ++q) mbar_init(&pq[q], 1);
     mbar_init(x_full, 1);
+    mbar_init(x_free, 1);
     mbar_init(d1_full, 1);
     mbar_init(d1_free, 4);
     mbar_init(z_full, 4);
     mbar_init(z_free, 1);
     mbar_init(d2_full, 1);
+    mbar_init(d2_free, 4);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -873,45 +882,68 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
   const uint32_t tmem = *tmem_slot;
   const uint32_t t_d1 = tmem, t_zh = tmem + 128, t_zl = tmem + 256, t_d2 = tmem + 384;
   constexpr uint32_t idesc = idesc_tf32(128, 128);
+  // a problem is processed when its CGLS is active and it has the size this kernel tiles
+  auto live = [&](const TCJob& J) { return J.n == n && !(J.active && !*J.active); };
+  // consumers: index of the j-th problem of this CTA (-1: none left); false on a failed wait
+  auto next_problem = [&](int j, int* p) -> bool {
+    if (!fwait(&pq[j & 3], (j >> 2) & 1, s_fail)) return false;
+    *p = *(volatile int*)&s_idx[j & 3];
+    return true;
+  };
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ----
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m1A) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m1R) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m2A) : "memory");
-    mbar_expect_tx(x_full, C::X_BYTES);
-    for (int pl = 0; pl < 2; ++pl)
-      for (int kb = 0; kb < 4; ++kb) tma_load_3d(xs + (pl * 4 + kb) * C::TILE, &J.m1A, x_full, kb * 32, 0, pl);
-    int si = 0;
+    int si = 0, j = 0;
     bool ok = true;
-    // slots in consumption order: S1(0), then S1(i + 1), S2(i) for every i
-    for (int v = -1; v < k && ok; ++v) {
-      const int i1 = v + 1;  // stage-1 term of this round (if < k)
-      for (int part = 0; part < 2 && ok; ++part) {
-        const bool s1 = part == 0;
-        if (s1 && i1 >= k) continue;
-        if (!s1 && v < 0) continue;
-        for (int kb = 0; kb < 4; ++kb, ++si) {
-          const int q = si % STAGES, round = si / STAGES;
-          if (round > 0 && !fwait(&empty[q], (round - 1) & 1, s_fail)) { ok = false; break; }
-          unsigned char* st = ring + q * C::SLOT;
-          mbar_expect_tx(&full[q], C::SLOT);
-          for (int pl = 0; pl < FPL; ++pl) {
-            if (s1) tma_load_4d(st + pl * C::TILE, &J.m1R, &full[q], kb * 32, 0, pl, i1);
-            else    tma_load_3d(st + pl * C::TILE, &J.m2A, &full[q], v * n + kb * 32, 0, pl);
+    for (;; ++j) {
+      int p;
+      do {
+        p = atomicAdd(queue, 1);
+      } while (p < njobs && !live(jobs[p]));
+      if (p >= njobs || !ok) p = -1;
+      s_idx[j & 3] = p;
+      mbar_arrive(&pq[j & 3]);  // release: the index is visible to whoever waits on pq
+      if (p < 0) break;
+      const TCJob& J = jobs[p];
+      const int k = J.k;
+      count_apply_work(k, n);
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m1A) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m1R) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m2A) : "memory");
+      // the iterate buffer is free once the previous problem's stage-1 MMAs have completed
+      if (j > 0 && !fwait(x_free, (j - 1) & 1, s_fail)) { ok = false; break; }
+      mbar_expect_tx(x_full, C::X_BYTES);
+      for (int pl = 0; pl < 2; ++pl)
+        for (int kb = 0; kb < 4; ++kb) tma_load_3d(xs + (pl * 4 + kb) * C::TILE, &J.m1A, x_full, kb * 32, 0, pl);
+      // slots in consumption order: S1(0), then S1(i + 1), S2(i) for every i
+      for (int v = -1; v < k && ok; ++v) {
+        const int i1 = v + 1;
+        for (int part = 0; part < 2 && ok; ++part) {
+          const bool s1 = part == 0;
+          if (s1 && i1 >= k) continue;
+          if (!s1 && v < 0) continue;
+          for (int kb = 0; kb < 4; ++kb, ++si) {
+            const int q = si % STAGES, round = si / STAGES;
+            if (round > 0 && !fwait(&empty[q], (round - 1) & 1, s_fail)) { ok = false; break; }
+            unsigned char* st = ring + q * C::SLOT;
+            mbar_expect_tx(&full[q], C::SLOT);
+            for (int pl = 0; pl < FPL; ++pl) {
+              if (s1) tma_load_4d(st + pl * C::TILE, &J.m1R, &full[q], kb * 32, 0, pl, i1);
+              else    tma_load_3d(st + pl * C::TILE, &J.m2A, &full[q], v * n + kb * 32, 0, pl);
+            }
           }
         }
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
-    int si = 0;
-    bool ok = fwait(x_full, 0, s_fail);
+    int si = 0, g = 0, j = 0;  // ring slot, CTA-wide term, problem
+    bool ok = true;
     const uint32_t x_hi = smem_u32(xs), x_lo = x_hi + 4 * C::TILE;
-    // S1(i): D1 = T1_i Xt^T, products (small first) T1lo*Xhi, T1hi*Xlo, T1hi*Xhi
-    auto stage1 = [&](int i) -> bool {
-      if (i >= 1) {
-        if (!fwait(d1_free, (i - 1) & 1, s_fail)) return false;
+    // S1 of CTA-wide term gi: D1 = T1 Xt^T, products (small first) T1lo*Xhi, T1hi*Xlo, T1hi*Xhi
+    auto stage1 = [&](int gi) -> bool {
+      if (gi >= 1) {
+        if (!fwait(d1_free, (gi - 1) & 1, s_fail)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       }
       for (int kb = 0; kb < 4; ++kb, ++si) {
@@ -932,9 +964,10 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
       mma_commit(d1_full);
       return true;
     };
-    // S2(i): D2 += Z T2^T, products Zlo*T2hi, Zhi*T2lo, Zhi*T2hi (A from TMEM)
-    auto stage2 = [&](int i) -> bool {
-      if (!fwait(z_full, i & 1, s_fail)) return false;
+    // S2 of term gi (problem term i): D2 += Z T2^T, products Zlo*T2hi, Zhi*T2lo, Zhi*T2hi
+    auto stage2 = [&](int gi, int i) -> bool {
+      if (!fwait(z_full, gi & 1, s_fail)) return false;
+      if (i == 0 && j > 0 && !fwait(d2_free, (j - 1) & 1, s_fail)) return false;  // D2 read out
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       for (int kb = 0; kb < 4; ++kb, ++si) {
         const int q = si % STAGES, round = si / STAGES;
@@ -954,69 +987,92 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
       mma_commit(z_free);
       return true;
     };
-    if (ok) ok = stage1(0);
-    for (int i = 0; i < k && ok; ++i) {
-      if (i + 1 < k) ok = stage1(i + 1);
-      if (ok) ok = stage2(i);
+    for (; ok; ++j) {
+      int p;
+      if (!next_problem(j, &p)) { ok = false; break; }
+      if (p < 0) break;
+      const TCJob& J = jobs[p];
+      const int k = J.k;
+      ok = fwait(x_full, j & 1, s_fail);
+      if (ok) ok = stage1(g);
+      if (ok && k == 1) mma_commit(x_free);
+      for (int i = 0; i < k && ok; ++i) {
+        if (i + 1 < k) {
+          ok = stage1(g + i + 1);
+          if (ok && i + 2 == k) mma_commit(x_free);  // last stage-1 MMAs of this problem issued
+        }
+        if (ok) ok = stage2(g + i, i);
+      }
+      if (ok) mma_commit(d2_full);
+      g += k;
     }
-    if (ok) mma_commit(d2_full);
   } else if (warp >= 2) {
     // ---- converter, then epilogue ----
     const int quarter = warp & 3;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    const int c = quarter * 32 + lane;  // TMEM lane: column of Y
+    int g = 0;
     bool ok = true;
-    for (int i = 0; i < k && ok; ++i) {
-      if (!fwait(d1_full, i & 1, s_fail)) { ok = false; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    for (int j = 0; ok; ++j) {
+      int p;
+      if (!next_problem(j, &p)) { ok = false; break; }
+      if (p < 0) break;
+      const TCJob& J = jobs[p];
+      const int k = J.k;
       uint32_t v[128];
+      for (int i = 0; i < k && ok; ++i, ++g) {
+        if (!fwait(d1_full, g & 1, s_fail)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int c = 0; c < 4; ++c) tmem_ld32_nowait(t_d1 + lane_base + c * 32, v + 32 * c);
+        for (int q = 0; q < 4; ++q) tmem_ld32_nowait(t_d1 + lane_base + q * 32, v + 32 * q);
+        tmem_ld_wait();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(d1_free);  // S1 of the next term may overwrite D1
+        if (g >= 1) {
+          if (!fwait(z_free, (g - 1) & 1, s_fail)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint32_t h[32];  // hi plane, then (after its store has issued) the lo plane
+#pragma unroll
+          for (int t = 0; t < 32; ++t) h[t] = __float_as_uint(tf32_round(__uint_as_float(v[32 * q + t])));
+          tmem_st32(t_zh + lane_base + q * 32, h);
+#pragma unroll
+          for (int t = 0; t < 32; ++t)
+            h[t] = __float_as_uint(tf32_round(__uint_as_float(v[32 * q + t]) - __uint_as_float(h[t])));
+          tmem_st32(t_zl + lane_base + q * 32, h);
+        }
+        tmem_st_wait();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(z_full);
+      }
+      if (!ok || !fwait(d2_full, j & 1, s_fail)) { ok = false; break; }
+      // epilogue: column c of Y from TMEM lane c; D2 is free for the next problem once read
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tmem_ld32_nowait(t_d2 + lane_base + q * 32, v + 32 * q);
       tmem_ld_wait();
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(d1_free);  // S1(i + 1) may overwrite D1
-      if (i >= 1) {
-        if (!fwait(z_free, (i - 1) & 1, s_fail)) { ok = false; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint32_t h[32];  // hi plane, then (after its store has issued) the lo plane
-#pragma unroll
-        for (int j = 0; j < 32; ++j) h[j] = __float_as_uint(tf32_round(__uint_as_float(v[32 * c + j])));
-        tmem_st32(t_zh + lane_base + c * 32, h);
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          h[j] = __float_as_uint(tf32_round(__uint_as_float(v[32 * c + j]) - __uint_as_float(h[j])));
-        tmem_st32(t_zl + lane_base + c * 32, h);
-      }
-      tmem_st_wait();
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(z_full);
-    }
-    ok = ok && fwait(d2_full, 0, s_fail);
-    // epilogue: D2[c][a] -> staging (the Xt region is free once every MMA has completed)
-    float* stg = (float*)xs;
-    const int c = quarter * 32 + lane;
-    if (ok) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t v[32];
-        tmem_ld32_nowait(t_d2 + lane_base + q * 32, v);
-        tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) stg[c * C::STAGE_LD + q * 32 + j] = __uint_as_float(v[j]);
-      }
-    }
-    asm volatile("bar.sync 1, 128;" ::: "memory");  // the four converter warps
-    if (ok && !*s_fail) {
-      const int a = threadIdx.x - 64;  // 0..127: output row, coalesced along a
+      if (lane == 0) mbar_arrive(d2_free);
       if (J.Yf) {
-        for (int cc = 0; cc < 128; ++cc) J.Yf[a + (size_t)cc * n] = stg[cc * C::STAGE_LD + a];
+        float4* y = (float4*)(J.Yf + (size_t)c * n);
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          y[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                             __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+      } else if (((uintptr_t)J.Y & 15) == 0) {  // caller's FP64 output: vector stores when aligned
+        double2* y = (double2*)(J.Y + (size_t)c * n);
+#pragma unroll
+        for (int q = 0; q < 64; ++q)
+          y[q] = make_double2((double)__uint_as_float(v[2 * q]), (double)__uint_as_float(v[2 * q + 1]));
       } else {
-        for (int cc = 0; cc < 128; ++cc) J.Y[a + (size_t)cc * n] = (double)stg[cc * C::STAGE_LD + a];
+        double* y = J.Y + (size_t)c * n;
+#pragma unroll
+        for (int q = 0; q < 128; ++q) y[q] = (double)__uint_as_float(v[q]);
       }
     }
   }
@@ -1032,6 +1088,13 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
+  if (threadIdx.x == 0) {  // the last CTA out resets the problem counter for the next launch
+    __threadfence();
+    if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(queue, 0);
+      atomicExch(queue + 1, 0);
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1045,6 +1108,7 @@ struct TCPlan {
   int prec = KPSB_P_TF32X3;
   bool fused = false;
   bool ext_split = false;  // the caller writes the split planes (xt_ext)
+  int* queue = nullptr;    // resident kernel: problem counter and finished-CTA counter (start at 0)
 };
 
 bool tc_plan_fused(const TCPlan* P) { return P && P->fused; }
@@ -1075,8 +1139,12 @@ static kpsb_status prepare_resident() {
 }
 
 template <int FPL>
-static kpsb_status launch_resident(const TCJob* jobs, int njobs, cudaStream_t st) {
-  tc_resident_kernel<FPL><<<njobs, 192, RCfg<FPL>::SMEM, st>>>(jobs);
+static kpsb_status launch_resident(const TCJob* jobs, int njobs, int* queue, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  KPSB_TRY_CUDA(cudaGetDevice(&dev));
+  KPSB_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = std::max(1, std::min(njobs, sms));  // persistent: one CTA per SM at most
+  tc_resident_kernel<FPL><<<grid, 192, RCfg<FPL>::SMEM, st>>>(jobs, njobs, queue);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
 }
@@ -1171,7 +1239,7 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
     P->kmax = std::max(P->kmax, kps[p]->k);
     floats += (fwd_h[p].xt_ext ? 0 : (size_t)2 * n * n) + (size_t)2 * n * kps[p]->k * n;
   }
-  cudaError_t e = cudaMallocAsync((void**)&P->work, sizeof(float) * floats + 2 * sizeof(TCJob) * njobs + 256, st);
+  cudaError_t e = cudaMallocAsync((void**)&P->work, sizeof(float) * floats + 2 * sizeof(TCJob) * njobs + 512, st);
   if (e != cudaSuccess) {
     delete P;
     set_error("tensor-core workspace: %s", cudaGetErrorString(e));
@@ -1199,7 +1267,9 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
   char* jb = (char*)(((uintptr_t)q + 255) & ~(uintptr_t)255);
   P->d_fwd = (TCJob*)jb;
   P->d_bwd = P->d_fwd + njobs;
-  e = cudaMemcpyAsync(P->d_fwd, hf.data(), sizeof(TCJob) * njobs, cudaMemcpyHostToDevice, st);
+  P->queue = (int*)(P->d_bwd + njobs);
+  e = cudaMemsetAsync(P->queue, 0, 2 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(P->d_fwd, hf.data(), sizeof(TCJob) * njobs, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(P->d_bwd, hb.data(), sizeof(TCJob) * njobs, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host job arrays go out of scope
   if (e != cudaSuccess) {
@@ -1237,8 +1307,8 @@ kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
     KPSB_CHECK_LAUNCH();
   }
   if (P->fused && resident_ok(n)) {
-    if (P->prec == KPSB_P_TF32X3) return launch_resident<2>(jobs, P->njobs, st);
-    return launch_resident<1>(jobs, P->njobs, st);
+    if (P->prec == KPSB_P_TF32X3) return launch_resident<2>(jobs, P->njobs, P->queue, st);
+    return launch_resident<1>(jobs, P->njobs, P->queue, st);
   }
   if (P->fused) {
     if (P->prec == KPSB_P_TF32X3) return launch_fused<FUSED_BN, 2>(jobs, P->njobs, n, st);

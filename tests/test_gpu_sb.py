@@ -340,3 +340,27 @@ def test_apply_work_counters_count_performed_work():
             assert flops == 8.0 * k * n ** 3
         finally:
             K.kpsb_gemm_timing(False)
+
+
+def test_persistent_apply_with_more_problems_than_sms():
+    """The n = 128 apply runs one persistent CTA per SM that walks its problems in turn; a
+    batch larger than the SM count (some CTAs carry two problems, with different k) gives
+    each problem the same bits as its solve alone."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    n, P = 128, 160
+    g = I.rng(77)
+    kps, bs = [], []
+    for p in range(P):
+        k = 1 + p % 8
+        Ax = (g.standard_normal((k, n, n)) / n).astype(np.float32)
+        Ay = (g.standard_normal((k, n, n)) / n).astype(np.float32)
+        sig = np.sort(g.random(k))[::-1] + 0.1
+        kps.append(K.kp_from_factors(Ax, Ay, sig))
+        bs.append(g.standard_normal((n, n)))
+    jobs = [dict(kp=kp, b=b, mu=1.0, lam=0.1, tv=K.ISO, iters=2) for kp, b in zip(kps, bs)]
+    outs, stats = K.sb_solve_batched(jobs, prec=K.P_TF32X2)
+    for p in (0, 7, 151, 152, 159):
+        x, st = K.sb_solve(kps[p], bs[p], 1.0, 0.1, K.ISO, 2, prec=K.P_TF32X2)
+        assert np.array_equal(x, outs[p]) and st.iota_total == stats[p].iota_total, p
