@@ -440,8 +440,9 @@ def main():
     B = args.batch
     W, S = args.warmup, args.steps
     # inputs of every step, distinct requests per rank and step
-    base = rank * 100000
-    steps_in = [make_inputs(K, I, torch, B, base + s * B, dev) for s in range(W + S)]
+    from paper_2410_00233_gb300 import shard
+
+    steps_in = [make_inputs(K, I, torch, B, shard.request_ids(rank, s, B).start, dev) for s in range(W + S)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     # warm-up
     for s in range(W):
@@ -477,13 +478,8 @@ def main():
     clk = clocks.stop()
     launches = K.kpsb_kernel_launches() - launches0
     t_rank = sum(times)
-    if dist is not None:
-        tt = torch.tensor([t_rank], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    else:
-        t_max = t_rank
-    value = world * B * S / t_max
+    t_max = shard.job_seconds(t_rank, dist, dev)
+    value = shard.throughput(B * S, world, t_max)
     if args.profile:
         if rank == 0:
             print(json.dumps({"profile_run": True, "value": world * B * S / t_max, "unit": "deblurs/s",
@@ -563,10 +559,7 @@ def main():
             K._check("sb_solve_batched", K.lib().sb_solve_batched(B, arr, 0, C.byref(o)))
             t_e2e += time.perf_counter() - t0
             del kps
-        if dist is not None:
-            tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
+        t_e2e = shard.job_seconds(t_e2e, dist, dev)
         h2d = B * (N_IMG * N_IMG * 8 + PSF_S * PSF_S * 8)
         d2h = B * N_IMG * N_IMG * 8
         e2e = {"value": world * B * n_e2e / t_e2e, "unit": "deblurs/s", "h2d_bytes_per_step": h2d,
