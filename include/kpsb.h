@@ -130,6 +130,17 @@ kpsb_status kp_info(kpsb_kp_t kp, int* n, int* k, int* kp_size, double* sigma);
  * Any pointer may be NULL. */
 kpsb_status kp_get_factors(kpsb_kp_t kp, float* Ax, float* Ay, double* sigma);
 
+/* Handle of the exact blurring operator A itself as an explicit dense matrix (eq. (1.1);
+ * the direct method of the paper's comparison, Sec. 4.3 case (i), Table 4 rows "A"):
+ * A is n^2 x n^2 FP64 column-major on the device (2 GiB at n = 128), built from the PSF
+ * (host, s0 x s1 column-major, centre (s0/2, s1/2)) with boundary bc exactly as kp_blur_dev
+ * applies it.  kp_apply / kp_apply_dev (precision KPSB_P_FP64 only), sb_solve, sb_solve_dev
+ * and sb_solve_batched accept the handle and run CGLS with A (always FP64, whatever the
+ * precision option); kp_info reports k = 0; kp_get_factors fails with KPSB_EINVAL.
+ * KPSB_EINVAL for n > 128 or a bad PSF / boundary, KPSB_ENOMEM if A does not fit.  Free
+ * with kp_free. */
+kpsb_status kp_dense_blur(const double* psf, int s0, int s1, int n, int bc, kpsb_kp_t* out);
+
 /* Make a handle from given factors (host, same layout as kp_get_factors): lets a caller
  * run sb_solve on identical factors, or reuse cached ones. */
 kpsb_status kp_from_factors(int n, int k, const float* Ax, const float* Ay,

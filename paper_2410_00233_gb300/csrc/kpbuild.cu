@@ -595,6 +595,7 @@ extern "C" kpsb_status kp_info(kpsb_kp_t kp, int* n, int* k, int* kp_size, doubl
 extern "C" kpsb_status kp_get_factors(kpsb_kp_t kp, float* Ax, float* Ay, double* sigma) {
   clear_error();
   KPSB_REQUIRE(kp, "null handle");
+  KPSB_REQUIRE(!kp->A_dense, "an explicit-operator handle has no Kronecker factors");
   size_t bytes = sizeof(float) * (size_t)kp->n * kp->n * kp->k;
   if (Ax) KPSB_TRY_CUDA(cudaMemcpy(Ax, kp->Ax, bytes, cudaMemcpyDeviceToHost));
   if (Ay) KPSB_TRY_CUDA(cudaMemcpy(Ay, kp->Ay, bytes, cudaMemcpyDeviceToHost));
@@ -627,6 +628,7 @@ extern "C" void kp_free(kpsb_kp_t kp) {
   if (!kp) return;
   if (kp->tc) tc_free(kp->tc);
   if (kp->Ax) cudaFree(kp->Ax);
+  if (kp->A_dense) cudaFree(kp->A_dense);
   delete kp;
 }
 

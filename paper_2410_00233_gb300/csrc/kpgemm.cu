@@ -201,6 +201,28 @@ extern "C" kpsb_status kp_apply_dev(kpsb_kp_t kp, const double* X, double* Y, in
   KPSB_REQUIRE(prec >= KPSB_P_FP64 && prec <= KPSB_P_TF32X2, "unknown precision %d", prec);
   cudaStream_t st = (cudaStream_t)stream;
   const int n = kp->n, k = kp->k;
+  if (kp->A_dense) {  // explicit operator: FP64 products
+    KPSB_REQUIRE(prec == KPSB_P_FP64, "an explicit-operator handle applies in FP64 only");
+    double* part = nullptr;
+    KPSB_TRY_CUDA(cudaMallocAsync((void**)&part, sizeof(double) * dense_partials(n) + 256, st));
+    KPJob J{};
+    J.n = n;
+    J.X = X;
+    J.Y = Y;
+    J.A = kp->A_dense;
+    J.Z = (char*)part + 256;
+    KPJob* Jd = (KPJob*)part;
+    cudaError_t e = cudaMemcpyAsync(Jd, &J, sizeof(KPJob), cudaMemcpyHostToDevice, st);
+    kpsb_status s = KPSB_OK;
+    if (e == cudaSuccess) s = dense_apply_batch(Jd, 1, n, transpose, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);  // the descriptor copy is from the host stack
+    cudaFreeAsync(part, st);
+    if (e != cudaSuccess || (s == KPSB_OK && e2 != cudaSuccess)) {
+      set_error("kp_apply_dev (explicit A): %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+      return KPSB_ECUDA;
+    }
+    return s;
+  }
   const bool tc = tc_supported(kp->n, prec);
   if ((prec == KPSB_P_TF32X3 || prec == KPSB_P_TF32X2) && !tc) prec = KPSB_P_FP32;  // untiled sizes
   size_t zb = tc ? 0 : kp_z_bytes(n, k, prec);

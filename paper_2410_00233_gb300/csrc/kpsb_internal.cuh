@@ -107,6 +107,7 @@ struct kpsb_kp {
   double* sigma_d = nullptr;  // k
   std::vector<double> sigma;  // host copy
   kpsb::TCTables* tc = nullptr;  // lazily built GEMM operand tables
+  double* A_dense = nullptr;  // explicit operator A (kp_dense_blur): n^2 x n^2 FP64, k = 0
   std::mutex mu;
 };
 
@@ -126,12 +127,18 @@ struct KPJob {
   // Tensor-core path only (zero for a plain apply):
   float* xt_ext;       // caller-maintained split planes of X ([2][n][n] row-major), or null
   float* yf;           // fused kernel: write the result in FP32 here instead of Y
+  // Explicit operator (kp_dense_blur handles): A (n^2 x n^2 FP64); Z holds the partials
+  const double* A;
 };
 // Y = sum sigma_i Ay_i X Ax_i^T (transpose 0) / sum sigma_i Ay_i^T X Ax_i (transpose 1)
 // for every job (all with the same n).  jobs_d: device copy of the descriptors.
 kpsb_status kp_apply_batch(const KPJob* jobs_d, int njobs, int n, int kmax, int transpose,
                            int prec, cudaStream_t st);
 size_t kp_z_bytes(int n, int k, int prec);
+// Explicit operator (dense.cu): Y = A X or A^T X for every job (all with the same n, J.A set,
+// J.Z with dense_partials(n) doubles of scratch).
+kpsb_status dense_apply_batch(const KPJob* jobs_d, int njobs, int n, int transpose, cudaStream_t st);
+size_t dense_partials(int n);
 // Work counters of the applies (sum of k n^3 and problem-applies over active problems),
 // optionally reset; out may be null.
 kpsb_status simt_work(unsigned long long* out, bool reset);

@@ -559,10 +559,12 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   S->kp = kp;
   S->n = n;
   S->prec = o.prec;
-  S->gemm_prec = gemm_prec_for(n, o.prec);
+  const bool dense = kp->A_dense != nullptr;  // explicit A: FP64 products, partial-sum scratch
+  S->gemm_prec = dense ? KPSB_P_FP64 : gemm_prec_for(n, o.prec);
   S->initialized = false;
-  const size_t zbytes = tc_supported(n, S->gemm_prec) ? 0 : a256(kp_z_bytes(n, kp->k, S->gemm_prec));
-  const bool fused = tc_fused_tiles(n, S->gemm_prec) > 0;
+  const size_t zbytes = dense ? a256(sizeof(double) * dense_partials(n))
+                              : tc_supported(n, S->gemm_prec) ? 0 : a256(kp_z_bytes(n, kp->k, S->gemm_prec));
+  const bool fused = !dense && tc_fused_tiles(n, S->gemm_prec) > 0;
   const size_t xtbytes = fused ? a256(sizeof(float) * 4 * N) : 0;  // Xt planes + z1f + f1f
   S->bytes = a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
              a256(sizeof(double) * sb_blocks(n) * 2) + 256 + xtbytes;
@@ -649,8 +651,9 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
   const size_t N = (size_t)n * n;
   int kmax = 0;
   for (int p = 0; p < P; ++p) kmax = std::max(kmax, set[p]->kp->k);
-  const int gemm_prec = gemm_prec_for(n, o.prec);
-  const bool tc = tc_supported(n, gemm_prec);
+  const bool dense = set[0]->kp->A_dense != nullptr;  // a group is all explicit or all KP
+  const int gemm_prec = dense ? KPSB_P_FP64 : gemm_prec_for(n, o.prec);
+  const bool tc = !dense && tc_supported(n, gemm_prec);
   // fused CGLS variant: every state carries split planes and epilogue partials
   bool fz = tc && tc_fused_tiles(n, gemm_prec) > 0;
   for (int p = 0; p < count; ++p) fz = fz && set[p]->prob.xt != nullptr;
@@ -668,6 +671,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     KPJob& F = fwd[p];
     F.Ax = S->kp->Ax; F.Ay = S->kp->Ay; F.sigma = S->kp->sigma_d; F.n = n; F.k = S->kp->k;
     F.X = S->prob.w; F.Y = S->prob.z1; F.Z = S->Z;
+    F.A = S->kp->A_dense;
     F.active = (const int*)((char*)S->prob.sc + offsetof(SBScal, active));
     KPJob& B = bwd[p];
     B = F;
@@ -707,14 +711,17 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     for (int p = 0; p < P; ++p) ksum += set[p]->kp->k;
     const double apply_flops = 4.0 * ksum * (double)n * n * n;  // 4 k n^3 per problem (Sec. 4.2)
     if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, gemm_prec, st, &plan))) break;
+    // kernel launches of one apply (forward / transpose)
     const int apply_launches = tc ? (fz ? 1 : 3) - (tc && !fz && tc_plan_fused(plan) ? 1 : 0) : 2;
+    const int ap_f = dense ? 2 : apply_launches, ap_b = dense ? 1 : apply_launches;
     const bool timed = gemm_timing_enabled();
     // One KP apply of the whole batch on stream sx (timed with events in instrumented mode).
     auto kp_apply_on = [&](int transpose, cudaStream_t sx) -> kpsb_status {
       int slot = timed ? gemm_timer_begin(sx) : -1;
-      kpsb_status r = tc ? tc_plan_apply(plan, transpose, sx)
-                         : kp_apply_batch(transpose ? dbwd : dfwd, P, n, kmax, transpose, gemm_prec, sx);
-      gemm_timer_end(slot, sx, apply_flops, apply_launches);
+      kpsb_status r = dense ? dense_apply_batch(transpose ? dbwd : dfwd, P, n, transpose, sx)
+                      : tc  ? tc_plan_apply(plan, transpose, sx)
+                            : kp_apply_batch(transpose ? dbwd : dfwd, P, n, kmax, transpose, gemm_prec, sx);
+      gemm_timer_end(slot, sx, apply_flops, transpose ? ap_b : ap_f);
       return r;
     };
     // Vector kernels: in the instrumented mode each launch is bracketed by an event pair
@@ -769,8 +776,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
       // Production path: the whole advance is one CUDA graph; each outer step's CGLS loop
       // is a device-side WHILE node, so no host round trip happens until the end.
       s = sb_graph_run(st, gv, dprobs, P, outer_steps, o.i_max, ctrs, outer_head, cgls_iter, shrink,
-                       fz ? 3 + apply_launches : 3 + apply_launches,
-                       fz ? 4 + 2 * apply_launches : 4 + 2 * apply_launches);
+                       3 + ap_b, 4 + ap_f + ap_b);
       if (s) break;
     } else {
       // Instrumented path: host-driven loop (CUDA events around every KP apply), checking
@@ -917,8 +923,9 @@ extern "C" kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int 
   // group by image size; each group shares its launches
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return jobs[a].kp->n < jobs[b].kp->n; });
+  // groups: same n and same operator kind (Kronecker sum or explicit A)
+  auto gkey = [&](int i) { return 2LL * jobs[i].kp->n + (jobs[i].kp->A_dense ? 1 : 0); };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gkey(a) < gkey(b); });
   size_t host_bytes = 0;
   for (int i = 0; i < count; ++i) host_bytes += 2 * sizeof(double) * (size_t)jobs[i].kp->n * jobs[i].kp->n;
   double* dbuf = nullptr;
@@ -948,7 +955,7 @@ extern "C" kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int 
     int g1 = g0;
     const int n = jobs[order[g0]].kp->n;
     std::vector<SBJobIn> grp;
-    while (g1 < count && jobs[order[g1]].kp->n == n) {
+    while (g1 < count && gkey(order[g1]) == gkey(order[g0])) {
       const kpsb_sb_job& J = jobs[order[g1]];
       double beta = J.beta > 0.0 ? J.beta : J.lambda * J.lambda / 2.0;
       grp.push_back(SBJobIn{J.kp, db[order[g1]], dx[order[g1]], J.mu, J.lambda, beta, J.tv, J.iters});

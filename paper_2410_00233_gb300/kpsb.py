@@ -87,6 +87,7 @@ _SIGS = {
     "kp_from_factors": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                   C.POINTER(C.c_double), C.POINTER(C.c_void_p)]),
     "kp_apply": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_int]),
+    "kp_dense_blur": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
     "kp_apply_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "kp_free": (None, [C.c_void_p]),
     "sb_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_double, C.c_int, C.c_int,
@@ -236,6 +237,14 @@ def kp_from_factors(Ax, Ay, sigma) -> KP:
     sg = np.ascontiguousarray(sigma, dtype=np.float64)
     out = C.c_void_p()
     _check("kp_from_factors", lib().kp_from_factors(n, k, _pf(ax), _pf(ay), _pd(sg), C.byref(out)))
+    return KP(out.value)
+
+
+def kp_dense_blur(psf, n: int, bc: int) -> KP:
+    """Handle of the explicit blurring operator A (n^2 x n^2 FP64 on the device, n <= 128)."""
+    pf = _f64(psf)
+    out = C.c_void_p()
+    _check("kp_dense_blur", lib().kp_dense_blur(_pd(pf), pf.shape[0], pf.shape[1], int(n), int(bc), C.byref(out)))
     return KP(out.value)
 
 

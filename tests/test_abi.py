@@ -67,3 +67,6 @@ def test_invalid_arguments_fail_without_touching_the_gpu():
     with pytest.raises(K.KpsbError) as e:
         K.kp_build(np.ones((3, 3)), 16385, K.BC_ZERO, 2, K.EGKB)  # n above KPSB_MAX_N
     assert e.value.code == -1
+    with pytest.raises(K.KpsbError) as e:
+        K.kp_dense_blur(np.ones((3, 3)), 200, K.BC_ZERO)  # explicit A limited to n <= 128
+    assert e.value.code == -1
