@@ -1,40 +1,51 @@
 // Kronecker-sum operator apply (Sec. 4.2, eq. (4.3)) on CUDA cores, batched over problems:
 //   forward   Y  = sum_i sigma_i Ay_i X Ax_i^T
 //   transpose X' = sum_i sigma_i Ay_i^T Y Ax_i
-// as two GEMM stages per problem: Z_i = sigma_i X op(Ax_i) (one tile grid per term), then
-// Y = sum_i op(Ay_i) Z_i (K dimension = k*n).  FP64 mode accumulates in FP64 (the plain
+// as two GEMM stages per problem and term, Z_i = sigma_i X op(Ax_i) and W_i = op(Ay_i) Z_i,
+// then Y = sum_i W_i in term order (deterministic).  FP64 mode accumulates in FP64 (the plain
 // path); FP32 mode rounds X to FP32 and accumulates in FP32.
 #include "kpsb_internal.cuh"
 
 namespace kpsb {
 
-static constexpr int GB_M = 64, GB_N = 64, GB_K = 16, GB_T = 256;
+// 32 x 32 output tiles, K slices of 16, 256 threads with 2 x 2 outputs each: small tiles and
+// one CTA per (tile, term) in both stages keep a single n = 128 problem on ~16 k CTAs.
+static constexpr int GT = 32, GB_K = 16, GB_T = 256;
 
 // Work actually performed by the applies of this file (as in the tensor-core file):
 // [0] sum of k n^3 over active problems, [1] active problem-applies.
 __device__ unsigned long long g_simt_work[2] = {0, 0};
 
-template <typename T>
-struct TileOps;
-
-// Load a GB_K x 64 operand tile into smem s[kk][mm] from src(mm, kk) = base[mm*sm + kk*sk].
+// Load a GB_K x GT operand tile into smem s[kk][mm] from src(mm, kk) = base[mm*sm + kk*sk].
 template <typename TA, typename TS>
-__device__ __forceinline__ void load_tile(TS (*s)[GB_M + 1], const TA* __restrict__ base, int sm,
-                                          int sk, int mlim, int klim) {
-  if (sm == 1) {
+__device__ __forceinline__ void load_tile(TS (*s)[GT + 1], const TA* __restrict__ base, int sm, int sk,
+                                          int mlim, int klim) {
 #pragma unroll
-    for (int u = 0; u < (GB_M * GB_K) / GB_T; ++u) {
-      int e = threadIdx.x + u * GB_T;
-      int mm = e % GB_M, kk = e / GB_M;
-      s[kk][mm] = (mm < mlim && kk < klim) ? (TS)base[(size_t)mm + (size_t)kk * sk] : (TS)0;
+  for (int u = 0; u < (GT * GB_K) / GB_T; ++u) {
+    const int e = threadIdx.x + u * GB_T;
+    int mm, kk;
+    if (sm == 1) {  // contiguous along m
+      mm = e % GT;
+      kk = e / GT;
+    } else {        // contiguous along k
+      kk = e % GB_K;
+      mm = e / GB_K;
     }
-  } else {
+    s[kk][mm] = (mm < mlim && kk < klim) ? (TS)base[(size_t)mm * sm + (size_t)kk * sk] : (TS)0;
+  }
+}
+
+// acc[x][y] += sum_kk As[kk][tx + 16x] Bs[kk][ty + 16y]
+template <typename TAcc>
+__device__ __forceinline__ void mma_tile(const TAcc (*As)[GT + 1], const TAcc (*Bs)[GT + 1], TAcc acc[2][2],
+                                         int tx, int ty) {
 #pragma unroll
-    for (int u = 0; u < (GB_M * GB_K) / GB_T; ++u) {
-      int e = threadIdx.x + u * GB_T;
-      int kk = e % GB_K, mm = e / GB_K;
-      s[kk][mm] = (mm < mlim && kk < klim) ? (TS)base[(size_t)mm * sm + (size_t)kk * sk] : (TS)0;
-    }
+  for (int kk = 0; kk < GB_K; ++kk) {
+    const TAcc a0 = As[kk][tx], a1 = As[kk][tx + 16], b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
+    acc[0][0] = fma(a0, b0, acc[0][0]);
+    acc[0][1] = fma(a0, b1, acc[0][1]);
+    acc[1][0] = fma(a1, b0, acc[1][0]);
+    acc[1][1] = fma(a1, b1, acc[1][1]);
   }
 }
 
@@ -46,112 +57,93 @@ __global__ void __launch_bounds__(GB_T) kp_stage1_kernel(const KPJob* __restrict
   const int i = blockIdx.y;
   if (i >= J.k || (J.active && !*J.active)) return;
   const int n = J.n;
-  const int tiles_m = (n + GB_M - 1) / GB_M;
-  const int m0 = (blockIdx.x % tiles_m) * GB_M, n0 = (blockIdx.x / tiles_m) * GB_N;
+  const int tiles_m = (n + GT - 1) / GT;
+  const int m0 = (blockIdx.x % tiles_m) * GT, n0 = (blockIdx.x / tiles_m) * GT;
   if (n0 >= n) return;
-  __shared__ TAcc As[GB_K][GB_M + 1];
-  __shared__ TAcc Bs[GB_K][GB_N + 1];
+  __shared__ TAcc As[GB_K][GT + 1];
+  __shared__ TAcc Bs[GB_K][GT + 1];
   const float* Ax = J.Ax + (size_t)i * n * n;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  TAcc acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  TAcc acc[2][2] = {{0, 0}, {0, 0}};
   for (int k0 = 0; k0 < n; k0 += GB_K) {
-    // A(r, l) = X[r + l n]
-    load_tile<double, TAcc>(As, J.X + m0 + (size_t)k0 * n, 1, n, n - m0, n - k0);
-    // B(l, j): forward Ax[j + l n] (j stride 1), transpose Ax[l + j n] (l stride 1)
+    load_tile<double, TAcc>(As, J.X + m0 + (size_t)k0 * n, 1, n, n - m0, n - k0);  // X(r, l)
     if (!transpose)
-      load_tile<float, TAcc>(Bs, Ax + n0 + (size_t)k0 * n, 1, n, n - n0, n - k0);
+      load_tile<float, TAcc>(Bs, Ax + n0 + (size_t)k0 * n, 1, n, n - n0, n - k0);  // Ax(j, l)
     else
-      load_tile<float, TAcc>(Bs, Ax + (size_t)n0 * n + k0, n, 1, n - n0, n - k0);
+      load_tile<float, TAcc>(Bs, Ax + (size_t)n0 * n + k0, n, 1, n - n0, n - k0);  // Ax(l, j)
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GB_K; ++kk) {
-      TAcc a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[kk][tx + 16 * u];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) b[u] = Bs[kk][ty + 16 * u];
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
-    }
+    mma_tile<TAcc>(As, Bs, acc, tx, ty);
     __syncthreads();
   }
   const TAcc sg = (TAcc)J.sigma[i];
   TZ* Z = (TZ*)J.Z + (size_t)i * n * n;
 #pragma unroll
-  for (int y = 0; y < 4; ++y) {
-    int c = n0 + ty + 16 * y;
-    if (c >= n) continue;
+  for (int y = 0; y < 2; ++y) {
+    const int c = n0 + ty + 16 * y;
 #pragma unroll
-    for (int x = 0; x < 4; ++x) {
-      int r = m0 + tx + 16 * x;
-      if (r < n) Z[r + (size_t)c * n] = (TZ)(sg * acc[x][y]);
+    for (int x = 0; x < 2; ++x) {
+      const int r = m0 + tx + 16 * x;
+      if (r < n && c < n) Z[r + (size_t)c * n] = (TZ)(sg * acc[x][y]);
     }
   }
 }
 
-// Stage 2: Y(r, c) = sum_i sum_l A_i(r, l) Z_i(l, c), A_i(r, l) = Ay_i(r, l) (forward) or
-// Ay_i(l, r) (transpose).  grid = (tiles, 1, njobs).
+// Stage 2, one term per CTA: W_i(r, c) = sum_l A_i(r, l) Z_i(l, c), A_i(r, l) = Ay_i(r, l)
+// (forward) or Ay_i(l, r) (transpose), into the partial buffer after Z.  grid = (tiles,
+// kmax, njobs).
 template <typename TAcc, typename TZ>
 __global__ void __launch_bounds__(GB_T) kp_stage2_kernel(const KPJob* __restrict__ jobs, int transpose) {
   const KPJob J = jobs[blockIdx.z];
-  if (J.active && !*J.active) return;
+  const int i = blockIdx.y;
+  if (i >= J.k || (J.active && !*J.active)) return;
   const int n = J.n;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && i == 0 && threadIdx.x == 0) {
     atomicAdd(&g_simt_work[0], (unsigned long long)J.k * n * n * n);
     atomicAdd(&g_simt_work[1], 1ull);
   }
-  const int tiles_m = (n + GB_M - 1) / GB_M;
-  const int m0 = (blockIdx.x % tiles_m) * GB_M, n0 = (blockIdx.x / tiles_m) * GB_N;
+  const int tiles_m = (n + GT - 1) / GT;
+  const int m0 = (blockIdx.x % tiles_m) * GT, n0 = (blockIdx.x / tiles_m) * GT;
   if (n0 >= n) return;
-  __shared__ TAcc As[GB_K][GB_M + 1];
-  __shared__ TAcc Bs[GB_K][GB_N + 1];
+  __shared__ TAcc As[GB_K][GT + 1];
+  __shared__ TAcc Bs[GB_K][GT + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  TAcc acc[4][4];
+  const size_t nn = (size_t)n * n;
+  const float* Ay = J.Ay + (size_t)i * nn;
+  const TZ* Z = (const TZ*)J.Z + (size_t)i * nn;
+  TAcc acc[2][2] = {{0, 0}, {0, 0}};
+  for (int k0 = 0; k0 < n; k0 += GB_K) {
+    if (!transpose)
+      load_tile<float, TAcc>(As, Ay + m0 + (size_t)k0 * n, 1, n, n - m0, n - k0);
+    else
+      load_tile<float, TAcc>(As, Ay + (size_t)m0 * n + k0, n, 1, n - m0, n - k0);
+    load_tile<TZ, TAcc>(Bs, Z + (size_t)n0 * n + k0, n, 1, n - n0, n - k0);  // Z(l, c)
+    __syncthreads();
+    mma_tile<TAcc>(As, Bs, acc, tx, ty);
+    __syncthreads();
+  }
+  TZ* W = (TZ*)J.Z + (size_t)J.k * nn + (size_t)i * nn;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int y = 0; y < 2; ++y) {
+    const int c = n0 + ty + 16 * y;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-  for (int i = 0; i < J.k; ++i) {
-    const float* Ay = J.Ay + (size_t)i * n * n;
-    const TZ* Z = (const TZ*)J.Z + (size_t)i * n * n;
-    for (int k0 = 0; k0 < n; k0 += GB_K) {
-      if (!transpose)
-        load_tile<float, TAcc>(As, Ay + m0 + (size_t)k0 * n, 1, n, n - m0, n - k0);
-      else
-        load_tile<float, TAcc>(As, Ay + (size_t)m0 * n + k0, n, 1, n - m0, n - k0);
-      // B(l, c) = Z[l + c n]
-      load_tile<TZ, TAcc>(Bs, Z + (size_t)n0 * n + k0, n, 1, n - n0, n - k0);
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < GB_K; ++kk) {
-        TAcc a[4], b[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = As[kk][tx + 16 * u];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) b[u] = Bs[kk][ty + 16 * u];
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
-      }
-      __syncthreads();
+    for (int x = 0; x < 2; ++x) {
+      const int r = m0 + tx + 16 * x;
+      if (r < n && c < n) W[r + (size_t)c * n] = (TZ)acc[x][y];
     }
   }
-#pragma unroll
-  for (int y = 0; y < 4; ++y) {
-    int c = n0 + ty + 16 * y;
-    if (c >= n) continue;
-#pragma unroll
-    for (int x = 0; x < 4; ++x) {
-      int r = m0 + tx + 16 * x;
-      if (r < n) J.Y[r + (size_t)c * n] = (double)acc[x][y];
-    }
+}
+
+// Y = sum_i W_i in term order.  grid = (blocks, njobs).
+template <typename TAcc, typename TZ>
+__global__ void kp_sum_terms_kernel(const KPJob* __restrict__ jobs) {
+  const KPJob J = jobs[blockIdx.y];
+  if (J.active && !*J.active) return;
+  const size_t nn = (size_t)J.n * J.n;
+  const TZ* W = (const TZ*)J.Z + (size_t)J.k * nn;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+    TAcc s = 0;
+    for (int i = 0; i < J.k; ++i) s += (TAcc)W[(size_t)i * nn + e];
+    J.Y[e] = (double)s;
   }
 }
 
@@ -164,30 +156,34 @@ kpsb_status simt_work(unsigned long long* out, bool reset) {
   return KPSB_OK;
 }
 
+// Z (k n^2) and the per-term partials W (k n^2), in the accumulation type.
 size_t kp_z_bytes(int n, int k, int prec) {
   size_t el = prec == KPSB_P_FP64 ? sizeof(double) : sizeof(float);
-  return el * (size_t)n * n * k;
+  return 2 * el * (size_t)n * n * k;
+}
+
+template <typename TAcc>
+static kpsb_status launch_simt(const KPJob* jobs_d, int njobs, int n, int kmax, int transpose, cudaStream_t st) {
+  const int tiles = ((n + GT - 1) / GT) * ((n + GT - 1) / GT);
+  dim3 g12(tiles, kmax, njobs);
+  kp_stage1_kernel<TAcc, TAcc><<<g12, GB_T, 0, st>>>(jobs_d, transpose);
+  KPSB_CHECK_LAUNCH();
+  kp_stage2_kernel<TAcc, TAcc><<<g12, GB_T, 0, st>>>(jobs_d, transpose);
+  KPSB_CHECK_LAUNCH();
+  const size_t nn = (size_t)n * n;
+  dim3 g3((unsigned)std::min<size_t>((nn + 255) / 256, 1024), njobs);
+  kp_sum_terms_kernel<TAcc, TAcc><<<g3, 256, 0, st>>>(jobs_d);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
 }
 
 kpsb_status kp_apply_batch(const KPJob* jobs_d, int njobs, int n, int kmax, int transpose, int prec,
                            cudaStream_t st) {
   if (njobs <= 0 || kmax <= 0) return KPSB_OK;
-  const int tiles = ((n + GB_M - 1) / GB_M) * ((n + GB_N - 1) / GB_N);
-  dim3 g1(tiles, kmax, njobs), g2(tiles, 1, njobs);
-  if (prec == KPSB_P_FP64) {
-    kp_stage1_kernel<double, double><<<g1, GB_T, 0, st>>>(jobs_d, transpose);
-    KPSB_CHECK_LAUNCH();
-    kp_stage2_kernel<double, double><<<g2, GB_T, 0, st>>>(jobs_d, transpose);
-  } else if (prec == KPSB_P_FP32) {
-    kp_stage1_kernel<float, float><<<g1, GB_T, 0, st>>>(jobs_d, transpose);
-    KPSB_CHECK_LAUNCH();
-    kp_stage2_kernel<float, float><<<g2, GB_T, 0, st>>>(jobs_d, transpose);
-  } else {
-    set_error("precision %d is not a CUDA-core mode", prec);
-    return KPSB_EINVAL;
-  }
-  KPSB_CHECK_LAUNCH();
-  return KPSB_OK;
+  if (prec == KPSB_P_FP64) return launch_simt<double>(jobs_d, njobs, n, kmax, transpose, st);
+  if (prec == KPSB_P_FP32) return launch_simt<float>(jobs_d, njobs, n, kmax, transpose, st);
+  set_error("precision %d is not a CUDA-core mode", prec);
+  return KPSB_EINVAL;
 }
 
 }  // namespace kpsb
@@ -252,7 +248,7 @@ extern "C" kpsb_status kp_apply_dev(kpsb_kp_t kp, const double* X, double* Y, in
     } else {
       s = kp_apply_batch(Jd, 1, n, k, transpose, prec, st);
     }
-    gemm_timer_end(slot, st, 4.0 * k * (double)n * n * n, tc ? 1 : 2);
+    gemm_timer_end(slot, st, 4.0 * k * (double)n * n * n, tc ? 1 : 3);
   }
   // the descriptor copy is from host stack memory: wait for it before returning
   cudaError_t e2 = cudaStreamSynchronize(st);

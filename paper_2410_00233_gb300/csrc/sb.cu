@@ -11,6 +11,9 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <string>
+#include <thread>
+
 #include "kpsb_internal.cuh"
 
 namespace kpsb {
@@ -712,7 +715,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     const double apply_flops = 4.0 * ksum * (double)n * n * n;  // 4 k n^3 per problem (Sec. 4.2)
     if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, gemm_prec, st, &plan))) break;
     // kernel launches of one apply (forward / transpose)
-    const int apply_launches = tc ? (fz ? 1 : 3) - (tc && !fz && tc_plan_fused(plan) ? 1 : 0) : 2;
+    const int apply_launches = tc ? (fz ? 1 : 3) - (tc && !fz && tc_plan_fused(plan) ? 1 : 0) : 3;
     const int ap_f = dense ? 2 : apply_launches, ap_b = dense ? 1 : apply_launches;
     const bool timed = gemm_timing_enabled();
     // One KP apply of the whole batch on stream sx (timed with events in instrumented mode).
@@ -950,24 +953,73 @@ extern "C" kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int 
     set_error("sb_solve_batched upload: %s", cudaGetErrorString(e));
     s = KPSB_ECUDA;
   }
-  int g0 = 0;
-  while (s == KPSB_OK && g0 < count) {
+  // groups [g0, g1) of the sorted order
+  std::vector<std::pair<int, int>> groups;
+  for (int g0 = 0; g0 < count;) {
     int g1 = g0;
-    const int n = jobs[order[g0]].kp->n;
-    std::vector<SBJobIn> grp;
-    while (g1 < count && gkey(order[g1]) == gkey(order[g0])) {
-      const kpsb_sb_job& J = jobs[order[g1]];
-      double beta = J.beta > 0.0 ? J.beta : J.lambda * J.lambda / 2.0;
-      grp.push_back(SBJobIn{J.kp, db[order[g1]], dx[order[g1]], J.mu, J.lambda, beta, J.tv, J.iters});
-      ++g1;
-    }
-    std::vector<kpsb_sb_stats> stv;
-    s = sb_run_group(grp, o, st, stv);
-    if (s == KPSB_OK)
-      for (int t = g0; t < g1; ++t)
-        if (jobs[order[t]].stats) *jobs[order[t]].stats = stv[t - g0];
+    while (g1 < count && gkey(order[g1]) == gkey(order[g0])) ++g1;
+    groups.emplace_back(g0, g1);
     g0 = g1;
   }
+  std::vector<kpsb_status> gs(groups.size(), KPSB_OK);
+  std::vector<std::string> gerr(groups.size());
+  auto run_group = [&](size_t gi, cudaStream_t gst) {
+    std::vector<SBJobIn> grp;
+    for (int t = groups[gi].first; t < groups[gi].second; ++t) {
+      const kpsb_sb_job& J = jobs[order[t]];
+      double beta = J.beta > 0.0 ? J.beta : J.lambda * J.lambda / 2.0;
+      grp.push_back(SBJobIn{J.kp, db[order[t]], dx[order[t]], J.mu, J.lambda, beta, J.tv, J.iters});
+    }
+    std::vector<kpsb_sb_stats> stv;
+    gs[gi] = sb_run_group(grp, o, gst, stv);
+    if (gs[gi] == KPSB_OK) {
+      for (int t = groups[gi].first; t < groups[gi].second; ++t)
+        if (jobs[order[t]].stats) *jobs[order[t]].stats = stv[t - groups[gi].first];
+    } else {
+      gerr[gi] = kpsb_last_error();
+    }
+  };
+  if (s == KPSB_OK && groups.size() == 1) {
+    run_group(0, st);
+  } else if (s == KPSB_OK) {
+    // Size groups are independent: each runs on its own stream from its own host thread,
+    // so small latency-bound groups overlap the large ones.  Every group starts after the
+    // uploads on st; the downloads below start after every group has synchronised.
+    int dev = 0;
+    cudaEvent_t up = nullptr;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&up, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(up, st);
+    if (e != cudaSuccess) {
+      set_error("sb_solve_batched: %s", cudaGetErrorString(e));
+      s = KPSB_ECUDA;
+    } else {
+      std::vector<std::thread> th;
+      for (size_t gi = 0; gi < groups.size(); ++gi)
+        th.emplace_back([&, gi] {
+          cudaStream_t gst = nullptr;
+          cudaError_t ge = cudaSetDevice(dev);
+          if (ge == cudaSuccess) ge = cudaStreamCreateWithFlags(&gst, cudaStreamNonBlocking);
+          if (ge == cudaSuccess) ge = cudaStreamWaitEvent(gst, up, 0);
+          if (ge == cudaSuccess) {
+            run_group(gi, gst);
+            ge = cudaStreamSynchronize(gst);
+          }
+          if (gst) cudaStreamDestroy(gst);
+          if (ge != cudaSuccess && gs[gi] == KPSB_OK) {
+            gs[gi] = KPSB_ECUDA;
+            gerr[gi] = std::string("size group stream: ") + cudaGetErrorString(ge);
+          }
+        });
+      for (auto& t : th) t.join();
+    }
+    if (up) cudaEventDestroy(up);
+  }
+  for (size_t gi = 0; gi < groups.size() && s == KPSB_OK; ++gi)
+    if (gs[gi] != KPSB_OK) {
+      set_error("%s", gerr[gi].c_str());
+      s = gs[gi];
+    }
   if (s == KPSB_OK && !on_device) {
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
       size_t nn = (size_t)jobs[i].kp->n * jobs[i].kp->n;
