@@ -130,6 +130,16 @@ kpsb_status kp_info(kpsb_kp_t kp, int* n, int* k, int* kp_size, double* sigma);
  * Any pointer may be NULL. */
 kpsb_status kp_get_factors(kpsb_kp_t kp, float* Ax, float* Ay, double* sigma);
 
+/* Kronecker-product sum of a general operator (no PSF structure; the extension the paper
+ * names as future work, Sec. 6): the TSVD of R(A) (Alg. 1 / Alg. 2, same options and
+ * rank rules as kp_build) with R(A) read from the explicit matrix by eq. (2.2).  A: host,
+ * N x N FP64 column-major (N = n^2, 2 <= n <= 128), copied once to the device in single
+ * precision for the TSVD as in Sec. 1; block (i, j) of A (rows i n.., columns j n..) is row
+ * i + j n of R(A), so the terms satisfy A ~= sum sigma_i Ax_i (x) Ay_i for column-major vec.
+ * The caller keeps A; the handle owns the factors (kp_free). */
+kpsb_status kp_build_dense(const double* A, int n, double rank_or_tol, int method,
+                           const kpsb_build_opts* opts, kpsb_kp_t* out);
+
 /* Handle of the exact blurring operator A itself as an explicit dense matrix (eq. (1.1);
  * the direct method of the paper's comparison, Sec. 4.3 case (i), Table 4 rows "A"):
  * A is n^2 x n^2 FP64 column-major on the device (2 GiB at n = 128), built from the PSF

@@ -191,7 +191,18 @@ struct BuildWork {
   EgkbState* st = nullptr;
   RAScratch ra;
   RedScratch red;
+  const float* A32 = nullptr;  // general operator: explicit A in FP32 (no PSF), or null
 };
+
+// R(A) products of the build: the PSF's index map, or the explicit matrix when one is given.
+static kpsb_status rop_apply(const BuildWork& w, int s0, int s1, int n, int bc, const float* V, int ldv,
+                             int nb, float* U, int ldu, int transpose, const float* prev, int ldp,
+                             const double* beta_dev, float beta_host, const int* skip, cudaStream_t st) {
+  if (w.A32)
+    return ra_dense_apply(w.A32, n, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host, skip, st);
+  return ra_apply(w.psf, s0, s1, n, bc, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host, skip,
+                  w.ra, st);
+}
 
 static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -276,8 +287,8 @@ static kpsb_status egkb_run(BuildWork& w, int n, int s0, int s1, int bc, const E
   KPSB_CHECK_LAUNCH();
   KPSB_TRY(la_scale_inv(w.S, N, d_norm, gate + 2, st));
   // q_1 = R^T s_1 / alpha_1
-  KPSB_TRY(ra_apply(w.psf, s0, s1, n, bc, w.S, (int)N, 1, w.Q, (int)N, 1, nullptr, 0, nullptr, 0.f,
-                    gate + 3, w.ra, st));
+  KPSB_TRY(rop_apply(w, s0, s1, n, bc, w.S, (int)N, 1, w.Q, (int)N, 1, nullptr, 0, nullptr, 0.f,
+                    gate + 3, st));
   KPSB_TRY(la_norm(w.Q, N, d_norm, w.red, gate + 3, st));
   egkb_after_alpha<<<1, 1, 0, st>>>(w.st, P, 1);
   KPSB_CHECK_LAUNCH();
@@ -295,8 +306,8 @@ static kpsb_status egkb_run(BuildWork& w, int n, int s0, int s1, int bc, const E
     const int* gs = gate + 2 * j;
     const int* gq = gate + 2 * j + 1;
     // s-phase
-    status = ra_apply(w.psf, s0, s1, n, bc, qjm1, (int)N, 1, sj, (int)N, 0, sjm1, (int)N,
-                      d_coef_s, 0.f, gs, w.ra, st);
+    status = rop_apply(w, s0, s1, n, bc, qjm1, (int)N, 1, sj, (int)N, 0, sjm1, (int)N,
+                      d_coef_s, 0.f, gs, st);
     if (status) break;
     status = cgs2(w.S, (int)N, full_reorth ? j - 1 : 0, sj, N, w.h, d_norm, w.red, gs, st);
     if (status) break;
@@ -306,8 +317,8 @@ static kpsb_status egkb_run(BuildWork& w, int n, int s0, int s1, int bc, const E
     if (status) break;
     if (j == kpmax + 1) break;  // only s_{kp+1} is needed from the last step
     // q-phase
-    status = ra_apply(w.psf, s0, s1, n, bc, sj, (int)N, 1, qj, (int)N, 1, qjm1, (int)N,
-                      d_coef_q, 0.f, gq, w.ra, st);
+    status = rop_apply(w, s0, s1, n, bc, sj, (int)N, 1, qj, (int)N, 1, qjm1, (int)N,
+                      d_coef_q, 0.f, gq, st);
     if (status) break;
     status = cgs2(w.Q, (int)N, j - 1, qj, N, w.h, d_norm, w.red, gq, st);
     if (status) break;
@@ -362,7 +373,7 @@ static kpsb_status handle_alloc(kpsb_kp** out, int n, int k, int kpsize) {
   return KPSB_OK;
 }
 
-static kpsb_status build_egkb(const float* psf_host, int s0, int s1, int n, int bc, int k,
+static kpsb_status build_egkb(const float* A32, const float* psf_host, int s0, int s1, int n, int bc, int k,
                               double tau, const kpsb_build_opts& o, cudaStream_t st, kpsb_kp** out) {
   EgkbParams P;
   P.k_fixed = tau > 0.0 ? 0 : k;
@@ -376,6 +387,7 @@ static kpsb_status build_egkb(const float* psf_host, int s0, int s1, int n, int 
   const long long N = (long long)n * n;
   BuildWork w;
   KPSB_TRY(work_alloc(w, n, s0, s1, kpmax, 1, st));
+  w.A32 = A32;
   kpsb_status s = KPSB_OK;
   do {
     cudaError_t e = cudaMemcpyAsync(w.psf, psf_host, sizeof(float) * s0 * s1, cudaMemcpyHostToDevice, st);
@@ -459,13 +471,14 @@ static kpsb_status svqb2(BuildWork& w, float* Y, long long N, int m, cudaStream_
 // Alg. 2 with q power iterations: Y = R F, orthonormalised after every apply of R or R^T
 // (step 2-3), H^T = R^T Q (step 4), SVD of H through the eigen-decomposition of H H^T
 // (k_p x k_p, FP64; step 5), U = Q U_H (step 6), V = H^T U_H Sigma^{-1}, truncation (step 7).
-static kpsb_status build_rsvd(const float* psf_host, int s0, int s1, int n, int bc, int k,
+static kpsb_status build_rsvd(const float* A32, const float* psf_host, int s0, int s1, int n, int bc, int k,
                               const kpsb_build_opts& o, cudaStream_t st, kpsb_kp** out) {
   const int kp = k + o.p;
   KPSB_REQUIRE(kp <= KP_MAX, "k + p = %d exceeds %d", kp, KP_MAX);
   const long long N = (long long)n * n;
   BuildWork w;
   KPSB_TRY(work_alloc(w, n, s0, s1, kp, kp, st));
+  w.A32 = A32;
   kpsb_status s = KPSB_OK;
   do {
     cudaError_t e = cudaMemcpyAsync(w.psf, psf_host, sizeof(float) * s0 * s1, cudaMemcpyHostToDevice, st);
@@ -479,22 +492,22 @@ static kpsb_status build_rsvd(const float* psf_host, int s0, int s1, int n, int 
       if (s) break;
     }
     float* Y = w.Q;
-    s = ra_apply(w.psf, s0, s1, n, bc, F, (int)N, kp, Y, (int)N, 0, nullptr, 0, nullptr, 0.f,
-                 nullptr, w.ra, st);
+    s = rop_apply(w, s0, s1, n, bc, F, (int)N, kp, Y, (int)N, 0, nullptr, 0, nullptr, 0.f,
+                 nullptr, st);
     if (!s) s = svqb2(w, Y, N, kp, st);
     for (int it = 0; it < o.power_iters && !s; ++it) {
-      s = ra_apply(w.psf, s0, s1, n, bc, Y, (int)N, kp, F, (int)N, 1, nullptr, 0, nullptr, 0.f,
-                   nullptr, w.ra, st);
+      s = rop_apply(w, s0, s1, n, bc, Y, (int)N, kp, F, (int)N, 1, nullptr, 0, nullptr, 0.f,
+                   nullptr, st);
       if (!s) s = svqb2(w, F, N, kp, st);
-      if (!s) s = ra_apply(w.psf, s0, s1, n, bc, F, (int)N, kp, Y, (int)N, 0, nullptr, 0, nullptr,
-                           0.f, nullptr, w.ra, st);
+      if (!s) s = rop_apply(w, s0, s1, n, bc, F, (int)N, kp, Y, (int)N, 0, nullptr, 0, nullptr,
+                           0.f, nullptr, st);
       if (!s) s = svqb2(w, Y, N, kp, st);
     }
     if (s) break;
     // H^T = R^T Q  (N x kp) into F
     float* Ht = F;
-    s = ra_apply(w.psf, s0, s1, n, bc, Y, (int)N, kp, Ht, (int)N, 1, nullptr, 0, nullptr, 0.f,
-                 nullptr, w.ra, st);
+    s = rop_apply(w, s0, s1, n, bc, Y, (int)N, kp, Ht, (int)N, 1, nullptr, 0, nullptr, 0.f,
+                 nullptr, st);
     if (s) break;
     double* G = w.small;
     double* U = G + 64 * 64;
@@ -578,8 +591,59 @@ extern "C" kpsb_status kp_build(const double* psf, int s0, int s1, int n, int bc
   std::vector<float> pf((size_t)s0 * s1);
   for (size_t i = 0; i < pf.size(); ++i) pf[i] = (float)psf[i];
   cudaStream_t st = (cudaStream_t)o.stream;
-  if (method == KPSB_EGKB) return build_egkb(pf.data(), s0, s1, n, bc, k, tau, o, st, out);
-  return build_rsvd(pf.data(), s0, s1, n, bc, k, o, st, out);
+  if (method == KPSB_EGKB) return build_egkb(nullptr, pf.data(), s0, s1, n, bc, k, tau, o, st, out);
+  return build_rsvd(nullptr, pf.data(), s0, s1, n, bc, k, o, st, out);
+}
+
+extern "C" kpsb_status kp_build_dense(const double* A, int n, double rank_or_tol, int method,
+                                      const kpsb_build_opts* opts, kpsb_kp_t* out) {
+  clear_error();
+  KPSB_REQUIRE(A && out, "null pointer");
+  *out = nullptr;
+  KPSB_REQUIRE(n >= 2 && n <= 128, "explicit operator limited to n in [2, 128] (got %d)", n);
+  KPSB_REQUIRE(method == KPSB_EGKB || method == KPSB_RSVD, "unknown method %d", method);
+  KPSB_REQUIRE(rank_or_tol > 0.0 && isfinite(rank_or_tol), "rank_or_tol must be > 0");
+  kpsb_build_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  double tau = 0.0;
+  int k;
+  if (rank_or_tol >= 1.0) {
+    k = (int)rank_or_tol;
+  } else {
+    KPSB_REQUIRE(method == KPSB_EGKB, "automatic rank needs EGKB (RSVD takes a fixed k)");
+    tau = rank_or_tol;
+    k = K_CAP;
+  }
+  KPSB_REQUIRE(k >= 1 && k <= KP_MAX, "rank %d outside [1, %d]", k, KP_MAX);
+  if (o.p <= 0) o.p = std::max(2, (k + 3) / 4);
+  if (o.power_iters <= 0) o.power_iters = 1;
+  if (o.k_min <= 0) o.k_min = 3;
+  KPSB_REQUIRE(std::min(k, K_CAP) + o.p <= KP_MAX || tau == 0.0, "k_cap + p exceeds %d", KP_MAX);
+  // the SP copy of A on the device (the R(A) products of the TSVD read it; Sec. 1)
+  const size_t NN = (size_t)n * n * n * n;
+  std::vector<float> a32(NN);
+  for (size_t i = 0; i < NN; ++i) a32[i] = (float)A[i];
+  float* dA = nullptr;
+  KPSB_TRY_CUDA(cudaMalloc((void**)&dA, sizeof(float) * NN));
+  cudaError_t e = cudaMemcpy(dA, a32.data(), sizeof(float) * NN, cudaMemcpyHostToDevice);
+  kpsb_status s = KPSB_OK;
+  if (e != cudaSuccess) {
+    set_error("explicit operator upload: %s", cudaGetErrorString(e));
+    s = KPSB_ECUDA;
+  } else {
+    const float one = 1.0f;  // unused 1 x 1 PSF: the products come from A
+    cudaStream_t st = (cudaStream_t)o.stream;
+    s = method == KPSB_EGKB ? build_egkb(dA, &one, 1, 1, n, KPSB_BC_ZERO, k, tau, o, st, out)
+                            : build_rsvd(dA, &one, 1, 1, n, KPSB_BC_ZERO, k, o, st, out);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (s == KPSB_OK && e2 != cudaSuccess) {
+      set_error("kp_build_dense: %s", cudaGetErrorString(e2));
+      s = KPSB_ECUDA;
+    }
+  }
+  cudaFree(dA);
+  return s;
 }
 
 extern "C" kpsb_status kp_info(kpsb_kp_t kp, int* n, int* k, int* kp_size, double* sigma) {

@@ -18,6 +18,11 @@ struct RAScratch {
 size_t ra_scratch_bytes(int n, int nb, int s_exp);
 RAScratch ra_scratch_carve(void* base, int n, int nb, int s_exp);
 kpsb_status ra_check(int s0, int s1, int n, int bc);
+// The same products for a general operator given as an explicit FP32 matrix A (N x N,
+// column-major): R(A)[i + j n, p + q n] = A[(i n + p) + (j n + q) N] (ra_dense.cu).
+kpsb_status ra_dense_apply(const float* A, int n, const float* V, int ldv, int nb, float* U, int ldu,
+                           int transpose, const float* prev, int ldp, const double* beta_dev,
+                           float beta_host, const int* skip, cudaStream_t st);
 // U = R(A) V (or R(A)^T V) [+ beta * prev], beta read from beta_dev when non-null.
 // skip (device int, may be null): when *skip != 0 the expand step writes nothing.
 kpsb_status ra_apply(const float* psf, int s0, int s1, int n, int bc, const float* V, int ldv,

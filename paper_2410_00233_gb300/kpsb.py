@@ -88,6 +88,8 @@ _SIGS = {
                                   C.POINTER(C.c_double), C.POINTER(C.c_void_p)]),
     "kp_apply": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_int]),
     "kp_dense_blur": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "kp_build_dense": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.c_double, C.c_int, C.POINTER(BuildOpts),
+                                 C.POINTER(C.c_void_p)]),
     "kp_apply_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "kp_free": (None, [C.c_void_p]),
     "sb_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_double, C.c_int, C.c_int,
@@ -203,6 +205,20 @@ def kp_build(psf, n: int, bc: int, rank_or_tol: float, method: int = EGKB, *, p=
     out = C.c_void_p()
     _check("kp_build", lib().kp_build(_pd(ps), ps.shape[0], ps.shape[1], int(n), int(bc),
                                       float(rank_or_tol), int(method), C.byref(o), C.byref(out)))
+    del keep
+    return KP(out.value)
+
+
+def kp_build_dense(A, n: int, rank_or_tol: float, method: int = EGKB, *, p=0, k_min=0, one_sided=False,
+                   power_iters=0, seed=0, start=None, stream=0) -> KP:
+    """KP sum of a general operator given as an explicit (n^2 x n^2) matrix (see kp_build_dense)."""
+    a = _f64(A)
+    if a.shape != (n * n, n * n):
+        raise ValueError(f"A must be {n * n} x {n * n}")
+    o, keep = _build_opts(p, k_min, one_sided, power_iters, seed, start, stream)
+    out = C.c_void_p()
+    _check("kp_build_dense", lib().kp_build_dense(_pd(a), int(n), float(rank_or_tol), int(method), C.byref(o),
+                                                  C.byref(out)))
     del keep
     return KP(out.value)
 

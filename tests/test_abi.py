@@ -70,3 +70,8 @@ def test_invalid_arguments_fail_without_touching_the_gpu():
     with pytest.raises(K.KpsbError) as e:
         K.kp_dense_blur(np.ones((3, 3)), 200, K.BC_ZERO)  # explicit A limited to n <= 128
     assert e.value.code == -1
+    import ctypes
+
+    dummy = (ctypes.c_double * 4)()
+    out = ctypes.c_void_p()
+    assert K.lib().kp_build_dense(dummy, 200, 3.0, K.EGKB, None, ctypes.byref(out)) == -1  # n > 128

@@ -79,3 +79,50 @@ def test_explicit_and_kp_jobs_in_one_batch_equal_alone():
     outs, stats = K.sb_solve_batched(jobs)
     for (x, st), xb, sb in zip(alone, outs, stats):
         assert np.array_equal(x, xb) and st.iota_total == sb.iota_total
+
+
+def _kron_operator(n, g, c=(5.0, 2.0, 1.0, 0.5), noise=1e-3):
+    """A general (non-PSF) operator: a short sum of Kronecker products plus a dense
+    perturbation, so R(A) has a clear leading rank-4 part and a noise floor."""
+    A = sum(ci * np.kron(g.standard_normal((n, n)), g.standard_normal((n, n))) for ci in c)
+    return A + noise * g.standard_normal(A.shape)
+
+
+@pytest.mark.parametrize("method", ["EGKB", "RSVD"])
+def test_general_operator_kp_build_matches_svd_of_rearrangement(method):
+    """kp_build_dense on an explicit operator without PSF structure: the leading singular
+    values equal those of the oracle's rearrangement R(A) (eq. (2.2)) from LAPACK, and the
+    rank-4 KP sum equals the best rank-4 approximation built from that SVD (Thm 2.1), within
+    single-precision tolerance."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    n, k = 16, 4
+    A = _kron_operator(n, I.rng(41))
+    R = O.rearrange(A, n, n, n, n)
+    U, S, Vt = np.linalg.svd(R)
+    kp = K.kp_build_dense(A, n, k, getattr(K, method), p=6, seed=5)
+    Ax, Ay, sig = K.kp_get_factors(kp)
+    assert np.max(np.abs(sig - S[:k])) <= 1e-4 * S[0]
+    best = sum(S[i] * np.kron(U[:, i].reshape(n, n, order="F"), Vt[i].reshape(n, n, order="F"))
+               for i in range(k))
+    got = sum(sig[i] * np.kron(Ax[i].astype(np.float64), Ay[i].astype(np.float64)) for i in range(k))
+    assert np.linalg.norm(got - best) <= 1e-4 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_explicit_blur_kp_build_matches_closed_form(bc):
+    """The explicit blur matrix through kp_build_dense has the singular values of the PSF's
+    closed form sigma(Gx^1/2 P^T Gy^1/2), the same as the index-map path."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    pr = I.problem_small(7)
+    n = pr.n
+    A = O.blur_matrix(pr.psf, n, bc)
+    ref = O.r_sigma_closed_form(O.r_factors(pr.psf, n, bc))
+    kp = K.kp_build_dense(A, n, 5, K.EGKB, p=4, seed=2)
+    sig = K.kp_info(kp)["sigma"]
+    assert np.max(np.abs(sig - ref[:5])) <= 1e-4 * ref[0]
+    kp2 = K.kp_build(pr.psf, n, bc, 5, K.EGKB, p=4, seed=2)
+    assert np.max(np.abs(K.kp_info(kp2)["sigma"] - sig)) <= 1e-4 * ref[0]
