@@ -94,6 +94,10 @@ typedef struct {
   int prec;          /* KPSB_P_* for the KP GEMMs; default KPSB_P_FP64 */
   int threshold_rule;/* KPSB_THR_EXACT (default) or KPSB_THR_PAPER */
   void* stream;      /* cudaStream_t */
+  int sub_batches;   /* sb_solve_batched: a size group of P problems is cut into this many
+                        parts that run concurrently on their own streams, so one part's
+                        FP64 vector kernels overlap another's tensor-core applies (results
+                        do not change).  0 (default): min(3, P / 64), at least 1; 1: off. */
 } kpsb_sb_opts;
 
 typedef struct {

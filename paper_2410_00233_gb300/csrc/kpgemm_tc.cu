@@ -820,7 +820,11 @@ struct RCfg {
   static constexpr int TILE = 128 * 128;                 // 128 rows x 32 K x 4 bytes
   static constexpr int X_BYTES = 2 * 4 * TILE;           // hi, lo planes; 4 K slices each
   static constexpr int SLOT = FPL * TILE;
-  static constexpr int STAGES = 96 * 1024 / SLOT;        // 6 (FPL 1) or 3 (FPL 2)
+#ifndef KPSB_RES_RING_KB
+#define KPSB_RES_RING_KB 96
+#endif
+  // ring of 16 KB planes: 96 KB gives 6 (FPL 1) or 3 (FPL 2) slots
+  static constexpr int STAGES = KPSB_RES_RING_KB * 1024 / SLOT;
   static constexpr int SMEM = X_BYTES + STAGES * SLOT + 1024 + 512;
 };
 

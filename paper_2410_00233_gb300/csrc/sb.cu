@@ -9,6 +9,7 @@
 // (horizontal, L_x (x) I), Dy along rows (vertical, I (x) L_y).
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -28,7 +29,10 @@ static constexpr int SB_T = 256;
 // Each block of a vector kernel handles one fixed chunk of SB_CHUNK elements (SB_EPT per
 // thread) and writes one reduction partial: the summation order depends on n only, so a
 // problem gives the same bits alone, in any batch, and in the serving loop.
-static constexpr int SB_EPT = 16;
+#ifndef KPSB_SB_EPT
+#define KPSB_SB_EPT 16
+#endif
+static constexpr int SB_EPT = KPSB_SB_EPT;  // 4, 8 or 16
 static constexpr int SB_CHUNK = SB_T * SB_EPT;
 static constexpr int SB_TILES_PER_CHUNK = SB_CHUNK / 1024;  // 32 x 32 tiles
 
@@ -849,6 +853,7 @@ kpsb_status sb_fill_defaults(const kpsb_sb_opts* opts, kpsb_sb_opts& o) {
   if (opts) o = *opts;
   if (o.tau_cgls <= 0.0) o.tau_cgls = 1e-4;
   if (o.i_max <= 0) o.i_max = 100;
+  KPSB_REQUIRE(o.sub_batches >= 0, "sub_batches must be >= 0 (got %d)", o.sub_batches);
   KPSB_REQUIRE(o.prec >= KPSB_P_FP64 && o.prec <= KPSB_P_TF32X2, "unknown precision %d", o.prec);
   KPSB_REQUIRE(o.threshold_rule == KPSB_THR_EXACT || o.threshold_rule == KPSB_THR_PAPER,
                "unknown threshold rule %d", o.threshold_rule);
@@ -953,12 +958,15 @@ extern "C" kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int 
     set_error("sb_solve_batched upload: %s", cudaGetErrorString(e));
     s = KPSB_ECUDA;
   }
-  // groups [g0, g1) of the sorted order
+  // groups [g0, g1) of the sorted order; a large group may be cut into parts that run
+  // concurrently (each part is an independent batch: same per-problem arithmetic)
   std::vector<std::pair<int, int>> groups;
   for (int g0 = 0; g0 < count;) {
     int g1 = g0;
     while (g1 < count && gkey(order[g1]) == gkey(order[g0])) ++g1;
-    groups.emplace_back(g0, g1);
+    const int size = g1 - g0;
+    const int np = std::max(1, std::min(size, o.sub_batches > 0 ? o.sub_batches : std::min(3, size / 64)));
+    for (int q = 0; q < np; ++q) groups.emplace_back(g0 + size * q / np, g0 + size * (q + 1) / np);
     g0 = g1;
   }
   std::vector<kpsb_status> gs(groups.size(), KPSB_OK);

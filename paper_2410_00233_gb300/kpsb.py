@@ -42,7 +42,7 @@ class BuildOpts(C.Structure):
 class SBOpts(C.Structure):
     _fields_ = [("beta", C.c_double), ("tau_sb", C.c_double), ("tau_cgls", C.c_double),
                 ("i_max", C.c_int), ("fixed_inner", C.c_int), ("prec", C.c_int),
-                ("threshold_rule", C.c_int), ("stream", C.c_void_p)]
+                ("threshold_rule", C.c_int), ("stream", C.c_void_p), ("sub_batches", C.c_int)]
 
 
 class SBStats(C.Structure):
@@ -277,11 +277,12 @@ def kp_apply_dev(kp: KP, X_ptr: int, Y_ptr: int, transpose: int = 0, prec: int =
 
 
 def _sb_opts(beta=0.0, tau_sb=0.0, tau_cgls=0.0, i_max=0, fixed_inner=False, prec=P_FP64,
-             threshold_rule=THR_EXACT, stream=0) -> SBOpts:
+             threshold_rule=THR_EXACT, stream=0, sub_batches=0) -> SBOpts:
     o = SBOpts()
     o.beta, o.tau_sb, o.tau_cgls = float(beta), float(tau_sb), float(tau_cgls)
     o.i_max, o.fixed_inner, o.prec, o.threshold_rule = int(i_max), int(bool(fixed_inner)), int(prec), int(threshold_rule)
     o.stream = C.c_void_p(int(stream)) if stream else None
+    o.sub_batches = int(sub_batches)
     return o
 
 

@@ -360,7 +360,29 @@ def test_persistent_apply_with_more_problems_than_sms():
         kps.append(K.kp_from_factors(Ax, Ay, sig))
         bs.append(g.standard_normal((n, n)))
     jobs = [dict(kp=kp, b=b, mu=1.0, lam=0.1, tv=K.ISO, iters=2) for kp, b in zip(kps, bs)]
-    outs, stats = K.sb_solve_batched(jobs, prec=K.P_TF32X2)
+    outs, stats = K.sb_solve_batched(jobs, prec=K.P_TF32X2, sub_batches=1)  # one part: 160 > SMs
     for p in (0, 7, 151, 152, 159):
         x, st = K.sb_solve(kps[p], bs[p], 1.0, 0.1, K.ISO, 2, prec=K.P_TF32X2)
         assert np.array_equal(x, outs[p]) and st.iota_total == stats[p].iota_total, p
+
+
+def test_sub_batches_give_the_same_bits():
+    """A batch cut into concurrent parts (sub_batches 1, 2, 3 and the default) returns the
+    same bits for every problem: each part is an independent batch of the same kernels."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    n, P = 128, 12
+    g = I.rng(91)
+    jobs = []
+    for p in range(P):
+        k = 2 + p % 5
+        kp = K.kp_from_factors((g.standard_normal((k, n, n)) / n).astype(np.float32),
+                               (g.standard_normal((k, n, n)) / n).astype(np.float32),
+                               np.sort(g.random(k))[::-1] + 0.1)
+        jobs.append(dict(kp=kp, b=g.standard_normal((n, n)), mu=1.0, lam=0.1, tv=K.ANISO, iters=2))
+    ref, st_ref = K.sb_solve_batched(jobs, prec=K.P_TF32X2, sub_batches=1)
+    for sb in (2, 3, 0):
+        outs, st = K.sb_solve_batched(jobs, prec=K.P_TF32X2, sub_batches=sb)
+        for a, b, s1, s2 in zip(ref, outs, st_ref, st):
+            assert np.array_equal(a, b) and s1.iota_total == s2.iota_total
