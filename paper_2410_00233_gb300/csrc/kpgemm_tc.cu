@@ -21,9 +21,12 @@
 // warps read their 32 TMEM lanes with tcgen05.ld and run the epilogue.  Every wait is
 // bounded: on timeout the CTA records an error code, drains and frees TMEM, and returns.
 #include <cuda.h>
+#include <stdio.h>
 #include <stdlib.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "kpsb_internal.cuh"
 
@@ -226,7 +229,8 @@ __device__ __forceinline__ float tf32_round(float x) {
 struct alignas(128) TCJob {
   CUtensorMap m1A;   // Xt planes: {n, n, 2}
   CUtensorMap m1B;   // T1 planes: {n, n, 2, k} (box 128 rows, two-stage kernel)
-  CUtensorMap m1F;   // T1 planes, box FUSED_BN rows (fused kernel)
+  CUtensorMap m1F;   // T1 planes, box 64 rows (fused kernel, BN = 64)
+  CUtensorMap m1G;   // T1 planes, box 32 rows (fused kernel, BN = 32)
   CUtensorMap m1R;   // T1 planes, box 128 rows (resident kernel, n = 128)
   CUtensorMap m2A;   // T2 planes: {k n, n, 2}
   CUtensorMap m2B;   // Zt planes: {k n, n, 2}
@@ -521,7 +525,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int c = c0 + cc + j;
-            if (c < n) J.Y[row + (size_t)c * n] = (double)v[j];
+            if (c < n) {
+              if (J.Yf) J.Yf[row + (size_t)c * n] = v[j];  // FP32 result for the CGLS kernels
+              else J.Y[row + (size_t)c * n] = (double)v[j];
+            }
           }
         }
       }
@@ -646,7 +653,8 @@ __global__ void __launch_bounds__(192, 1) tc_fused_kernel(const TCJob* __restric
   if (warp == 0 && lane == 0) {
     // ---- TMA producer: slots in the MMA's consumption order ----
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m1A) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m1F) : "memory");
+    const CUtensorMap* mF = BN == 64 ? &J.m1F : &J.m1G;  // T1 slices with BN-row boxes
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)mF) : "memory");
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m2A) : "memory");
     int si = 0;
     bool ok = true;
@@ -661,7 +669,7 @@ __global__ void __launch_bounds__(192, 1) tc_fused_kernel(const TCJob* __restric
           tma_load_3d(st, &J.m1A, &full[s], kb * 32, rc * 128, 0);
           tma_load_3d(st + C::XA_BYTES, &J.m1A, &full[s], kb * 32, rc * 128, 1);
           for (int pl = 0; pl < FPL; ++pl)
-            tma_load_4d(st + 2 * C::XA_BYTES + pl * C::TB_BYTES, &J.m1F, &full[s], kb * 32, c0, pl, i);
+            tma_load_4d(st + 2 * C::XA_BYTES + pl * C::TB_BYTES, mF, &full[s], kb * 32, c0, pl, i);
         }
       }
       if (v >= 1 && ok) {
@@ -1104,18 +1112,24 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
 // ------------------------------------------------------------------------------------------
 // Host side: plans (one per batched solve: tensor maps built once) and launches
 // ------------------------------------------------------------------------------------------
+// Apply variants.  Every one computes the same split products; the choice only moves time.
+enum { TCV_TWO_STAGE = 0, TCV_FUSED64 = 1, TCV_FUSED32 = 2, TCV_RESIDENT = 3, TCV_COUNT = 4 };
+
 struct TCPlan {
   TCJob* d_fwd = nullptr;
   TCJob* d_bwd = nullptr;
   float* work = nullptr;  // Xt and Zt of every problem
   int njobs = 0, n = 0, kmax = 0;
   int prec = KPSB_P_TF32X3;
-  bool fused = false;
+  bool fused = false;      // single-launch apply (the variant is not the two-stage pair)
+  int variant = 0;         // TCV_* chosen for this plan (autotuned, section below)
   bool ext_split = false;  // the caller writes the split planes (xt_ext)
   int* queue = nullptr;    // resident kernel: problem counter and finished-CTA counter (start at 0)
 };
 
 bool tc_plan_fused(const TCPlan* P) { return P && P->fused; }
+
+int tc_plan_launches(const TCPlan* P) { return (P->ext_split ? 0 : 1) + (P->fused ? 1 : 2); }
 
 static constexpr int S1_BN = 128, S1_STAGES = 3;
 static constexpr int S2_BN = 64, S2_STAGES = 4;
@@ -1154,7 +1168,15 @@ static kpsb_status launch_resident(const TCJob* jobs, int njobs, int* queue, cud
 }
 
 // n = 128 runs the resident kernel (KPSB_FUSED_TILED=1 selects the tiled fused kernel).
-static bool resident_ok(int n) { return n == 128 && !getenv("KPSB_FUSED_TILED"); }
+static bool variant_ok(int v, int n) {
+  switch (v) {
+    case TCV_TWO_STAGE: return true;
+    case TCV_FUSED64: return n % 128 == 0 && (n / 128 + 2) * 64 <= 512;
+    case TCV_FUSED32: return n % 128 == 0 && n <= 768;
+    case TCV_RESIDENT: return n == 128;
+    default: return false;
+  }
+}
 
 // Fused kernel where its TMEM fits (R + 2) x BN columns: n <= 768 with BN = 64.
 static bool fused_ok(int n) { return n % 128 == 0 && (n / 128 + 2) * FUSED_BN <= 512 && !getenv("KPSB_TWO_STAGE"); }
@@ -1192,10 +1214,11 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
     cuuint64_t s[3] = {fb * n, fb * n * n, fb * 2 * n * n};
     KPSB_TRY(make_map(&J.m1B, transpose ? T->T1t : T->T1f, 4, d, s, S1_BN));
   }
-  {  // T1 again with FUSED_BN-row boxes (fused kernel)
+  {  // T1 again with 64- and 32-row boxes (fused kernel)
     cuuint64_t d[4] = {(cuuint64_t)n, (cuuint64_t)n, 2, (cuuint64_t)k};
     cuuint64_t s[3] = {fb * n, fb * n * n, fb * 2 * n * n};
-    KPSB_TRY(make_map(&J.m1F, transpose ? T->T1t : T->T1f, 4, d, s, FUSED_BN));
+    KPSB_TRY(make_map(&J.m1F, transpose ? T->T1t : T->T1f, 4, d, s, 64));
+    KPSB_TRY(make_map(&J.m1G, transpose ? T->T1t : T->T1f, 4, d, s, 32));
   }
   {  // T1 with 128-row boxes (resident kernel)
     cuuint64_t d[4] = {(cuuint64_t)n, (cuuint64_t)n, 2, (cuuint64_t)k};
@@ -1215,6 +1238,86 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
   return KPSB_OK;
 }
 
+// ---- variant autotuner ----------------------------------------------------------------------
+// The first plan of each (n, precision, k_max, batch-size bucket, split mode) times every
+// valid variant on its own operands (one warm-up and two timed forward applies, CUDA events
+// on the plan's stream, activity flags ignored) and keeps the fastest for the process.
+// KPSB_TC_VARIANT=v forces variant v where valid; KPSB_TUNE_LOG=1 prints the choices.
+struct TuneKey {
+  int n, prec, kmax, pbucket, ext;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n, prec, kmax, pbucket, ext) < std::tie(o.n, o.prec, o.kmax, o.pbucket, o.ext);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tune;
+static kpsb_status launch_variant(const TCPlan* P, const TCJob* jobs, int variant, cudaStream_t st);
+
+static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStream_t st) {
+  const int n = P->n;
+  if (getenv("KPSB_TWO_STAGE")) { P->variant = TCV_TWO_STAGE; return KPSB_OK; }
+  if (const char* f = getenv("KPSB_TC_VARIANT")) {
+    const int v = atoi(f);
+    if (variant_ok(v, n)) { P->variant = v; return KPSB_OK; }
+  }
+  if (n == 128 && getenv("KPSB_FUSED_TILED")) { P->variant = TCV_FUSED64; return KPSB_OK; }
+  std::vector<int> cand;
+  for (int v = 0; v < TCV_COUNT; ++v)
+    if (variant_ok(v, n)) cand.push_back(v);
+  if (cand.size() == 1) { P->variant = cand[0]; return KPSB_OK; }
+  int pb = 1;
+  while (pb < P->njobs) pb <<= 1;
+  const TuneKey key{n, P->prec, P->kmax, pb, P->ext_split ? 1 : 0};
+  std::lock_guard<std::mutex> lk(g_tune_mu);  // one tuner at a time; later plans reuse the choice
+  auto it = g_tune.find(key);
+  if (it != g_tune.end()) { P->variant = it->second; return KPSB_OK; }
+  // operands as planned, without the activity flags (a new problem is not active yet)
+  std::vector<TCJob> tj(hf);
+  for (auto& J : tj) J.active = nullptr;
+  TCJob* dj = nullptr;
+  unsigned long long saved[2] = {0, 0};
+  cudaEvent_t a = nullptr, b = nullptr;
+  kpsb_status s = KPSB_OK;
+  cudaError_t e = cudaMallocAsync((void**)&dj, sizeof(TCJob) * P->njobs, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dj, tj.data(), sizeof(TCJob) * P->njobs, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(saved, g_tc_work, sizeof(saved));  // tuning is not work
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  int best = cand[0];
+  float best_ms = 0.f;
+  for (size_t c = 0; c < cand.size() && e == cudaSuccess && s == KPSB_OK; ++c) {
+    s = launch_variant(P, dj, cand[c], st);
+    if (s == KPSB_OK) e = cudaEventRecord(a, st);
+    for (int r = 0; r < 2 && s == KPSB_OK && e == cudaSuccess; ++r) s = launch_variant(P, dj, cand[c], st);
+    if (s == KPSB_OK && e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (s == KPSB_OK && e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (s == KPSB_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (s == KPSB_OK && e == cudaSuccess && (c == 0 || ms < best_ms)) {
+      best = cand[c];
+      best_ms = ms;
+    }
+    if (getenv("KPSB_TUNE_LOG") && e == cudaSuccess)
+      fprintf(stderr, "[kpsb tune] n=%d prec=%d kmax=%d jobs<=%d variant %d: %.3f ms\n", n, P->prec, P->kmax, pb,
+              cand[c], ms / 2);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_work, saved, sizeof(saved));
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (dj) cudaFreeAsync(dj, st);
+  if (s != KPSB_OK) return s;
+  if (e != cudaSuccess) {
+    set_error("tensor-core variant tuning: %s", cudaGetErrorString(e));
+    return KPSB_ECUDA;
+  }
+  if (s == KPSB_OK) s = tc_check_error();
+  if (s != KPSB_OK) return s;
+  g_tune[key] = best;
+  P->variant = best;
+  return KPSB_OK;
+}
+
 kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h, int njobs, int n,
                            int prec, cudaStream_t st, TCPlan** out) {
   KPSB_REQUIRE(tc_supported(n, prec), "tensor-core path needs n %% 128 == 0 (n = %d)", n);
@@ -1225,13 +1328,15 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
   KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 1>()));
   KPSB_TRY((prepare_fused<FUSED_BN, 1>()));
   KPSB_TRY((prepare_fused<FUSED_BN, 2>()));
+  KPSB_TRY((prepare_fused<32, 1>()));
+  KPSB_TRY((prepare_fused<32, 2>()));
   KPSB_TRY(prepare_resident<1>());
   KPSB_TRY(prepare_resident<2>());
   TCPlan* P = new TCPlan();
   P->njobs = njobs;
   P->n = n;
   P->prec = prec;
-  P->fused = fused_ok(n);
+  P->fused = fused_ok(n);  // the states carry split planes and FP32 outputs for a one-launch apply
   std::vector<TCTables*> tabs(njobs);
   size_t floats = 0;
   for (int p = 0; p < njobs; ++p) {
@@ -1282,6 +1387,12 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
     set_error("tensor-core plan upload: %s", cudaGetErrorString(e));
     return KPSB_ECUDA;
   }
+  kpsb_status ts = tune_variant(P, hf, st);
+  if (ts != KPSB_OK) {
+    tc_plan_free(P, st);
+    return ts;
+  }
+  P->fused = P->variant != TCV_TWO_STAGE;
   *out = P;
   return KPSB_OK;
 }
@@ -1302,6 +1413,26 @@ static kpsb_status launch_gemm(const TCJob* jobs, int njobs, int n, int kmax, cu
   return KPSB_OK;
 }
 
+static kpsb_status launch_variant(const TCPlan* P, const TCJob* jobs, int variant, cudaStream_t st) {
+  const int n = P->n;
+  const bool x3 = P->prec == KPSB_P_TF32X3;
+  switch (variant) {
+    case TCV_RESIDENT: return x3 ? launch_resident<2>(jobs, P->njobs, P->queue, st)
+                                 : launch_resident<1>(jobs, P->njobs, P->queue, st);
+    case TCV_FUSED64: return x3 ? launch_fused<64, 2>(jobs, P->njobs, n, st) : launch_fused<64, 1>(jobs, P->njobs, n, st);
+    case TCV_FUSED32: return x3 ? launch_fused<32, 2>(jobs, P->njobs, n, st) : launch_fused<32, 1>(jobs, P->njobs, n, st);
+    default: break;
+  }
+  if (x3) {
+    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 2>(jobs, P->njobs, n, P->kmax, st)));
+    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 2>(jobs, P->njobs, n, P->kmax, st)));
+  } else {
+    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 1>(jobs, P->njobs, n, P->kmax, st)));
+    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 1>(jobs, P->njobs, n, P->kmax, st)));
+  }
+  return KPSB_OK;
+}
+
 kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
   const TCJob* jobs = transpose ? P->d_bwd : P->d_fwd;
   const int n = P->n;
@@ -1310,22 +1441,7 @@ kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
     tc_split_kernel<<<gs, 256, 0, st>>>(jobs);
     KPSB_CHECK_LAUNCH();
   }
-  if (P->fused && resident_ok(n)) {
-    if (P->prec == KPSB_P_TF32X3) return launch_resident<2>(jobs, P->njobs, P->queue, st);
-    return launch_resident<1>(jobs, P->njobs, P->queue, st);
-  }
-  if (P->fused) {
-    if (P->prec == KPSB_P_TF32X3) return launch_fused<FUSED_BN, 2>(jobs, P->njobs, n, st);
-    return launch_fused<FUSED_BN, 1>(jobs, P->njobs, n, st);
-  }
-  if (P->prec == KPSB_P_TF32X3) {
-    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 2>(jobs, P->njobs, n, P->kmax, st)));
-    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 2>(jobs, P->njobs, n, P->kmax, st)));
-  } else {
-    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 1>(jobs, P->njobs, n, P->kmax, st)));
-    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 1>(jobs, P->njobs, n, P->kmax, st)));
-  }
-  return KPSB_OK;
+  return launch_variant(P, jobs, P->variant, st);
 }
 
 kpsb_status tc_work(unsigned long long* out, bool reset) {

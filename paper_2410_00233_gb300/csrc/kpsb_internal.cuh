@@ -159,6 +159,9 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
 kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st);
 // True when the plan runs the fused kernel with CGLS epilogues (inputs split by the caller).
 bool tc_plan_fused(const TCPlan* P);
+// Kernel launches of one apply of the plan (split kernel when not supplied, then one fused
+// launch or the two-stage pair).
+int tc_plan_launches(const TCPlan* P);
 // Column tiles of the fused kernel for size n, 0 if n is not handled by it.
 int tc_fused_tiles(int n, int prec);
 void tc_plan_free(TCPlan* P, cudaStream_t st);

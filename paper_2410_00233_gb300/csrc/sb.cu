@@ -719,7 +719,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     const double apply_flops = 4.0 * ksum * (double)n * n * n;  // 4 k n^3 per problem (Sec. 4.2)
     if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, gemm_prec, st, &plan))) break;
     // kernel launches of one apply (forward / transpose)
-    const int apply_launches = tc ? (fz ? 1 : 3) - (tc && !fz && tc_plan_fused(plan) ? 1 : 0) : 3;
+    const int apply_launches = tc ? tc_plan_launches(plan) : 3;
     const int ap_f = dense ? 2 : apply_launches, ap_b = dense ? 1 : apply_launches;
     const bool timed = gemm_timing_enabled();
     // One KP apply of the whole batch on stream sx (timed with events in instrumented mode).

@@ -246,9 +246,13 @@ def test_resident_fused_and_two_stage_tensor_core_paths_agree(prec_name, transpo
         op = _oracle_op(Ax, Ay, sig)
         ref = O.kp_apply_t(op, X) if transpose else O.kp_apply(op, X)
         ys = {}
-        for name, env in (("default", None), ("tiled", "KPSB_FUSED_TILED"), ("two_stage", "KPSB_TWO_STAGE")):
+        # default = the autotuned variant; KPSB_TC_VARIANT forces one (0 two-stage, 1 fused
+        # BN 64, 2 fused BN 32, 3 resident n = 128)
+        for name, env, val in (("default", None, None), ("tiled", "KPSB_FUSED_TILED", "1"),
+                               ("two_stage", "KPSB_TWO_STAGE", "1"), ("fused64", "KPSB_TC_VARIANT", "1"),
+                               ("fused32", "KPSB_TC_VARIANT", "2"), ("v0", "KPSB_TC_VARIANT", "0")):
             if env:
-                monkeypatch.setenv(env, "1")
+                monkeypatch.setenv(env, val)
             kp = K.kp_from_factors(Ax, Ay, sig)  # fresh handle: the path is chosen per plan
             ys[name] = K.kp_apply(kp, X, transpose, prec)
             if env:
