@@ -567,8 +567,17 @@ def main():
     # every forward apply is followed by one ||z||^2 kernel, every transpose apply by one f kernel
     phases["cgls_iterations_batch"] = phases["cgls_zz_launches"]
     gapplies = phases["cgls_zz_launches"] + phases["cgls_f_launches"]
-    pa, _ = K.kpsb_apply_counts()  # problem-applies actually performed (active problems)
+    pa, kn3 = K.kpsb_apply_counts()  # problem-applies actually performed (active problems), sum k n^3
     phases["active_problems_per_apply"] = pa / gapplies if gapplies else None
+    # DRAM traffic of the n = 128 resident apply (TF32x2), scaled from one ncu capture of the
+    # same kernel on 4 requests with distinct operators (4.529 MB read, nothing written back:
+    # the outputs stay in L2) by the units it reads: per active problem the split iterate
+    # (128 KB) and 128 KB of tables per term, i.e. (k + 1) units; that capture held
+    # sum (k + 1) = 35 units.
+    traffic = None
+    if prec == K.P_TF32X2 and N_IMG == 128 and gapplies and pa:
+        units_per_launch = (kn3 / N_IMG ** 3 + pa) / gapplies
+        traffic = 4529280.0 / 35.0 * units_per_launch
     K.kpsb_gemm_timing(False)
     # ISNR of the mixed path on the first timed step
     reqs = steps_in[W]
@@ -660,7 +669,9 @@ def main():
             peak = 152 * 2 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             roof = {"bound": "alu", "peak_note": "FP64 FMA: 152 SM x 2 lanes x 2 x max SM clock"}
         roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_note": "bytes per launch (DRAM read + write), scaled from an ncu capture of the "
+                                     "same kernel at 4 requests by (k + 1) units per active problem",
                      "kernel": ("KP apply: fused tensor-core kernel, 1 launch per apply" if gl and gl == gapplies
                                 else "KP apply (%d launches per apply)" % round(gl / max(1, gapplies))),
                      "launches": gl, "kernel_ms": gms, "instrumented_step_s": t_instr,
