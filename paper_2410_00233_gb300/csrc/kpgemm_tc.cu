@@ -1161,7 +1161,9 @@ static kpsb_status launch_resident(const TCJob* jobs, int njobs, int* queue, cud
   int dev = 0, sms = 0;
   KPSB_TRY_CUDA(cudaGetDevice(&dev));
   KPSB_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = std::max(1, std::min(njobs, sms));  // persistent: one CTA per SM at most
+  // persistent: one CTA per SM at most (fewer CTAs than problems measured slower: each
+  // concurrent part's iteration waits for its own apply)
+  const int grid = std::max(1, std::min(njobs, sms));
   tc_resident_kernel<FPL><<<grid, 192, RCfg<FPL>::SMEM, st>>>(jobs, njobs, queue);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;

@@ -26,6 +26,10 @@ static constexpr int SB_T = 256;
 #define KPSB_SB_MIN_BLOCKS 4
 #endif
 #define SB_BOUNDS __launch_bounds__(SB_T, KPSB_SB_MIN_BLOCKS)
+#ifndef KPSB_SB_MIN_BLOCKS_X
+#define KPSB_SB_MIN_BLOCKS_X KPSB_SB_MIN_BLOCKS
+#endif
+#define SB_BOUNDS_X __launch_bounds__(SB_T, KPSB_SB_MIN_BLOCKS_X)  // x and r update kernels
 // Each block of a vector kernel handles one fixed chunk of SB_CHUNK elements (SB_EPT per
 // thread) and writes one reduction partial: the summation order depends on n only, so a
 // problem gives the same bits alone, in any batch, and in the serving loop.
@@ -236,7 +240,7 @@ __global__ void SB_BOUNDS sb_cgls_zz_kernel(const SBProb* __restrict__ probs) {
 }
 
 // x += mu w; r -= mu z (steps 5-6); RC_CGLS = ||mu w|| / ||x|| (eq. (5.1)) and the stop test.
-__global__ void SB_BOUNDS sb_cgls_x_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS_X sb_cgls_x_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
   const double mu = P.sc->step;
   const double c1 = -mu * P.sqrt_mu, c2 = -mu * (0.5 * P.lam);  // r -= mu z, one FMA each
@@ -392,7 +396,7 @@ __global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int i
 
 // x += mu w, r -= mu z (steps 5-6, mu from the zz kernel); RC_CGLS (5.1) and the stop
 // test; the planes of r1 for the transpose apply.
-__global__ void SB_BOUNDS sb_x_tc_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS_X sb_x_tc_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
   (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
