@@ -55,10 +55,11 @@ def parse():
     ap.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
     ap.add_argument("--count", type=int, default=64, help="serving: requests")
     ap.add_argument("--sizes", default="128,256", help="serving: image sizes drawn uniformly")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batched96", "sweep", "direct"],
+    ap.add_argument("--workload", default="medium", choices=["medium", "batched96", "sweep", "direct", "tsvd"],
                     help="medium: the headline batch; batched96: 96 uneven problems (n 64..384) in "
                          "one batched launch; sweep: 100 lambda values on one set of KP factors; "
-                         "direct: split Bregman with the explicit A vs the KP sum on one request")
+                         "direct: split Bregman with the explicit A vs the KP sum on one request; "
+                         "tsvd: the TSVD in single vs double precision, full vs one-sided reorthogonalisation")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: the timed steps only (no replay, e2e, plain or CPU legs), "
                          "with the library's host-driven loop (ncu cannot profile kernels inside "
@@ -443,6 +444,50 @@ def direct_main(args):
                 "so one direct CGLS step costs 4 N^2 flops against 8 k n^3 with the KP sum"}), flush=True)
 
 
+def tsvd_main(args):
+    """The paper's SP/DP comparison of the TSVD (Sec. 1, Sec. 5: EGKB(SP), EGKB(DP), RSVD):
+    build time per precision and reorthogonalisation, and how far the single-precision
+    singular values sit from the double-precision ones, at configuration 2 (n = 128, auto k)
+    and configuration 3 (n = 512, k = 20)."""
+    import numpy as np
+    import torch
+
+    from paper_2410_00233_gb300 import inputs as I
+    from paper_2410_00233_gb300 import kpsb as K
+
+    torch.cuda.set_device(0)
+    K.lib()
+    rows = []
+    for name, pr, rank in (("cfg2 n=128 auto-k", I.problem_medium(0), None),
+                           ("cfg3 n=512 k=20", I.problem_large(0), 20)):
+        rk = pr.tau if rank is None else rank
+        variants = [("EGKB full", K.EGKB, False), ("EGKB one-sided", K.EGKB, True)]
+        if rank is not None:
+            variants.append(("RSVD", K.RSVD, False))
+        for vname, method, one_sided in variants:
+            res = {}
+            for prec, fp64 in (("SP", False), ("DP", True)):
+                opts = dict(p=pr.p if method == K.EGKB else 10, seed=pr.seed, one_sided=one_sided, fp64=fp64)
+                K.kp_build(pr.psf, pr.n, pr.bc, rk, method, **opts).close()  # warm-up
+                ts = []
+                for _ in range(3):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    kp = K.kp_build(pr.psf, pr.n, pr.bc, rk, method, **opts)
+                    torch.cuda.synchronize()
+                    ts.append(time.perf_counter() - t0)
+                    sig = K.kp_info(kp)["sigma"]
+                    kp.close()
+                res[prec] = (min(ts), sig)
+            (t_sp, s_sp), (t_dp, s_dp) = res["SP"], res["DP"]
+            k = min(len(s_sp), len(s_dp))
+            rows.append({"config": name, "method": vname, "k_sp": len(s_sp), "k_dp": len(s_dp),
+                         "sp_ms": 1000 * t_sp, "dp_ms": 1000 * t_dp, "dp_over_sp": t_dp / t_sp,
+                         "max_sigma_diff_over_sigma1": float(np.max(np.abs(s_sp[:k] - s_dp[:k])) / s_dp[0])})
+    print(json.dumps({"metric": "TSVD of R(A): single vs double precision (build time, sigma agreement)",
+                      "unit": "ms", "n_gpus": 1, "data": "synthetic", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.cpu_worker > 0:
@@ -462,6 +507,9 @@ def main():
         return
     if args.workload == "direct":
         direct_main(args)
+        return
+    if args.workload == "tsvd":
+        tsvd_main(args)
         return
 
     import numpy as np

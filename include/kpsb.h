@@ -82,6 +82,10 @@ typedef struct {
   const float* start_host; /* optional host input: EGKB start vector y (n^2), or RSVD test
                         matrix F (n^2 x k_p, column-major).  NULL = Philox + Box-Muller */
   void* stream;      /* cudaStream_t for the work (NULL = legacy default stream) */
+  int fp64;          /* 1: the TSVD in FP64 throughout (PSF, Krylov / sketch bases, R(A)
+                        products; the paper's DP variant); 0 (default): single precision,
+                        FP64 scalars.  The factors are stored in FP32 either way, sigma in FP64.
+                        kp_build_dense supports single precision only. */
 } kpsb_build_opts;
 
 /* Options of sb_solve; zero-initialise, 0 selects the default. */

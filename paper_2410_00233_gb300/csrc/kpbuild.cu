@@ -180,12 +180,14 @@ __global__ void rsvd_sigma_kernel(const double* lam, const double* U, int m, int
 }
 
 // ---- workspace ---------------------------------------------------------------------------------
+// T: element type of the PSF and the Krylov / sketch bases (float: SP TSVD, double: FP64).
+template <typename T>
 struct BuildWork {
   char* base = nullptr;
-  float* psf = nullptr;
-  float* S = nullptr;   // N x (KP + 1)
-  float* Q = nullptr;   // N x KP
-  float* T = nullptr;   // N x KP (RSVD temp)
+  T* psf = nullptr;
+  T* S = nullptr;    // N x (KP + 1)
+  T* Q = nullptr;    // N x KP
+  T* Tmp = nullptr;  // N x KP (RSVD temp)
   double* h = nullptr;  // 128
   double* small = nullptr;  // small matrices: C, U, S, V, G, ...
   EgkbState* st = nullptr;
@@ -194,8 +196,9 @@ struct BuildWork {
   const float* A32 = nullptr;  // general operator: explicit A in FP32 (no PSF), or null
 };
 
-// R(A) products of the build: the PSF's index map, or the explicit matrix when one is given.
-static kpsb_status rop_apply(const BuildWork& w, int s0, int s1, int n, int bc, const float* V, int ldv,
+// R(A) products of the build: the PSF's index map, or the explicit matrix when one is given
+// (SP only).
+static kpsb_status rop_apply(const BuildWork<float>& w, int s0, int s1, int n, int bc, const float* V, int ldv,
                              int nb, float* U, int ldu, int transpose, const float* prev, int ldp,
                              const double* beta_dev, float beta_host, const int* skip, cudaStream_t st) {
   if (w.A32)
@@ -203,35 +206,46 @@ static kpsb_status rop_apply(const BuildWork& w, int s0, int s1, int n, int bc, 
   return ra_apply(w.psf, s0, s1, n, bc, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host, skip,
                   w.ra, st);
 }
+static kpsb_status rop_apply(const BuildWork<double>& w, int s0, int s1, int n, int bc, const double* V,
+                             int ldv, int nb, double* U, int ldu, int transpose, const double* prev, int ldp,
+                             const double* beta_dev, double beta_host, const int* skip, cudaStream_t st) {
+  return ra_apply(w.psf, s0, s1, n, bc, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host, skip,
+                  w.ra, st);
+}
+
+template <typename T> constexpr double eps_of();
+template <> constexpr double eps_of<float>() { return 1.1920928955078125e-07; }
+template <> constexpr double eps_of<double>() { return 2.220446049250313e-16; }
 
 static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
-static kpsb_status work_alloc(BuildWork& w, int n, int s0, int s1, int kpmax, int nb_ra,
+template <typename T>
+static kpsb_status work_alloc(BuildWork<T>& w, int n, int s0, int s1, int kpmax, int nb_ra,
                               cudaStream_t st) {
   const size_t N = (size_t)n * n;
   const int smax = std::max(s0, s1);
   size_t off_psf = 0;
-  size_t off_S = off_psf + a256(sizeof(float) * s0 * s1);
-  size_t off_Q = off_S + a256(sizeof(float) * N * (kpmax + 1));
-  size_t off_T = off_Q + a256(sizeof(float) * N * (kpmax + 1));
-  size_t off_h = off_T + a256(sizeof(float) * N * (kpmax + 1));
+  size_t off_S = off_psf + a256(sizeof(T) * s0 * s1);
+  size_t off_Q = off_S + a256(sizeof(T) * N * (kpmax + 1));
+  size_t off_T = off_Q + a256(sizeof(T) * N * (kpmax + 1));
+  size_t off_h = off_T + a256(sizeof(T) * N * (kpmax + 1));
   size_t off_small = off_h + a256(sizeof(double) * 256);
   size_t small_sz = a256(sizeof(double) * 12 * 130 * 66);
   size_t off_st = off_small + small_sz;
   size_t off_ra = off_st + a256(sizeof(EgkbState));
-  size_t ra_bytes = ra_scratch_bytes(n, nb_ra, smax);
+  size_t ra_bytes = ra_scratch_bytes(n, nb_ra, smax, sizeof(T));
   size_t off_red = off_ra + a256(ra_bytes);
   size_t red_bytes = a256(sizeof(double) * RED_MAX_BLOCKS * 64 * 64) + 256;
   size_t total = off_red + red_bytes;
   KPSB_TRY_CUDA(cudaMallocAsync((void**)&w.base, total, st));
-  w.psf = (float*)(w.base + off_psf);
-  w.S = (float*)(w.base + off_S);
-  w.Q = (float*)(w.base + off_Q);
-  w.T = (float*)(w.base + off_T);
+  w.psf = (T*)(w.base + off_psf);
+  w.S = (T*)(w.base + off_S);
+  w.Q = (T*)(w.base + off_Q);
+  w.Tmp = (T*)(w.base + off_T);
   w.h = (double*)(w.base + off_h);
   w.small = (double*)(w.base + off_small);
   w.st = (EgkbState*)(w.base + off_st);
-  w.ra = ra_scratch_carve(w.base + off_ra, n, nb_ra, smax);
+  w.ra = ra_scratch_carve(w.base + off_ra, n, nb_ra, smax, sizeof(T));
   w.red.counter = (unsigned int*)(w.base + off_red);
   w.red.part = (double*)(w.base + off_red + 256);
   // counters must start at zero
@@ -245,7 +259,8 @@ struct HostPsf {
 };
 
 // CGS2: two passes of v -= B (B^T v) against m columns; the second pass also gives ||v||.
-static kpsb_status cgs2(const float* B, int ldb, int m, float* v, long long N, double* h,
+template <typename T>
+static kpsb_status cgs2(const T* B, int ldb, int m, T* v, long long N, double* h,
                         double* norm_out, const RedScratch& red, const int* gate, cudaStream_t st) {
   if (m > 0) {
     KPSB_TRY(la_dot_block(B, ldb, m, v, N, h, red, gate, st));
@@ -264,7 +279,22 @@ static kpsb_status cgs2(const float* B, int ldb, int m, float* v, long long N, d
 //   q_j = R^T s_j - t_j q_{j-1}, reorthogonalised against q_1..q_{j-1}, alpha_j, nu_j.
 // Reorthogonalisation is classical Gram-Schmidt applied twice (CGS2), the blocked form
 // of the modified Gram-Schmidt of the paper (same projection, at least as orthogonal).
-static kpsb_status egkb_run(BuildWork& w, int n, int s0, int s1, int bc, const EgkbParams& P,
+// Copies a caller's FP32 start block (n^2 x m) into dst of the basis type.
+template <typename T>
+static kpsb_status upload_start(const float* host, T* dst, T* staging, long long count, cudaStream_t st) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    (void)staging;
+    KPSB_TRY_CUDA(cudaMemcpyAsync(dst, host, sizeof(float) * count, cudaMemcpyHostToDevice, st));
+    return KPSB_OK;
+  } else {
+    float* f = (float*)staging;  // staging holds count doubles, so count floats fit
+    KPSB_TRY_CUDA(cudaMemcpyAsync(f, host, sizeof(float) * count, cudaMemcpyHostToDevice, st));
+    return la_convert<double, float>(f, dst, count, st);
+  }
+}
+
+template <typename T>
+static kpsb_status egkb_run(BuildWork<T>& w, int n, int s0, int s1, int bc, const EgkbParams& P,
                             int full_reorth, int kpmax, const float* start_host,
                             unsigned long long seed, cudaStream_t st, int* nq_out, int* ns_out,
                             int* ksel_out, std::vector<double>& alpha, std::vector<double>& tvec) {
@@ -273,9 +303,9 @@ static kpsb_status egkb_run(BuildWork& w, int n, int s0, int s1, int bc, const E
   KPSB_CHECK_LAUNCH();
   // s_1 = y / ||y||
   if (start_host) {
-    KPSB_TRY_CUDA(cudaMemcpyAsync(w.S, start_host, sizeof(float) * N, cudaMemcpyHostToDevice, st));
+    KPSB_TRY(upload_start<T>(start_host, w.S, w.Tmp, N, st));
   } else {
-    KPSB_TRY(la_randn(w.S, N, seed, st));
+    KPSB_TRY(la_randn<T>(w.S, N, seed, st));
   }
   int* gate = (int*)((char*)w.st + offsetof(EgkbState, gate));
   double* d_norm = ST_FIELD(w.st, norm);
@@ -287,7 +317,7 @@ static kpsb_status egkb_run(BuildWork& w, int n, int s0, int s1, int bc, const E
   KPSB_CHECK_LAUNCH();
   KPSB_TRY(la_scale_inv(w.S, N, d_norm, gate + 2, st));
   // q_1 = R^T s_1 / alpha_1
-  KPSB_TRY(rop_apply(w, s0, s1, n, bc, w.S, (int)N, 1, w.Q, (int)N, 1, nullptr, 0, nullptr, 0.f,
+  KPSB_TRY(rop_apply(w, s0, s1, n, bc, w.S, (int)N, 1, w.Q, (int)N, 1, nullptr, 0, nullptr, (T)0,
                     gate + 3, st));
   KPSB_TRY(la_norm(w.Q, N, d_norm, w.red, gate + 3, st));
   egkb_after_alpha<<<1, 1, 0, st>>>(w.st, P, 1);
@@ -299,15 +329,15 @@ static kpsb_status egkb_run(BuildWork& w, int n, int s0, int s1, int bc, const E
   *h_fin = 0;
   kpsb_status status = KPSB_OK;
   for (int j = 2; j <= kpmax + 1 && status == KPSB_OK; ++j) {
-    float* sj = w.S + (size_t)(j - 1) * N;
-    float* sjm1 = w.S + (size_t)(j - 2) * N;
-    float* qjm1 = w.Q + (size_t)(j - 2) * N;
-    float* qj = w.Q + (size_t)(j - 1) * N;
+    T* sj = w.S + (size_t)(j - 1) * N;
+    T* sjm1 = w.S + (size_t)(j - 2) * N;
+    T* qjm1 = w.Q + (size_t)(j - 2) * N;
+    T* qj = w.Q + (size_t)(j - 1) * N;
     const int* gs = gate + 2 * j;
     const int* gq = gate + 2 * j + 1;
     // s-phase
     status = rop_apply(w, s0, s1, n, bc, qjm1, (int)N, 1, sj, (int)N, 0, sjm1, (int)N,
-                      d_coef_s, 0.f, gs, st);
+                      d_coef_s, (T)0, gs, st);
     if (status) break;
     status = cgs2(w.S, (int)N, full_reorth ? j - 1 : 0, sj, N, w.h, d_norm, w.red, gs, st);
     if (status) break;
@@ -318,7 +348,7 @@ static kpsb_status egkb_run(BuildWork& w, int n, int s0, int s1, int bc, const E
     if (j == kpmax + 1) break;  // only s_{kp+1} is needed from the last step
     // q-phase
     status = rop_apply(w, s0, s1, n, bc, sj, (int)N, 1, qj, (int)N, 1, qjm1, (int)N,
-                      d_coef_q, 0.f, gq, st);
+                      d_coef_q, (T)0, gq, st);
     if (status) break;
     status = cgs2(w.Q, (int)N, j - 1, qj, N, w.h, d_norm, w.red, gq, st);
     if (status) break;
@@ -373,7 +403,8 @@ static kpsb_status handle_alloc(kpsb_kp** out, int n, int k, int kpsize) {
   return KPSB_OK;
 }
 
-static kpsb_status build_egkb(const float* A32, const float* psf_host, int s0, int s1, int n, int bc, int k,
+template <typename T>
+static kpsb_status build_egkb(const float* A32, const T* psf_host, int s0, int s1, int n, int bc, int k,
                               double tau, const kpsb_build_opts& o, cudaStream_t st, kpsb_kp** out) {
   EgkbParams P;
   P.k_fixed = tau > 0.0 ? 0 : k;
@@ -381,16 +412,16 @@ static kpsb_status build_egkb(const float* A32, const float* psf_host, int s0, i
   P.p = o.p;
   P.k_min = o.k_min;
   P.tau = tau;
-  P.bd_tol = 30.0 * 1.1920928955078125e-07;
+  P.bd_tol = 30.0 * eps_of<T>();
   const int kpmax = P.k_cap + P.p;
   KPSB_REQUIRE(kpmax <= KP_MAX, "k + p = %d exceeds %d", kpmax, KP_MAX);
   const long long N = (long long)n * n;
-  BuildWork w;
+  BuildWork<T> w;
   KPSB_TRY(work_alloc(w, n, s0, s1, kpmax, 1, st));
   w.A32 = A32;
   kpsb_status s = KPSB_OK;
   do {
-    cudaError_t e = cudaMemcpyAsync(w.psf, psf_host, sizeof(float) * s0 * s1, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(w.psf, psf_host, sizeof(T) * s0 * s1, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { set_error("psf upload: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
     int nq = 0, ns = 0, ksel = 0;
     std::vector<double> alpha, tv;
@@ -446,23 +477,24 @@ static kpsb_status build_egkb(const float* A32, const float* psf_host, int s0, i
 
 // Orthonormalise the m columns of Y (N x m) in place by SVQB twice (Gram matrix, its
 // eigen-decomposition, Y <- Y D^{-1/2} W Lambda^{-1/2}); null directions become zero.
-static kpsb_status svqb2(BuildWork& w, float* Y, long long N, int m, cudaStream_t st) {
+template <typename T>
+static kpsb_status svqb2(BuildWork<T>& w, T* Y, long long N, int m, cudaStream_t st) {
   double* G = w.small;
   double* Gs = G + 64 * 64;
   double* d = Gs + 64 * 64;
   double* U = d + 64;
   double* lam = U + 64 * 64;
   double* W = lam + 64;
-  double* T = W + 64 * 64;
+  double* Tm = W + 64 * 64;
   for (int pass = 0; pass < 2; ++pass) {
     KPSB_TRY(la_gram(Y, (int)N, N, m, G, w.red, st));
     svqb_scale_kernel<<<1, 256, 0, st>>>(G, m, Gs, d);
     KPSB_CHECK_LAUNCH();
     KPSB_TRY(la_small_svd(Gs, m, m, m, U, lam, W, nullptr, st));
-    svqb_transform_kernel<<<1, 256, 0, st>>>(W, lam, d, m, 1e-12, T);
+    svqb_transform_kernel<<<1, 256, 0, st>>>(W, lam, d, m, 1e-12, Tm);
     KPSB_CHECK_LAUNCH();
-    KPSB_TRY(la_matmul_small(Y, (int)N, N, m, T, m, m, w.T, (int)N, st));
-    KPSB_TRY_CUDA(cudaMemcpyAsync(Y, w.T, sizeof(float) * N * m, cudaMemcpyDeviceToDevice, st));
+    KPSB_TRY(la_matmul_small(Y, (int)N, N, m, Tm, m, m, w.Tmp, (int)N, st));
+    KPSB_TRY_CUDA(cudaMemcpyAsync(Y, w.Tmp, sizeof(T) * N * m, cudaMemcpyDeviceToDevice, st));
   }
   return KPSB_OK;
 }
@@ -471,42 +503,43 @@ static kpsb_status svqb2(BuildWork& w, float* Y, long long N, int m, cudaStream_
 // Alg. 2 with q power iterations: Y = R F, orthonormalised after every apply of R or R^T
 // (step 2-3), H^T = R^T Q (step 4), SVD of H through the eigen-decomposition of H H^T
 // (k_p x k_p, FP64; step 5), U = Q U_H (step 6), V = H^T U_H Sigma^{-1}, truncation (step 7).
-static kpsb_status build_rsvd(const float* A32, const float* psf_host, int s0, int s1, int n, int bc, int k,
+template <typename T>
+static kpsb_status build_rsvd(const float* A32, const T* psf_host, int s0, int s1, int n, int bc, int k,
                               const kpsb_build_opts& o, cudaStream_t st, kpsb_kp** out) {
   const int kp = k + o.p;
   KPSB_REQUIRE(kp <= KP_MAX, "k + p = %d exceeds %d", kp, KP_MAX);
   const long long N = (long long)n * n;
-  BuildWork w;
+  BuildWork<T> w;
   KPSB_TRY(work_alloc(w, n, s0, s1, kp, kp, st));
   w.A32 = A32;
   kpsb_status s = KPSB_OK;
   do {
-    cudaError_t e = cudaMemcpyAsync(w.psf, psf_host, sizeof(float) * s0 * s1, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(w.psf, psf_host, sizeof(T) * s0 * s1, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { set_error("psf upload: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
-    float* F = w.S;  // N x kp
+    T* F = w.S;  // N x kp
     if (o.start_host) {
-      e = cudaMemcpyAsync(F, o.start_host, sizeof(float) * N * kp, cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) { set_error("F upload: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
+      s = upload_start<T>(o.start_host, F, w.Tmp, N * kp, st);
+      if (s) break;
     } else {
-      s = la_randn(F, N * kp, o.seed, st);
+      s = la_randn<T>(F, N * kp, o.seed, st);
       if (s) break;
     }
-    float* Y = w.Q;
-    s = rop_apply(w, s0, s1, n, bc, F, (int)N, kp, Y, (int)N, 0, nullptr, 0, nullptr, 0.f,
+    T* Y = w.Q;
+    s = rop_apply(w, s0, s1, n, bc, F, (int)N, kp, Y, (int)N, 0, nullptr, 0, nullptr, (T)0,
                  nullptr, st);
     if (!s) s = svqb2(w, Y, N, kp, st);
     for (int it = 0; it < o.power_iters && !s; ++it) {
-      s = rop_apply(w, s0, s1, n, bc, Y, (int)N, kp, F, (int)N, 1, nullptr, 0, nullptr, 0.f,
+      s = rop_apply(w, s0, s1, n, bc, Y, (int)N, kp, F, (int)N, 1, nullptr, 0, nullptr, (T)0,
                    nullptr, st);
       if (!s) s = svqb2(w, F, N, kp, st);
       if (!s) s = rop_apply(w, s0, s1, n, bc, F, (int)N, kp, Y, (int)N, 0, nullptr, 0, nullptr,
-                           0.f, nullptr, st);
+                           (T)0, nullptr, st);
       if (!s) s = svqb2(w, Y, N, kp, st);
     }
     if (s) break;
     // H^T = R^T Q  (N x kp) into F
-    float* Ht = F;
-    s = rop_apply(w, s0, s1, n, bc, Y, (int)N, kp, Ht, (int)N, 1, nullptr, 0, nullptr, 0.f,
+    T* Ht = F;
+    s = rop_apply(w, s0, s1, n, bc, Y, (int)N, kp, Ht, (int)N, 1, nullptr, 0, nullptr, (T)0,
                  nullptr, st);
     if (s) break;
     double* G = w.small;
@@ -528,7 +561,8 @@ static kpsb_status build_rsvd(const float* A32, const float* psf_host, int s0, i
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { set_error("rsvd: %s", cudaGetErrorString(e)); s = KPSB_ECUDA; break; }
     int kk = 0;
-    while (kk < k && hsig[kk] > 1e-6 * hsig[0]) ++kk;
+    const double drop = sizeof(T) == sizeof(float) ? 1e-6 : 1e-13;  // below the arithmetic's resolution
+    while (kk < k && hsig[kk] > drop * hsig[0]) ++kk;
     if (kk == 0) {
       set_error("RSVD: R(A) applied to the test matrix vanishes");
       s = KPSB_EBREAKDOWN;
@@ -588,11 +622,16 @@ extern "C" kpsb_status kp_build(const double* psf, int s0, int s1, int n, int bc
   if (o.power_iters <= 0) o.power_iters = 1;
   if (o.k_min <= 0) o.k_min = 3;
   KPSB_REQUIRE(std::min(k, K_CAP) + o.p <= KP_MAX || tau == 0.0, "k_cap + p exceeds %d", KP_MAX);
+  cudaStream_t st = (cudaStream_t)o.stream;
+  if (o.fp64) {  // the TSVD in FP64 throughout (PSF, bases, R(A) products)
+    std::vector<double> pd(psf, psf + (size_t)s0 * s1);
+    if (method == KPSB_EGKB) return build_egkb<double>(nullptr, pd.data(), s0, s1, n, bc, k, tau, o, st, out);
+    return build_rsvd<double>(nullptr, pd.data(), s0, s1, n, bc, k, o, st, out);
+  }
   std::vector<float> pf((size_t)s0 * s1);
   for (size_t i = 0; i < pf.size(); ++i) pf[i] = (float)psf[i];
-  cudaStream_t st = (cudaStream_t)o.stream;
-  if (method == KPSB_EGKB) return build_egkb(nullptr, pf.data(), s0, s1, n, bc, k, tau, o, st, out);
-  return build_rsvd(nullptr, pf.data(), s0, s1, n, bc, k, o, st, out);
+  if (method == KPSB_EGKB) return build_egkb<float>(nullptr, pf.data(), s0, s1, n, bc, k, tau, o, st, out);
+  return build_rsvd<float>(nullptr, pf.data(), s0, s1, n, bc, k, o, st, out);
 }
 
 extern "C" kpsb_status kp_build_dense(const double* A, int n, double rank_or_tol, int method,
@@ -620,6 +659,7 @@ extern "C" kpsb_status kp_build_dense(const double* A, int n, double rank_or_tol
   if (o.power_iters <= 0) o.power_iters = 1;
   if (o.k_min <= 0) o.k_min = 3;
   KPSB_REQUIRE(std::min(k, K_CAP) + o.p <= KP_MAX || tau == 0.0, "k_cap + p exceeds %d", KP_MAX);
+  KPSB_REQUIRE(!o.fp64, "kp_build_dense runs the single-precision TSVD only");
   // the SP copy of A on the device (the R(A) products of the TSVD read it; Sec. 1)
   const size_t NN = (size_t)n * n * n * n;
   std::vector<float> a32(NN);
@@ -634,8 +674,8 @@ extern "C" kpsb_status kp_build_dense(const double* A, int n, double rank_or_tol
   } else {
     const float one = 1.0f;  // unused 1 x 1 PSF: the products come from A
     cudaStream_t st = (cudaStream_t)o.stream;
-    s = method == KPSB_EGKB ? build_egkb(dA, &one, 1, 1, n, KPSB_BC_ZERO, k, tau, o, st, out)
-                            : build_rsvd(dA, &one, 1, 1, n, KPSB_BC_ZERO, k, o, st, out);
+    s = method == KPSB_EGKB ? build_egkb<float>(dA, &one, 1, 1, n, KPSB_BC_ZERO, k, tau, o, st, out)
+                            : build_rsvd<float>(dA, &one, 1, 1, n, KPSB_BC_ZERO, k, o, st, out);
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (s == KPSB_OK && e2 != cudaSuccess) {
       set_error("kp_build_dense: %s", cudaGetErrorString(e2));

@@ -11,12 +11,13 @@ namespace kpsb {
 
 // ---- R(A) block apply (ra.cu) -----------------------------------------------------------
 struct RAScratch {
-  float* part;             // per-tile diagonal / anti-diagonal partial sums
-  float* w;                // mixed tap weights, nb x s_exp
+  float* part;             // per-tile diagonal / anti-diagonal partial sums (element type of V)
+  float* w;                // mixed tap weights, nb x s_exp (element type of V)
   unsigned int* counters;  // last-block counters, nb (must start at zero)
 };
-size_t ra_scratch_bytes(int n, int nb, int s_exp);
-RAScratch ra_scratch_carve(void* base, int n, int nb, int s_exp);
+// el = sizeof the element type of the vectors (float or double)
+size_t ra_scratch_bytes(int n, int nb, int s_exp, size_t el = sizeof(float));
+RAScratch ra_scratch_carve(void* base, int n, int nb, int s_exp, size_t el = sizeof(float));
 kpsb_status ra_check(int s0, int s1, int n, int bc);
 // The same products for a general operator given as an explicit FP32 matrix A (N x N,
 // column-major): R(A)[i + j n, p + q n] = A[(i n + p) + (j n + q) N] (ra_dense.cu).
@@ -29,6 +30,11 @@ kpsb_status ra_apply(const float* psf, int s0, int s1, int n, int bc, const floa
                      int nb, float* U, int ldu, int transpose, const float* prev, int ldp,
                      const double* beta_dev, float beta_host, const int* skip,
                      const RAScratch& scr, cudaStream_t st);
+// The same in FP64 (PSF, vectors and scratch all double): the FP64 TSVD.
+kpsb_status ra_apply(const double* psf, int s0, int s1, int n, int bc, const double* V, int ldv,
+                     int nb, double* U, int ldu, int transpose, const double* prev, int ldp,
+                     const double* beta_dev, double beta_host, const int* skip,
+                     const RAScratch& scr, cudaStream_t st);
 
 // ---- dense helpers (la.cu) --------------------------------------------------------------
 // Scratch of a deterministic grid reduction (partials + counter).
@@ -38,31 +44,42 @@ struct RedScratch {
 };
 static constexpr int RED_MAX_BLOCKS = 304;
 
+// Templates on the basis element type T (float: SP TSVD; double: FP64 TSVD); instantiated
+// in la.cu for both.
 // h[i] = sum_r S[r + i ldS] v[r], i < m  (FP64 result; m <= 128).
-kpsb_status la_dot_block(const float* S, int ldS, int m, const float* v, long long N,
+template <typename T>
+kpsb_status la_dot_block(const T* S, int ldS, int m, const T* v, long long N,
                          double* h, const RedScratch& red, const int* skip, cudaStream_t st);
 // v -= S h (m columns); when norm_out != null also writes ||v||_2 (after the update).
-kpsb_status la_update(const float* S, int ldS, int m, const double* h, float* v, long long N,
+template <typename T>
+kpsb_status la_update(const T* S, int ldS, int m, const double* h, T* v, long long N,
                       double* norm_out, const RedScratch& red, const int* skip, cudaStream_t st);
 // ||v||_2 into norm_out (FP64).
-kpsb_status la_norm(const float* v, long long N, double* norm_out, const RedScratch& red,
+template <typename T>
+kpsb_status la_norm(const T* v, long long N, double* norm_out, const RedScratch& red,
                     const int* skip, cudaStream_t st);
 // v *= 1 / *norm (norm device FP64; zero norm leaves v unchanged).
-kpsb_status la_scale_inv(float* v, long long N, const double* norm, const int* skip,
-                         cudaStream_t st);
-// G = Y^T Y (m x m FP64, column-major), Y N x m FP32 with leading dimension ldy; m <= 64.
-kpsb_status la_gram(const float* Y, int ldy, long long N, int m, double* G,
+template <typename T>
+kpsb_status la_scale_inv(T* v, long long N, const double* norm, const int* skip, cudaStream_t st);
+// G = Y^T Y (m x m FP64, column-major), Y N x m with leading dimension ldy; m <= 64.
+template <typename T>
+kpsb_status la_gram(const T* Y, int ldy, long long N, int m, double* G,
                     const RedScratch& red, cudaStream_t st);
 // Out (N x kk, ldo) = Y (N x m, ldy) * T (m x kk FP64 column-major, ldt);  Out != Y.
-kpsb_status la_matmul_small(const float* Y, int ldy, long long N, int m, const double* T,
-                            int ldt, int kk, float* Out, int ldo, cudaStream_t st);
+template <typename TY, typename TO>
+kpsb_status la_matmul_small(const TY* Y, int ldy, long long N, int m, const double* T,
+                            int ldt, int kk, TO* Out, int ldo, cudaStream_t st);
+// out[i] = in[i] converted.
+template <typename TO, typename TI>
+kpsb_status la_convert(const TI* in, TO* out, long long N, cudaStream_t st);
 // One-sided Jacobi SVD of an m x nc FP64 matrix in device memory (one thread block):
 // A = U diag(S) V^T, S descending.  m <= 128, nc <= 64, m >= nc.  sweeps may be null.
 kpsb_status la_small_svd(const double* A, int lda, int m, int nc, double* U, double* S,
                          double* V, int* sweeps, cudaStream_t st);
-// Standard normal FP32 values from Philox4x32-10 (counter = element index, key = seed)
-// and the Box-Muller transform.
-kpsb_status la_randn(float* out, long long count, unsigned long long seed, cudaStream_t st);
+// Standard normal values from Philox4x32-10 (counter = element index, key = seed) and the
+// Box-Muller transform (computed in FP64, stored as T).
+template <typename T>
+kpsb_status la_randn(T* out, long long count, unsigned long long seed, cudaStream_t st);
 
 // ---- KP operator handle ---------------------------------------------------------------
 struct TCTables;  // tensor-core operand tables (kpgemm_tc.cu)

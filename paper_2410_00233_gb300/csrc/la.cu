@@ -16,9 +16,13 @@ static int red_blocks(long long N, int per_thread) {
   return (int)std::max(1LL, std::min<long long>(b, RED_MAX_BLOCKS));
 }
 
+// The block helpers are templates on the basis element type: float for the single-
+// precision TSVD, double for the FP64 one (reductions are FP64 in both).
+
 // ---- h = S^T v --------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(LA_THREADS) dot_block_kernel(
-    const float* __restrict__ S, int ldS, int m, const float* __restrict__ v, long long N,
+    const T* __restrict__ S, int ldS, int m, const T* __restrict__ v, long long N,
     double* __restrict__ part, unsigned int* __restrict__ counter, double* __restrict__ h,
     const int* skip) {
   if (gate_skip(skip)) return;
@@ -26,14 +30,14 @@ __global__ void __launch_bounds__(LA_THREADS) dot_block_kernel(
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long r0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   for (int c0 = 0; c0 < m; c0 += 8) {
-    float acc[8];
+    T acc[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+    for (int u = 0; u < 8; ++u) acc[u] = 0;
     for (long long r = r0; r < N; r += stride) {
-      float x = v[r];
+      T x = v[r];
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        if (c0 + u < m) acc[u] = fmaf(S[r + (size_t)(c0 + u) * ldS], x, acc[u]);
+        if (c0 + u < m) acc[u] = fma(S[r + (size_t)(c0 + u) * ldS], x, acc[u]);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -50,33 +54,35 @@ __global__ void __launch_bounds__(LA_THREADS) dot_block_kernel(
   }
 }
 
-kpsb_status la_dot_block(const float* S, int ldS, int m, const float* v, long long N, double* h,
+template <typename T>
+kpsb_status la_dot_block(const T* S, int ldS, int m, const T* v, long long N, double* h,
                          const RedScratch& red, const int* skip, cudaStream_t st) {
   if (m <= 0) return KPSB_OK;
   int nb = red_blocks(N, 4);
-  dot_block_kernel<<<nb, LA_THREADS, 0, st>>>(S, ldS, m, v, N, red.part, red.counter, h, skip);
+  dot_block_kernel<T><<<nb, LA_THREADS, 0, st>>>(S, ldS, m, v, N, red.part, red.counter, h, skip);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
 }
 
 // ---- v -= S h, optional ||v|| -------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(LA_THREADS) update_kernel(
-    const float* __restrict__ S, int ldS, int m, const double* __restrict__ h, float* __restrict__ v,
+    const T* __restrict__ S, int ldS, int m, const double* __restrict__ h, T* __restrict__ v,
     long long N, double* __restrict__ part, unsigned int* __restrict__ counter,
     double* __restrict__ norm_out, const int* skip) {
   if (gate_skip(skip)) return;
-  __shared__ float hs[128];
+  __shared__ T hs[128];
   __shared__ double sh[32];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) hs[i] = (float)h[i];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) hs[i] = (T)h[i];
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
-  float ss = 0.f;
+  T ss = 0;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += stride) {
-    float corr = 0.f;
-    for (int i = 0; i < m; ++i) corr = fmaf(S[r + (size_t)i * ldS], hs[i], corr);
-    float x = v[r] - corr;
+    T corr = 0;
+    for (int i = 0; i < m; ++i) corr = fma(S[r + (size_t)i * ldS], hs[i], corr);
+    T x = v[r] - corr;
     v[r] = x;
-    ss = fmaf(x, x, ss);
+    ss = fma(x, x, ss);
   }
   if (!norm_out) return;
   double t = block_sum<double>((double)ss, sh);
@@ -89,45 +95,48 @@ __global__ void __launch_bounds__(LA_THREADS) update_kernel(
   }
 }
 
-kpsb_status la_update(const float* S, int ldS, int m, const double* h, float* v, long long N,
+template <typename T>
+kpsb_status la_update(const T* S, int ldS, int m, const double* h, T* v, long long N,
                       double* norm_out, const RedScratch& red, const int* skip, cudaStream_t st) {
   int nb = red_blocks(N, 4);
-  update_kernel<<<nb, LA_THREADS, 0, st>>>(S, ldS, m, h, v, N, red.part, red.counter, norm_out,
-                                           skip);
+  update_kernel<T><<<nb, LA_THREADS, 0, st>>>(S, ldS, m, h, v, N, red.part, red.counter, norm_out, skip);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
 }
 
-kpsb_status la_norm(const float* v, long long N, double* norm_out, const RedScratch& red,
+template <typename T>
+kpsb_status la_norm(const T* v, long long N, double* norm_out, const RedScratch& red,
                     const int* skip, cudaStream_t st) {
-  return la_update(nullptr, 0, 0, nullptr, const_cast<float*>(v), N, norm_out, red, skip, st);
+  return la_update<T>(nullptr, 0, 0, nullptr, const_cast<T*>(v), N, norm_out, red, skip, st);
 }
 
-__global__ void scale_inv_kernel(float* __restrict__ v, long long N, const double* __restrict__ nrm,
+template <typename T>
+__global__ void scale_inv_kernel(T* __restrict__ v, long long N, const double* __restrict__ nrm,
                                  const int* skip) {
   if (gate_skip(skip)) return;
   double d = *nrm;
-  float s = d > 0.0 ? (float)(1.0 / d) : 0.f;  // zero norm: the vector is cleared
+  T s = d > 0.0 ? (T)(1.0 / d) : (T)0;  // zero norm: the vector is cleared
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N;
        r += (long long)gridDim.x * blockDim.x)
     v[r] *= s;
 }
 
-kpsb_status la_scale_inv(float* v, long long N, const double* norm, const int* skip,
-                         cudaStream_t st) {
+template <typename T>
+kpsb_status la_scale_inv(T* v, long long N, const double* norm, const int* skip, cudaStream_t st) {
   int nb = (int)std::min<long long>((N + 1023) / 1024, 1216);
-  scale_inv_kernel<<<nb, LA_THREADS, 0, st>>>(v, N, norm, skip);
+  scale_inv_kernel<T><<<nb, LA_THREADS, 0, st>>>(v, N, norm, skip);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
 }
 
 // ---- G = Y^T Y (FP64) ----------------------------------------------------------------------
-__global__ void __launch_bounds__(LA_THREADS) gram_kernel(const float* __restrict__ Y, int ldy,
+template <typename T>
+__global__ void __launch_bounds__(LA_THREADS) gram_kernel(const T* __restrict__ Y, int ldy,
                                                          long long N, int m,
                                                          double* __restrict__ part,
                                                          unsigned int* __restrict__ counter,
                                                          double* __restrict__ G) {
-  __shared__ float ch[32][65];
+  __shared__ T ch[32][65];
   const int npair = m * m;
   double acc[16];
 #pragma unroll
@@ -137,7 +146,7 @@ __global__ void __launch_bounds__(LA_THREADS) gram_kernel(const float* __restric
     for (int e = threadIdx.x; e < 32 * m; e += blockDim.x) {
       int rr = e % 32, c = e / 32;
       long long r = rb + rr;
-      ch[rr][c] = r < N ? Y[r + (size_t)c * ldy] : 0.f;
+      ch[rr][c] = r < N ? Y[r + (size_t)c * ldy] : (T)0;
     }
     __syncthreads();
 #pragma unroll
@@ -164,51 +173,85 @@ __global__ void __launch_bounds__(LA_THREADS) gram_kernel(const float* __restric
   }
 }
 
-kpsb_status la_gram(const float* Y, int ldy, long long N, int m, double* G, const RedScratch& red,
+template <typename T>
+kpsb_status la_gram(const T* Y, int ldy, long long N, int m, double* G, const RedScratch& red,
                     cudaStream_t st) {
   KPSB_REQUIRE(m >= 1 && m <= 64, "gram width %d outside [1,64]", m);
   int nb = (int)std::max(1LL, std::min<long long>((N + 31) / 32, 152));
-  gram_kernel<<<nb, LA_THREADS, 0, st>>>(Y, ldy, N, m, red.part, red.counter, G);
+  gram_kernel<T><<<nb, LA_THREADS, 0, st>>>(Y, ldy, N, m, red.part, red.counter, G);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
 }
 
 // ---- Out = Y T --------------------------------------------------------------------------------
+template <typename TY, typename TO>
 __global__ void __launch_bounds__(LA_THREADS) matmul_small_kernel(
-    const float* __restrict__ Y, int ldy, long long N, int m, const double* __restrict__ T, int ldt,
-    int kk, float* __restrict__ Out, int ldo) {
-  __shared__ float Ts[64 * 64];
+    const TY* __restrict__ Y, int ldy, long long N, int m, const double* __restrict__ T, int ldt,
+    int kk, TO* __restrict__ Out, int ldo) {
+  __shared__ TY Ts[64 * 64];
   for (int e = threadIdx.x; e < m * kk; e += blockDim.x) {
     int i = e % m, j = e / m;
-    Ts[i + j * 64] = (float)T[i + (size_t)j * ldt];
+    Ts[i + j * 64] = (TY)T[i + (size_t)j * ldt];
   }
   __syncthreads();
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N;
        r += (long long)gridDim.x * blockDim.x) {
     for (int j0 = 0; j0 < kk; j0 += 16) {
-      float acc[16];
+      TY acc[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+      for (int u = 0; u < 16; ++u) acc[u] = 0;
       for (int i = 0; i < m; ++i) {
-        float y = Y[r + (size_t)i * ldy];
+        TY y = Y[r + (size_t)i * ldy];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) acc[u] = fmaf(y, Ts[i + (j0 + u) * 64], acc[u]);
+        for (int u = 0; u < 16; ++u) acc[u] = fma(y, Ts[i + (j0 + u) * 64], acc[u]);
       }
 #pragma unroll
       for (int u = 0; u < 16; ++u)
-        if (j0 + u < kk) Out[r + (size_t)(j0 + u) * ldo] = acc[u];
+        if (j0 + u < kk) Out[r + (size_t)(j0 + u) * ldo] = (TO)acc[u];
     }
   }
 }
 
-kpsb_status la_matmul_small(const float* Y, int ldy, long long N, int m, const double* T, int ldt,
-                            int kk, float* Out, int ldo, cudaStream_t st) {
+template <typename TY, typename TO>
+kpsb_status la_matmul_small(const TY* Y, int ldy, long long N, int m, const double* T, int ldt,
+                            int kk, TO* Out, int ldo, cudaStream_t st) {
   KPSB_REQUIRE(m >= 1 && m <= 64 && kk >= 1 && kk <= 64, "small matmul %dx%d outside 64", m, kk);
   int nb = (int)std::min<long long>((N + LA_THREADS - 1) / LA_THREADS, 152 * 8);
-  matmul_small_kernel<<<nb, LA_THREADS, 0, st>>>(Y, ldy, N, m, T, ldt, kk, Out, ldo);
+  matmul_small_kernel<TY, TO><<<nb, LA_THREADS, 0, st>>>(Y, ldy, N, m, T, ldt, kk, Out, ldo);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
 }
+
+// element-type conversion (start vectors given in FP32 to the FP64 TSVD)
+template <typename TO, typename TI>
+__global__ void convert_kernel(const TI* __restrict__ in, TO* __restrict__ out, long long N) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+       r += (long long)gridDim.x * blockDim.x)
+    out[r] = (TO)in[r];
+}
+
+template <typename TO, typename TI>
+kpsb_status la_convert(const TI* in, TO* out, long long N, cudaStream_t st) {
+  int nb = (int)std::min<long long>((N + 255) / 256, 152 * 8);
+  convert_kernel<TO, TI><<<std::max(1, nb), 256, 0, st>>>(in, out, N);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+template kpsb_status la_dot_block<float>(const float*, int, int, const float*, long long, double*, const RedScratch&, const int*, cudaStream_t);
+template kpsb_status la_dot_block<double>(const double*, int, int, const double*, long long, double*, const RedScratch&, const int*, cudaStream_t);
+template kpsb_status la_update<float>(const float*, int, int, const double*, float*, long long, double*, const RedScratch&, const int*, cudaStream_t);
+template kpsb_status la_update<double>(const double*, int, int, const double*, double*, long long, double*, const RedScratch&, const int*, cudaStream_t);
+template kpsb_status la_norm<float>(const float*, long long, double*, const RedScratch&, const int*, cudaStream_t);
+template kpsb_status la_norm<double>(const double*, long long, double*, const RedScratch&, const int*, cudaStream_t);
+template kpsb_status la_scale_inv<float>(float*, long long, const double*, const int*, cudaStream_t);
+template kpsb_status la_scale_inv<double>(double*, long long, const double*, const int*, cudaStream_t);
+template kpsb_status la_gram<float>(const float*, int, long long, int, double*, const RedScratch&, cudaStream_t);
+template kpsb_status la_gram<double>(const double*, int, long long, int, double*, const RedScratch&, cudaStream_t);
+template kpsb_status la_matmul_small<float, float>(const float*, int, long long, int, const double*, int, int, float*, int, cudaStream_t);
+template kpsb_status la_matmul_small<double, double>(const double*, int, long long, int, const double*, int, int, double*, int, cudaStream_t);
+template kpsb_status la_matmul_small<double, float>(const double*, int, long long, int, const double*, int, int, float*, int, cudaStream_t);
+template kpsb_status la_convert<double, float>(const float*, double*, long long, cudaStream_t);
 
 // ---- one-sided Jacobi SVD (Hestenes) in one thread block -----------------------------------
 // Columns p < q are rotated so that they become orthogonal; a cyclic "round robin"
@@ -324,7 +367,8 @@ __device__ __forceinline__ void philox_round(uint32_t& x0, uint32_t& x1, uint32_
   x0 = y0; x1 = y1; x2 = y2; x3 = y3;
 }
 
-__global__ void randn_kernel(float* __restrict__ out, long long count, uint32_t key0, uint32_t key1) {
+template <typename T>
+__global__ void randn_kernel(T* __restrict__ out, long long count, uint32_t key0, uint32_t key1) {
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g * 4 < count;
        g += (long long)gridDim.x * blockDim.x) {
     uint32_t x0 = (uint32_t)g, x1 = (uint32_t)(g >> 32), x2 = 0u, x3 = 0u;
@@ -343,18 +387,21 @@ __global__ void randn_kernel(float* __restrict__ out, long long count, uint32_t 
       double rad = sqrt(-2.0 * log(u1));
       double th = 6.283185307179586 * u2;
       long long i0 = g * 4 + 2 * pr;
-      if (i0 < count) out[i0] = (float)(rad * cos(th));
-      if (i0 + 1 < count) out[i0 + 1] = (float)(rad * sin(th));
+      if (i0 < count) out[i0] = (T)(rad * cos(th));
+      if (i0 + 1 < count) out[i0 + 1] = (T)(rad * sin(th));
     }
   }
 }
 
-kpsb_status la_randn(float* out, long long count, unsigned long long seed, cudaStream_t st) {
+template <typename T>
+kpsb_status la_randn(T* out, long long count, unsigned long long seed, cudaStream_t st) {
   int nb = (int)std::min<long long>((count / 4 + 255) / 256 + 1, 152 * 8);
-  randn_kernel<<<nb, 256, 0, st>>>(out, count, (uint32_t)seed, (uint32_t)(seed >> 32));
+  randn_kernel<T><<<nb, 256, 0, st>>>(out, count, (uint32_t)seed, (uint32_t)(seed >> 32));
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
 }
+template kpsb_status la_randn<float>(float*, long long, unsigned long long, cudaStream_t);
+template kpsb_status la_randn<double>(double*, long long, unsigned long long, cudaStream_t);
 
 }  // namespace kpsb
 

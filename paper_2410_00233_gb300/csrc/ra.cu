@@ -36,18 +36,19 @@ __device__ __forceinline__ bool ra_tile_anti(int tr, int tq, int c, int s, int n
 // One 64x64 tile of one column of V: diagonal and anti-diagonal partial sums.  The last
 // block of each column combines the partials (fixed order) into D, mixes with P and
 // writes w.
+template <typename T>
 __global__ void __launch_bounds__(256) ra_reduce_kernel(
-    const float* __restrict__ V, int ldv, int n, int bc, int s_red, int c_red, int s_exp,
-    const float* __restrict__ psf, int s0, int transpose, float* __restrict__ part,
-    unsigned int* __restrict__ counters, float* __restrict__ wout) {
-  __shared__ float tile[RA_TS * (RA_TS + 1)];
+    const T* __restrict__ V, int ldv, int n, int bc, int s_red, int c_red, int s_exp,
+    const T* __restrict__ psf, int s0, int transpose, T* __restrict__ part,
+    unsigned int* __restrict__ counters, T* __restrict__ wout) {
+  __shared__ T tile[RA_TS * (RA_TS + 1)];
   __shared__ double Dsh[RA_MAX_S];
   const int nt = (n + RA_TS - 1) / RA_TS;
   const int ntiles = nt * nt;
   const int tr = blockIdx.x % nt, tq = blockIdx.x / nt;
   const int col = blockIdx.y;
-  const float* v = V + (size_t)col * ldv;
-  float* mypart = part + ((size_t)col * ntiles + blockIdx.x) * RA_SLOTS;
+  const T* v = V + (size_t)col * ldv;
+  T* mypart = part + ((size_t)col * ntiles + blockIdx.x) * RA_SLOTS;
   const bool rel_d = ra_tile_direct(tr, tq, c_red, s_red);
   const bool rel_a = bc == KPSB_BC_REFLEXIVE && ra_tile_anti(tr, tq, c_red, s_red, n);
   if (rel_d || rel_a) {
@@ -55,14 +56,14 @@ __global__ void __launch_bounds__(256) ra_reduce_kernel(
     const int r = tr * RA_TS + rl;
     for (int ql = q0; ql < RA_TS; ql += 4) {
       int q = tq * RA_TS + ql;
-      tile[ql * (RA_TS + 1) + rl] = (r < n && q < n) ? v[r + (size_t)q * n] : 0.f;
+      tile[ql * (RA_TS + 1) + rl] = (r < n && q < n) ? v[r + (size_t)q * n] : (T)0;
     }
     __syncthreads();
     const int t = threadIdx.x;
     if (t < 2 * RA_TS - 1) {
       if (rel_d) {
         int d = t - (RA_TS - 1);  // rl - ql
-        float acc = 0.f;
+        T acc = 0;
         int lo = d > 0 ? d : 0, hi = d < 0 ? RA_TS + d : RA_TS;
         for (int i = lo; i < hi; ++i) acc += tile[(i - d) * (RA_TS + 1) + i];
         mypart[t] = acc;
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(256) ra_reduce_kernel(
     } else if (t >= 128 && t < 128 + 2 * RA_TS - 1) {
       if (rel_a) {
         int sg = t - 128;  // rl + ql
-        float acc = 0.f;
+        T acc = 0;
         int lo = sg - (RA_TS - 1) > 0 ? sg - (RA_TS - 1) : 0, hi = sg < RA_TS - 1 ? sg : RA_TS - 1;
         for (int i = lo; i <= hi; ++i) acc += tile[(sg - i) * (RA_TS + 1) + i];
         mypart[t] = acc;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256) ra_reduce_kernel(
   }
   if (!last_block_arrive(&counters[col], (unsigned)ntiles)) return;
   // ---- last block of this column: D_t for every tap t, fixed order ----
-  const float* cp = part + (size_t)col * ntiles * RA_SLOTS;
+  const T* cp = part + (size_t)col * ntiles * RA_SLOTS;
   for (int t = threadIdx.x; t < s_red; t += blockDim.x) {
     double acc = 0.0;
     const int dl = t - c_red;  // global diagonal r - q
@@ -121,28 +122,29 @@ __global__ void __launch_bounds__(256) ra_reduce_kernel(
     } else {
       for (int b = 0; b < s_red; ++b) acc += (double)psf[o + b * s0] * Dsh[b];
     }
-    wout[(size_t)col * s_exp + o] = (float)acc;
+    wout[(size_t)col * s_exp + o] = (T)acc;
   }
 }
 
 // U[i + j n] = sum over taps t with j = ext(i - t + c) of w_t, optionally + beta * prev.
+template <typename T>
 __global__ void __launch_bounds__(256) ra_expand_kernel(
-    const float* __restrict__ wbuf, int s_exp, int c_exp, int n, int bc, float* __restrict__ U,
-    int ldu, const float* __restrict__ prev, int ldp, const double* __restrict__ beta_dev,
-    float beta_host, const int* __restrict__ skip) {
+    const T* __restrict__ wbuf, int s_exp, int c_exp, int n, int bc, T* __restrict__ U,
+    int ldu, const T* __restrict__ prev, int ldp, const double* __restrict__ beta_dev,
+    T beta_host, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  __shared__ float w[RA_MAX_S];
+  __shared__ T w[RA_MAX_S];
   const int col = blockIdx.y;
   for (int t = threadIdx.x; t < s_exp; t += blockDim.x) w[t] = wbuf[(size_t)col * s_exp + t];
   __syncthreads();
-  float beta = beta_dev ? (float)(*beta_dev) : beta_host;
+  T beta = beta_dev ? (T)(*beta_dev) : beta_host;
   const long long N = (long long)n * n;
-  float* u = U + (size_t)col * ldu;
-  const float* pv = prev ? prev + (size_t)col * ldp : nullptr;
+  T* u = U + (size_t)col * ldu;
+  const T* pv = prev ? prev + (size_t)col * ldp : nullptr;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
        e += (long long)gridDim.x * blockDim.x) {
     int i = (int)(e % n), j = (int)(e / n);
-    float acc = 0.f;
+    T acc = 0;
     int t = i - j + c_exp;
     if (t >= 0 && t < s_exp) acc += w[t];
     if (bc == KPSB_BC_REFLEXIVE) {
@@ -151,26 +153,26 @@ __global__ void __launch_bounds__(256) ra_expand_kernel(
       t -= 2 * n;
       if (t >= 0 && t < s_exp) acc += w[t];
     }
-    if (pv) acc = fmaf(beta, pv[e], acc);
+    if (pv) acc = fma(beta, pv[e], acc);
     u[e] = acc;
   }
 }
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-size_t ra_scratch_bytes(int n, int nb, int s_exp) {
+size_t ra_scratch_bytes(int n, int nb, int s_exp, size_t el) {
   int nt = (n + RA_TS - 1) / RA_TS;
-  return align256((size_t)nb * sizeof(unsigned int)) + align256((size_t)nb * s_exp * sizeof(float)) +
-         align256((size_t)nb * nt * nt * RA_SLOTS * sizeof(float));
+  return align256((size_t)nb * sizeof(unsigned int)) + align256((size_t)nb * s_exp * el) +
+         align256((size_t)nb * nt * nt * RA_SLOTS * el);
 }
 
-RAScratch ra_scratch_carve(void* base, int n, int nb, int s_exp) {
+RAScratch ra_scratch_carve(void* base, int n, int nb, int s_exp, size_t el) {
   char* p = (char*)base;
   RAScratch s;
   s.counters = (unsigned int*)p;
   p += align256((size_t)nb * sizeof(unsigned int));
   s.w = (float*)p;
-  p += align256((size_t)nb * s_exp * sizeof(float));
+  p += align256((size_t)nb * s_exp * el);
   s.part = (float*)p;
   return s;
 }
@@ -188,24 +190,40 @@ kpsb_status ra_check(int s0, int s1, int n, int bc) {
   return KPSB_OK;
 }
 
-kpsb_status ra_apply(const float* psf, int s0, int s1, int n, int bc, const float* V, int ldv,
-                     int nb, float* U, int ldu, int transpose, const float* prev, int ldp,
-                     const double* beta_dev, float beta_host, const int* skip,
-                     const RAScratch& scr, cudaStream_t st) {
+template <typename T>
+static kpsb_status ra_apply_t(const T* psf, int s0, int s1, int n, int bc, const T* V, int ldv, int nb, T* U,
+                              int ldu, int transpose, const T* prev, int ldp, const double* beta_dev,
+                              T beta_host, const int* skip, const RAScratch& scr, cudaStream_t st) {
   const int s_red = transpose ? s1 : s0, c_red = s_red / 2;
   const int s_exp = transpose ? s0 : s1, c_exp = s_exp / 2;
   const int nt = (n + RA_TS - 1) / RA_TS;
   dim3 g1(nt * nt, nb);
-  ra_reduce_kernel<<<g1, 256, 0, st>>>(V, ldv, n, bc, s_red, c_red, s_exp, psf, s0, transpose,
-                                       scr.part, scr.counters, scr.w);
+  ra_reduce_kernel<T><<<g1, 256, 0, st>>>(V, ldv, n, bc, s_red, c_red, s_exp, psf, s0, transpose,
+                                          (T*)scr.part, scr.counters, (T*)scr.w);
   KPSB_CHECK_LAUNCH();
   long long N = (long long)n * n;
   int bx = (int)std::min<long long>((N + 255) / 256, 1024);
   dim3 g2(bx, nb);
-  ra_expand_kernel<<<g2, 256, 0, st>>>(scr.w, s_exp, c_exp, n, bc, U, ldu, prev, ldp, beta_dev,
-                                       beta_host, skip);
+  ra_expand_kernel<T><<<g2, 256, 0, st>>>((const T*)scr.w, s_exp, c_exp, n, bc, U, ldu, prev, ldp, beta_dev,
+                                          beta_host, skip);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
+}
+
+kpsb_status ra_apply(const float* psf, int s0, int s1, int n, int bc, const float* V, int ldv,
+                     int nb, float* U, int ldu, int transpose, const float* prev, int ldp,
+                     const double* beta_dev, float beta_host, const int* skip,
+                     const RAScratch& scr, cudaStream_t st) {
+  return ra_apply_t<float>(psf, s0, s1, n, bc, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host,
+                           skip, scr, st);
+}
+
+kpsb_status ra_apply(const double* psf, int s0, int s1, int n, int bc, const double* V, int ldv,
+                     int nb, double* U, int ldu, int transpose, const double* prev, int ldp,
+                     const double* beta_dev, double beta_host, const int* skip,
+                     const RAScratch& scr, cudaStream_t st) {
+  return ra_apply_t<double>(psf, s0, s1, n, bc, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev,
+                            beta_host, skip, scr, st);
 }
 
 // ---- dense R(A) from the index map (tests, explicit mode) -------------------------------

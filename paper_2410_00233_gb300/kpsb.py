@@ -36,7 +36,8 @@ class KpsbError(RuntimeError):
 
 class BuildOpts(C.Structure):
     _fields_ = [("p", C.c_int), ("k_min", C.c_int), ("one_sided", C.c_int), ("power_iters", C.c_int),
-                ("seed", C.c_ulonglong), ("start_host", C.POINTER(C.c_float)), ("stream", C.c_void_p)]
+                ("seed", C.c_ulonglong), ("start_host", C.POINTER(C.c_float)), ("stream", C.c_void_p),
+                ("fp64", C.c_int)]
 
 
 class SBOpts(C.Structure):
@@ -185,8 +186,9 @@ class KP:
         return kp_info(self)
 
 
-def _build_opts(p=0, k_min=0, one_sided=False, power_iters=0, seed=0, start=None, stream=0):
+def _build_opts(p=0, k_min=0, one_sided=False, power_iters=0, seed=0, start=None, stream=0, fp64=False):
     o = BuildOpts()
+    o.fp64 = int(bool(fp64))
     o.p, o.k_min, o.one_sided, o.power_iters = int(p), int(k_min), int(bool(one_sided)), int(power_iters)
     o.seed = int(seed)
     keep = None
@@ -198,10 +200,10 @@ def _build_opts(p=0, k_min=0, one_sided=False, power_iters=0, seed=0, start=None
 
 
 def kp_build(psf, n: int, bc: int, rank_or_tol: float, method: int = EGKB, *, p=0, k_min=0,
-             one_sided=False, power_iters=0, seed=0, start=None, stream=0) -> KP:
-    """TSVD of R(A) + Terms(A_k) (see kp_build in include/kpsb.h)."""
+             one_sided=False, power_iters=0, seed=0, start=None, stream=0, fp64=False) -> KP:
+    """TSVD of R(A) + Terms(A_k) (see kp_build in include/kpsb.h); fp64=True: FP64 TSVD."""
     ps = _f64(psf)
-    o, keep = _build_opts(p, k_min, one_sided, power_iters, seed, start, stream)
+    o, keep = _build_opts(p, k_min, one_sided, power_iters, seed, start, stream, fp64)
     out = C.c_void_p()
     _check("kp_build", lib().kp_build(_pd(ps), ps.shape[0], ps.shape[1], int(n), int(bc),
                                       float(rank_or_tol), int(method), C.byref(o), C.byref(out)))
@@ -210,12 +212,12 @@ def kp_build(psf, n: int, bc: int, rank_or_tol: float, method: int = EGKB, *, p=
 
 
 def kp_build_dense(A, n: int, rank_or_tol: float, method: int = EGKB, *, p=0, k_min=0, one_sided=False,
-                   power_iters=0, seed=0, start=None, stream=0) -> KP:
+                   power_iters=0, seed=0, start=None, stream=0, fp64=False) -> KP:
     """KP sum of a general operator given as an explicit (n^2 x n^2) matrix (see kp_build_dense)."""
     a = _f64(A)
     if a.shape != (n * n, n * n):
         raise ValueError(f"A must be {n * n} x {n * n}")
-    o, keep = _build_opts(p, k_min, one_sided, power_iters, seed, start, stream)
+    o, keep = _build_opts(p, k_min, one_sided, power_iters, seed, start, stream, fp64)
     out = C.c_void_p()
     _check("kp_build_dense", lib().kp_build_dense(_pd(a), int(n), float(rank_or_tol), int(method), C.byref(o),
                                                   C.byref(out)))
@@ -325,7 +327,8 @@ def kp_build_batched(problems) -> list:
         ps = _f64(pr["psf"])
         keep.append(ps)
         o, k2 = _build_opts(pr.get("p", 0), pr.get("k_min", 0), pr.get("one_sided", False),
-                            pr.get("power_iters", 0), pr.get("seed", 0), pr.get("start"))
+                            pr.get("power_iters", 0), pr.get("seed", 0), pr.get("start"),
+                            fp64=pr.get("fp64", False))
         keep.append(k2)
         arr[i].psf = _pd(ps)
         arr[i].s0, arr[i].s1 = ps.shape

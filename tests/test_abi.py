@@ -75,3 +75,6 @@ def test_invalid_arguments_fail_without_touching_the_gpu():
     dummy = (ctypes.c_double * 4)()
     out = ctypes.c_void_p()
     assert K.lib().kp_build_dense(dummy, 200, 3.0, K.EGKB, None, ctypes.byref(out)) == -1  # n > 128
+    with pytest.raises(K.KpsbError) as e:
+        K.kp_build_dense(np.eye(16), 4, 2.0, K.EGKB, fp64=True)  # explicit operators: SP TSVD only
+    assert e.value.code == -1

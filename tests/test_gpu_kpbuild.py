@@ -144,3 +144,52 @@ def test_large_config_sampled_sigma_vs_closed_form():
     U, sig, V = _factor_vectors(K, kp)
     assert abs(abs(U[:, 0] @ Ucf[:, 0]) - 1) < 1e-3
     assert abs(abs(V[:, 0] @ Vcf[:, 0]) - 1) < 1e-3
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("one_sided", [False, True])
+def test_fp64_egkb_matches_closed_form_to_fp64_accuracy(bc, one_sided):
+    """The FP64 TSVD (PSF, bases and R(A) products in double; the paper's DP variant):
+    sigma_k within 1e-10 sigma_1 of the closed form sigma(Gx^1/2 P^T Gy^1/2), full or
+    one-sided reorthogonalisation, against 1e-4 for the single-precision path."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    pr = I.problem_small(3)
+    ref = O.r_sigma_closed_form(O.r_factors(pr.psf, pr.n, bc))
+    kp = K.kp_build(pr.psf, pr.n, bc, 5, K.EGKB, p=4, seed=7, one_sided=one_sided, fp64=True)
+    sig = K.kp_info(kp)["sigma"]
+    assert np.max(np.abs(sig - ref[:5])) <= 1e-10 * ref[0]
+    sp = K.kp_info(K.kp_build(pr.psf, pr.n, bc, 5, K.EGKB, p=4, seed=7, one_sided=one_sided))["sigma"]
+    assert np.max(np.abs(sp - ref[:5])) <= 1e-4 * ref[0]
+
+
+def test_fp64_rsvd_exact_once_the_sketch_spans_the_range():
+    """RSVD in FP64 with k + p >= rank(R(A)) (<= s) recovers the leading singular values to
+    FP64 accuracy (the sketch spans the range of R(A))."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    pr = I.problem_small(5)  # 9 x 9 PSF: rank(R(A)) <= 9
+    ref = O.r_sigma_closed_form(O.r_factors(pr.psf, pr.n, pr.bc))
+    kp = K.kp_build(pr.psf, pr.n, pr.bc, 5, K.RSVD, p=6, seed=3, fp64=True)
+    sig = K.kp_info(kp)["sigma"]
+    assert np.max(np.abs(sig - ref[:5])) <= 1e-10 * ref[0]
+
+
+def test_fp64_egkb_at_medium_size_and_auto_rank():
+    """FP64 EGKB on the medium configuration (n = 128, 31 x 31 mixture PSF, reflexive, automatic
+    rank): the same rank as the single-precision build and sigma within 1e-10 sigma_1 of the
+    closed form; the factors of both builds agree (products, up to sign)."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    pr = I.problem_medium(2)
+    ref = O.r_sigma_closed_form(O.r_factors(pr.psf, pr.n, pr.bc))
+    kd = K.kp_build(pr.psf, pr.n, pr.bc, pr.tau, K.EGKB, p=pr.p, seed=pr.seed, fp64=True)
+    ks = K.kp_build(pr.psf, pr.n, pr.bc, pr.tau, K.EGKB, p=pr.p, seed=pr.seed)
+    sd, ss = K.kp_info(kd)["sigma"], K.kp_info(ks)["sigma"]
+    k = min(len(sd), len(ss))
+    assert abs(len(sd) - len(ss)) <= 1
+    assert np.max(np.abs(sd[:k] - ref[:k])) <= 1e-10 * ref[0]
+    assert np.max(np.abs(ss[:k] - ref[:k])) <= 1e-4 * ref[0]
