@@ -742,7 +742,7 @@ def main():
             "config": {"workload": WORKLOAD, "batch_per_gpu": B, "global_batch": B * world,
                        "n": N_IMG, "psf": PSF_S, "outer_iters": args.outer, "mean_k": statistics.mean(ks),
                        "kp_gemm": prec_name, "l2": "flushed (256 MB write) between timed steps",
-                       "sub_batches": "auto: %d concurrent parts of the batch" % max(1, min(3, B // 64)),
+                       "sub_batches": "auto: %d concurrent parts of the batch" % max(1, min(4, B // 64)),
                        "parallelism": f"dp{world} (independent requests per GPU)"},
             "p50_ms": 1000.0 * lat[len(lat) // 2], "p99_ms": 1000.0 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "isnr_db_mean": statistics.mean(isnr_mixed),

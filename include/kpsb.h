@@ -101,7 +101,7 @@ typedef struct {
   int sub_batches;   /* sb_solve_batched: a size group of P problems is cut into this many
                         parts that run concurrently on their own streams, so one part's
                         FP64 vector kernels overlap another's tensor-core applies (results
-                        do not change).  0 (default): min(3, P / 64), at least 1; 1: off. */
+                        do not change).  0 (default): min(4, P / 64), at least 1; 1: off. */
 } kpsb_sb_opts;
 
 typedef struct {

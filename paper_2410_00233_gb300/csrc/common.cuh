@@ -20,6 +20,7 @@ void clear_error();
 // owner counts the kernels that actually ran.
 void count_launch(long long n = 1);
 void set_capture_mode(bool on);
+void trace(cudaStream_t st, const char* phase);
 bool gemm_timing_enabled();
 // CUDA-event timing (kpsb_gemm_timing / kpsb_timer_stats) by category: the
 // Kronecker-sum GEMM applies and the split Bregman vector kernels.

@@ -1,7 +1,11 @@
 // Instrumentation: process-wide kernel-launch counter and CUDA-event timing of the
 // Kronecker-sum GEMM applies and of the split Bregman vector kernels (recorded on the
 // stream each one runs on, by category).
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <atomic>
+#include <chrono>
 #include <mutex>
 #include <vector>
 
@@ -18,6 +22,17 @@ void count_launch(long long n) {
 }
 
 void set_capture_mode(bool on) { t_capturing = on; }
+
+// Host phase trace: with KPSB_TRACE set in the environment, each call prints one stderr line
+// "[kpsb trace] <seconds since the first trace> <stream> <phase>".
+void trace(cudaStream_t st, const char* phase) {
+  static const bool on = getenv("KPSB_TRACE") != nullptr;
+  if (!on) return;
+  using clk = std::chrono::steady_clock;
+  static const clk::time_point t0 = clk::now();
+  const double t = std::chrono::duration<double>(clk::now() - t0).count();
+  fprintf(stderr, "[kpsb trace] %.6f %p %s\n", t, (void*)st, phase);
+}
 
 namespace {
 struct TimerRec {

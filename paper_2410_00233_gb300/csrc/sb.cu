@@ -12,6 +12,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
 #include <string>
 #include <thread>
 
@@ -451,6 +454,32 @@ __global__ void sb_cond_kernel(cudaGraphConditionalHandle h, const SBProb* __res
   }
 }
 
+// Start gate of the parts that one batched call runs concurrently (one host thread each).
+// Measured on GB300: a graph instantiation issued while other parts' graphs are running can
+// wait for those graphs to finish (seconds) the first time a process holds that many live
+// graphs; with every part's graph instantiated before any part launches, it never waits.
+// A part arrives once: after instantiating its graph, or when it leaves without one.  The
+// wait is bounded, so a part that never arrives costs the others at most that bound.
+struct LaunchGate {
+  std::mutex m;
+  std::condition_variable cv;
+  int arrived = 0, total = 0;
+};
+static thread_local LaunchGate* t_gate = nullptr;
+static thread_local bool t_gate_done = false;
+
+static void gate_arrive(bool wait) {
+  LaunchGate* g = t_gate;
+  if (!g || t_gate_done) return;
+  t_gate_done = true;
+  std::unique_lock<std::mutex> lk(g->m);
+  if (++g->arrived >= g->total) {
+    g->cv.notify_all();
+  } else if (wait) {
+    g->cv.wait_for(lk, std::chrono::seconds(30), [g] { return g->arrived >= g->total; });
+  }
+}
+
 // Builds and runs `max_iters` outer steps of a batch as one CUDA graph: per outer step the
 // head launches, a WHILE node whose body is one CGLS iteration plus the condition kernel,
 // and the shrinkage (initialisation of new problems happens before, in sb_advance).  The graph is captured from the same launch sequences as the
@@ -516,9 +545,16 @@ static kpsb_status sb_graph_run(cudaStream_t st, dim3 gv, const SBProb* dprobs, 
     capturing = false;
     if (s != KPSB_OK || e != cudaSuccess) break;
     if ((e = e2) != cudaSuccess) break;
+    trace(st, "graph captured");
     if ((e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) break;
+    if ((e = cudaGraphUpload(ge, st)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+    trace(st, "graph instantiated and uploaded");
+    gate_arrive(true);
+    trace(st, "graph launch");
     if ((e = cudaGraphLaunch(ge, st)) != cudaSuccess) break;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+    trace(st, "graph done");
   } while (0);
   if (capturing) {
     cudaGraph_t tmp = nullptr;
@@ -721,7 +757,9 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     double ksum = 0.0;
     for (int p = 0; p < P; ++p) ksum += set[p]->kp->k;
     const double apply_flops = 4.0 * ksum * (double)n * n * n;  // 4 k n^3 per problem (Sec. 4.2)
+    trace(st, "advance setup queued");
     if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, gemm_prec, st, &plan))) break;
+    trace(st, "apply plan ready");
     // kernel launches of one apply (forward / transpose)
     const int apply_launches = tc ? tc_plan_launches(plan) : 3;
     const int ap_f = dense ? 2 : apply_launches, ap_b = dense ? 1 : apply_launches;
@@ -792,6 +830,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     } else {
       // Instrumented path: host-driven loop (CUDA events around every KP apply), checking
       // the device flags every few CGLS iterations.
+      gate_arrive(false);
       const int CHUNK = 4;
       for (int ell = 0; ell < outer_steps && s == KPSB_OK; ++ell) {
         if ((s = outer_head(st))) break;
@@ -969,7 +1008,7 @@ extern "C" kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int 
     int g1 = g0;
     while (g1 < count && gkey(order[g1]) == gkey(order[g0])) ++g1;
     const int size = g1 - g0;
-    const int np = std::max(1, std::min(size, o.sub_batches > 0 ? o.sub_batches : std::min(3, size / 64)));
+    const int np = std::max(1, std::min(size, o.sub_batches > 0 ? o.sub_batches : std::min(4, size / 64)));
     for (int q = 0; q < np; ++q) groups.emplace_back(g0 + size * q / np, g0 + size * (q + 1) / np);
     g0 = g1;
   }
@@ -1007,8 +1046,12 @@ extern "C" kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int 
       s = KPSB_ECUDA;
     } else {
       std::vector<std::thread> th;
+      LaunchGate gate;
+      gate.total = (int)groups.size();
       for (size_t gi = 0; gi < groups.size(); ++gi)
         th.emplace_back([&, gi] {
+          t_gate = &gate;
+          t_gate_done = false;
           cudaStream_t gst = nullptr;
           cudaError_t ge = cudaSetDevice(dev);
           if (ge == cudaSuccess) ge = cudaStreamCreateWithFlags(&gst, cudaStreamNonBlocking);
@@ -1017,6 +1060,8 @@ extern "C" kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int 
             run_group(gi, gst);
             ge = cudaStreamSynchronize(gst);
           }
+          gate_arrive(false);  // a part that left before launching a graph
+          t_gate = nullptr;
           if (gst) cudaStreamDestroy(gst);
           if (ge != cudaSuccess && gs[gi] == KPSB_OK) {
             gs[gi] = KPSB_ECUDA;

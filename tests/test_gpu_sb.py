@@ -371,7 +371,7 @@ def test_persistent_apply_with_more_problems_than_sms():
 
 
 def test_sub_batches_give_the_same_bits():
-    """A batch cut into concurrent parts (sub_batches 1, 2, 3 and the default) returns the
+    """A batch cut into concurrent parts (sub_batches 1 to 5 and the default) returns the
     same bits for every problem: each part is an independent batch of the same kernels."""
     need_gpu()
     from paper_2410_00233_gb300 import kpsb as K
@@ -386,7 +386,7 @@ def test_sub_batches_give_the_same_bits():
                                np.sort(g.random(k))[::-1] + 0.1)
         jobs.append(dict(kp=kp, b=g.standard_normal((n, n)), mu=1.0, lam=0.1, tv=K.ANISO, iters=2))
     ref, st_ref = K.sb_solve_batched(jobs, prec=K.P_TF32X2, sub_batches=1)
-    for sb in (2, 3, 0):
+    for sb in (2, 3, 4, 5, 0):
         outs, st = K.sb_solve_batched(jobs, prec=K.P_TF32X2, sub_batches=sb)
         for a, b, s1, s2 in zip(ref, outs, st_ref, st):
             assert np.array_equal(a, b) and s1.iota_total == s2.iota_total
