@@ -325,6 +325,16 @@ kpsb_status kpsb_apply_counts(unsigned long long* problem_applies, unsigned long
  * category. */
 kpsb_status kpsb_timer_stats(int category, unsigned long long* launches, double* ms, double* flops);
 
+/* Self-check of the exact integer binary32 <-> binary64 conversions that the split Bregman
+ * vector kernels use in place of the conversion instructions (which GB300 issues to its FP64
+ * pipe): every binary32 value widened, and n_random binary64 values (spread over the
+ * binary32 subnormal, normal and overflow range, with round-to-nearest-even tie cases, zeros,
+ * infinities and NaNs; drawn from `seed`) rounded, each compared bit for bit with the
+ * hardware conversion on the current device (NaN against NaN).  *mismatches receives the
+ * number that differ (0 expected).  Blocking; KPSB_ECUDA on a CUDA error. */
+kpsb_status kpsb_conversion_check(unsigned long long n_random, unsigned long long seed,
+                                  unsigned long long* mismatches);
+
 /* Thread-local message for the last error of this thread ("" if none). */
 const char* kpsb_last_error(void);
 

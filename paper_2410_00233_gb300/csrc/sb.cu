@@ -18,6 +18,7 @@
 #include <string>
 #include <thread>
 
+#include "fpconv.cuh"
 #include "kpsb_internal.cuh"
 
 namespace kpsb {
@@ -25,21 +26,28 @@ namespace kpsb {
 static constexpr int SB_T = 256;
 // Minimum resident blocks per SM requested from the compiler for the vector kernels
 // (register cap 65536 / (SB_T * KPSB_SB_MIN_BLOCKS)).
+// Measured on the 256-request medium batch (4 concurrent parts): 6 (40 registers; a few
+// bytes of spill in the ||z||^2 kernel) beats 4 (64 registers) by 3 %: these kernels wait on
+// memory, and more resident warps hide more of it.
 #ifndef KPSB_SB_MIN_BLOCKS
-#define KPSB_SB_MIN_BLOCKS 4
+#define KPSB_SB_MIN_BLOCKS 6
 #endif
 #define SB_BOUNDS __launch_bounds__(SB_T, KPSB_SB_MIN_BLOCKS)
 #ifndef KPSB_SB_MIN_BLOCKS_X
-#define KPSB_SB_MIN_BLOCKS_X KPSB_SB_MIN_BLOCKS
+#define KPSB_SB_MIN_BLOCKS_X 5  // 48 registers: 6 spills in the x update
 #endif
 #define SB_BOUNDS_X __launch_bounds__(SB_T, KPSB_SB_MIN_BLOCKS_X)  // x and r update kernels
+// once-per-outer-step kernels and the CUDA-core path's x update, which would spill under
+// the caps above
+#define SB_BOUNDS_WIDE __launch_bounds__(SB_T, 4)
 // Each block of a vector kernel handles one fixed chunk of SB_CHUNK elements (SB_EPT per
 // thread) and writes one reduction partial: the summation order depends on n only, so a
 // problem gives the same bits alone, in any batch, and in the serving loop.
 #ifndef KPSB_SB_EPT
-#define KPSB_SB_EPT 16
+#define KPSB_SB_EPT 8
 #endif
-static constexpr int SB_EPT = KPSB_SB_EPT;  // 4, 8 or 16
+static constexpr int SB_EPT = KPSB_SB_EPT;  // 4, 8 or 16 (8: twice the blocks of 16, which
+                                            // the concurrent parts interleave better)
 static constexpr int SB_CHUNK = SB_T * SB_EPT;
 static constexpr int SB_TILES_PER_CHUNK = SB_CHUNK / 1024;  // 32 x 32 tiles
 
@@ -143,7 +151,7 @@ __global__ void SB_BOUNDS sb_setup_kernel(const SBProb* __restrict__ probs) {
 }
 
 // Outer step start: xprev = x; CGLS from x = 0 with r = bhat = [sqrt(mu) b; lam(dx-gx); lam(dy-gy)].
-__global__ void SB_BOUNDS sb_outer_init_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS_WIDE sb_outer_init_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->sb_active)
   SB_FOR_E {
     P.xprev[e] = P.x[e];
@@ -168,7 +176,7 @@ __global__ void SB_BOUNDS sb_cgls_f_kernel(const SBProb* __restrict__ probs, int
   double ss = 0.0;
   SB_FOR_RC {
     const int r = r_, c = c_;
-    const double f1 = P.f1f ? (double)P.f1f[e] : P.f1[e];
+    const double f1 = P.f1f ? f2d_bits(P.f1f[e]) : P.f1[e];
     double t = (c < n - 1 ? P.r2[e] : 0.0) + (r < n - 1 ? P.r3[e] : 0.0);
     if (c >= 1) t -= P.r2[e - n];
     if (r >= 1) t -= P.r3[e - 1];
@@ -243,7 +251,7 @@ __global__ void SB_BOUNDS sb_cgls_zz_kernel(const SBProb* __restrict__ probs) {
 }
 
 // x += mu w; r -= mu z (steps 5-6); RC_CGLS = ||mu w|| / ||x|| (eq. (5.1)) and the stop test.
-__global__ void SB_BOUNDS_X sb_cgls_x_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS_WIDE sb_cgls_x_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
   const double mu = P.sc->step;
   const double c1 = -mu * P.sqrt_mu, c2 = -mu * (0.5 * P.lam);  // r -= mu z, one FMA each
@@ -272,7 +280,7 @@ __global__ void SB_BOUNDS_X sb_cgls_x_kernel(const SBProb* __restrict__ probs) {
 }
 
 // Shrinkage (3.10) / (3.13) and Bregman updates (3.8)-(3.9); RC_SB (5.2).
-__global__ void SB_BOUNDS sb_shrink_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS_WIDE sb_shrink_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->sb_active)
   double sd = 0.0, sp = 0.0;
   const double thr = P.thr;
@@ -338,8 +346,13 @@ __device__ __forceinline__ void store_xt_tile(float* __restrict__ xt, int n, int
 }
 
 // Writes the TF32 hi / lo split of v into the tile; returns v rounded to FP32.
+// KPSB_SPLIT_INT_ROUND 1 rounds v to FP32 on the integer pipes (same bits as the conversion
+// instruction, which issues to the FP64 pipe).
+#ifndef KPSB_SPLIT_INT_ROUND
+#define KPSB_SPLIT_INT_ROUND 0
+#endif
 __device__ __forceinline__ float put_split(float (*th)[33], float (*tl)[33], int a, int b, double v) {
-  const float f = (float)v;
+  const float f = KPSB_SPLIT_INT_ROUND ? d2f_rn_bits(v) : (float)v;
   const float h = tf32_rna(f);
   th[a][b] = h;
   tl[a][b] = tf32_rna(f - h);

@@ -121,6 +121,7 @@ _SIGS = {
     "kpsb_gemm_stats": (C.c_int, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "kpsb_timer_stats": (C.c_int, [C.c_int, C.POINTER(C.c_ulonglong), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "kpsb_apply_counts": (C.c_int, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
+    "kpsb_conversion_check": (C.c_int, [C.c_ulonglong, C.c_ulonglong, C.POINTER(C.c_ulonglong)]),
 }
 
 
@@ -480,6 +481,15 @@ def kpsb_apply_counts():
     pa, kn3 = C.c_ulonglong(), C.c_ulonglong()
     _check("kpsb_apply_counts", lib().kpsb_apply_counts(C.byref(pa), C.byref(kn3)))
     return int(pa.value), int(kn3.value)
+
+
+def kpsb_conversion_check(n_random=1 << 26, seed=1):
+    """Mismatches of the integer binary32 <-> binary64 conversions against the hardware ones
+    (every binary32 value, n_random binary64 values); 0 expected."""
+    bad = C.c_ulonglong()
+    _check("kpsb_conversion_check", lib().kpsb_conversion_check(C.c_ulonglong(n_random), C.c_ulonglong(seed),
+                                                                C.byref(bad)))
+    return int(bad.value)
 
 
 def kpsb_small_svd(A):
