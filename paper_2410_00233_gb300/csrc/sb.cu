@@ -212,7 +212,7 @@ __global__ void SB_BOUNDS sb_cgls_w_kernel(const SBProb* __restrict__ probs, int
 __global__ void SB_BOUNDS sb_cgls_zz_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
   // |z|^2 = mu |z1|^2 + (lambda/2)^2 (|raw Dx w|^2 + |raw Dy w|^2), two sums.  z1 from the
-  // tensor-core apply is FP32: its squares are summed in FP32 per thread (16 terms), the
+  // tensor-core apply is FP32: its squares are summed in FP32 per thread (SB_EPT terms), the
   // partials in FP64.
   double sz = 0.0, sd = 0.0;
   float szf = 0.0f;
@@ -392,7 +392,7 @@ __global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int i
   (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
   const double dl = P.sc->delta;
-  float wwf = 0.0f;  // ||w||^2 for RC_CGLS, from the FP32 value split below (16 terms per thread)
+  float wwf = 0.0f;  // ||w||^2 for RC_CGLS, from the FP32 value split below (SB_EPT terms per thread)
   SB_TILES_BEGIN
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
