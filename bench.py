@@ -398,7 +398,7 @@ def sweep_main(args):
 def direct_main(args):
     """The paper's comparison (Sec. 4.3, Table 4): split Bregman with the explicit operator A
     (FP64 dense products) against the same solve with the KP sum (FP64 and TF32x2 products),
-    on one configuration-2 request (n = 128), with the predicted speed-up of eq. (4.4)."""
+    on one medium request (n = 128, 31x31 PSF), with the predicted speed-up of eq. (4.4)."""
     import numpy as np
     import torch
 
@@ -448,8 +448,8 @@ def direct_main(args):
 def tsvd_main(args):
     """The paper's SP/DP comparison of the TSVD (Sec. 1, Sec. 5: EGKB(SP), EGKB(DP), RSVD):
     build time per precision and reorthogonalisation, and how far the single-precision
-    singular values sit from the double-precision ones, at configuration 2 (n = 128, auto k)
-    and configuration 3 (n = 512, k = 20)."""
+    singular values sit from the double-precision ones, on the medium workload (n = 128, auto
+    k) and the large one (n = 512, 63x63 turbulence-like PSF, k = 20)."""
     import numpy as np
     import torch
 
@@ -459,8 +459,8 @@ def tsvd_main(args):
     torch.cuda.set_device(0)
     K.lib()
     rows = []
-    for name, pr, rank in (("cfg2 n=128 auto-k", I.problem_medium(0), None),
-                           ("cfg3 n=512 k=20", I.problem_large(0), 20)):
+    for name, pr, rank in (("medium n=128 auto-k", I.problem_medium(0), None),
+                           ("large n=512 k=20", I.problem_large(0), 20)):
         rk = pr.tau if rank is None else rank
         variants = [("EGKB full", K.EGKB, False), ("EGKB one-sided", K.EGKB, True)]
         if rank is not None:
