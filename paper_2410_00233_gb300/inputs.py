@@ -130,7 +130,7 @@ class Problem:
     x_true: np.ndarray
     zeta: np.ndarray  # noise direction, n x n
     eta: float  # noise level
-    start: np.ndarray  # GKB start vector y (length n^2, float32 draws widened to float64)
+    start: np.ndarray  # GKB start vector y (length n^2, float64 draws; a FP32 build rounds them)
     k: int = 5  # target rank (fixed-rank mode) or cap (auto mode)
     p: int = 2
     tau: float = 0.0  # > 0: automatic rank with relative tolerance tau
