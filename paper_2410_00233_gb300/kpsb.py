@@ -166,10 +166,18 @@ def _pf(a: np.ndarray):
 
 
 class KP:
-    """Owning handle of a KP-sum operator (device factors)."""
+    """Owning handle of a KP-sum operator (device factors) for n x n images."""
 
-    def __init__(self, ptr: int):
+    def __init__(self, ptr: int, n: int | None = None):
         self.ptr = C.c_void_p(ptr)
+        self._n = None if n is None else int(n)
+
+    @property
+    def n(self) -> int:
+        """Image side of the operator (read from the handle once if not known)."""
+        if self._n is None:
+            self._n = kp_info(self)["n"]
+        return self._n
 
     def close(self):
         if self.ptr and self.ptr.value:
@@ -185,6 +193,39 @@ class KP:
     @property
     def info(self):
         return kp_info(self)
+
+
+# The C ABI reads and writes host arrays by the sizes the operator implies, so every host
+# array is checked here first: a wrong shape is a ValueError, never an out-of-bounds access.
+def _psf2d(psf) -> np.ndarray:
+    ps = _f64(psf)
+    if ps.ndim != 2 or ps.shape[0] < 1 or ps.shape[1] < 1:
+        raise ValueError(f"psf must be a non-empty 2-D array (got shape {ps.shape})")
+    return ps
+
+
+def _image(kp: "KP", a, name: str) -> np.ndarray:
+    af = _f64(a)
+    n = kp.n
+    if af.shape != (n, n):
+        raise ValueError(f"{name} must be an {n} x {n} array for this operator (got shape {af.shape})")
+    return af
+
+
+def _check_start(start, n: int, rank_or_tol: float, method: int, p: int):
+    """A caller's start is the EGKB start vector y (n^2 entries) or the RSVD test matrix F
+    (n^2 x k_p, k_p = k + p with p defaulting to max(2, ceil(k/4)), as the library does)."""
+    if start is None:
+        return
+    if method == RSVD:
+        if rank_or_tol < 1.0:
+            return  # the library rejects automatic rank with RSVD itself
+        k = int(rank_or_tol)
+        need = n * n * (k + (int(p) if p > 0 else max(2, (k + 3) // 4)))
+    else:
+        need = n * n
+    if np.size(start) != need:
+        raise ValueError(f"start must have {need} entries for this build (got {np.size(start)})")
 
 
 def _build_opts(p=0, k_min=0, one_sided=False, power_iters=0, seed=0, start=None, stream=0, fp64=False):
@@ -203,13 +244,14 @@ def _build_opts(p=0, k_min=0, one_sided=False, power_iters=0, seed=0, start=None
 def kp_build(psf, n: int, bc: int, rank_or_tol: float, method: int = EGKB, *, p=0, k_min=0,
              one_sided=False, power_iters=0, seed=0, start=None, stream=0, fp64=False) -> KP:
     """TSVD of R(A) + Terms(A_k) (see kp_build in include/kpsb.h); fp64=True: FP64 TSVD."""
-    ps = _f64(psf)
+    ps = _psf2d(psf)
+    _check_start(start, int(n), float(rank_or_tol), int(method), int(p))
     o, keep = _build_opts(p, k_min, one_sided, power_iters, seed, start, stream, fp64)
     out = C.c_void_p()
     _check("kp_build", lib().kp_build(_pd(ps), ps.shape[0], ps.shape[1], int(n), int(bc),
                                       float(rank_or_tol), int(method), C.byref(o), C.byref(out)))
     del keep
-    return KP(out.value)
+    return KP(out.value, n)
 
 
 def kp_build_dense(A, n: int, rank_or_tol: float, method: int = EGKB, *, p=0, k_min=0, one_sided=False,
@@ -218,12 +260,13 @@ def kp_build_dense(A, n: int, rank_or_tol: float, method: int = EGKB, *, p=0, k_
     a = _f64(A)
     if a.shape != (n * n, n * n):
         raise ValueError(f"A must be {n * n} x {n * n}")
+    _check_start(start, int(n), float(rank_or_tol), int(method), int(p))
     o, keep = _build_opts(p, k_min, one_sided, power_iters, seed, start, stream, fp64)
     out = C.c_void_p()
     _check("kp_build_dense", lib().kp_build_dense(_pd(a), int(n), float(rank_or_tol), int(method), C.byref(o),
                                                   C.byref(out)))
     del keep
-    return KP(out.value)
+    return KP(out.value, n)
 
 
 def kp_info(kp: KP):
@@ -248,27 +291,33 @@ def kp_get_factors(kp: KP):
 
 
 def kp_from_factors(Ax, Ay, sigma) -> KP:
+    """Handle from k terms Ax[i], Ay[i] (n x n each) and sigma (k)."""
     Ax = np.asarray(Ax, dtype=np.float32)
     Ay = np.asarray(Ay, dtype=np.float32)
+    if Ax.ndim != 3 or Ax.shape[1] != Ax.shape[2] or Ay.shape != Ax.shape:
+        raise ValueError(f"Ax and Ay must both be k x n x n (got {Ax.shape} and {Ay.shape})")
     k, n, _ = Ax.shape
+    if np.shape(sigma) != (k,):
+        raise ValueError(f"sigma must have k = {k} entries (got shape {np.shape(sigma)})")
     ax = np.ascontiguousarray(Ax.transpose(0, 2, 1)).reshape(-1)  # column-major blocks
     ay = np.ascontiguousarray(Ay.transpose(0, 2, 1)).reshape(-1)
     sg = np.ascontiguousarray(sigma, dtype=np.float64)
     out = C.c_void_p()
     _check("kp_from_factors", lib().kp_from_factors(n, k, _pf(ax), _pf(ay), _pd(sg), C.byref(out)))
-    return KP(out.value)
+    return KP(out.value, n)
 
 
 def kp_dense_blur(psf, n: int, bc: int) -> KP:
     """Handle of the explicit blurring operator A (n^2 x n^2 FP64 on the device, n <= 128)."""
-    pf = _f64(psf)
+    pf = _psf2d(psf)
     out = C.c_void_p()
     _check("kp_dense_blur", lib().kp_dense_blur(_pd(pf), pf.shape[0], pf.shape[1], int(n), int(bc), C.byref(out)))
-    return KP(out.value)
+    return KP(out.value, n)
 
 
 def kp_apply(kp: KP, X, transpose: int = 0, prec: int = P_FP64) -> np.ndarray:
-    Xf = _f64(X)
+    """Y = sum_i sigma_i Ay_i X Ax_i^T (transpose = 0) or its adjoint, X an n x n array."""
+    Xf = _image(kp, X, "X")
     Y = np.zeros_like(Xf, order="F")
     _check("kp_apply", lib().kp_apply(kp.ptr, _pd(Xf), _pd(Y), int(transpose), int(prec)))
     return Y
@@ -303,7 +352,7 @@ def _stats(s: SBStats) -> Stats:
 
 def sb_solve(kp: KP, b, mu: float, lam: float, tv: int, iters: int, **opts):
     """Split Bregman deblurring on host arrays; returns (x, Stats)."""
-    bf = _f64(b)
+    bf = _image(kp, b, "b")
     x = np.zeros_like(bf, order="F")
     st = SBStats()
     o = _sb_opts(**opts)
@@ -325,7 +374,9 @@ def kp_build_batched(problems) -> list:
     arr = (Problem * len(problems))()
     keep = []
     for i, pr in enumerate(problems):
-        ps = _f64(pr["psf"])
+        ps = _psf2d(pr["psf"])
+        _check_start(pr.get("start"), int(pr["n"]), float(pr["rank_or_tol"]), int(pr.get("method", EGKB)),
+                     int(pr.get("p", 0)))
         keep.append(ps)
         o, k2 = _build_opts(pr.get("p", 0), pr.get("k_min", 0), pr.get("one_sided", False),
                             pr.get("power_iters", 0), pr.get("seed", 0), pr.get("start"),
@@ -339,7 +390,7 @@ def kp_build_batched(problems) -> list:
         arr[i].opts = o
     outs = (C.c_void_p * len(problems))()
     _check("kp_build_batched", lib().kp_build_batched(len(problems), arr, outs))
-    return [KP(outs[i]) for i in range(len(problems))]
+    return [KP(outs[i], int(pr["n"])) for i, pr in enumerate(problems)]
 
 
 def sb_solve_batched(jobs, on_device: bool = False, **opts):
@@ -353,7 +404,7 @@ def sb_solve_batched(jobs, on_device: bool = False, **opts):
         if on_device:
             arr[i].b, arr[i].x = j["b"], j["x"]
         else:
-            bf = _f64(j["b"])
+            bf = _image(j["kp"], j["b"], f"jobs[{i}]['b']")
             xf = np.zeros_like(bf, order="F")
             keep.append(bf)
             outs.append(xf)
@@ -407,8 +458,10 @@ class Server:
 
     def submit(self, psf, n, bc, rank_or_tol, b, mu, lam, tv, iters, *, method=EGKB, beta=0.0,
                prec=P_TF32X2, psf_key=0) -> int:
-        ps = _f64(psf)
+        ps = _psf2d(psf)
         bf = _f64(b)
+        if bf.shape != (int(n), int(n)):
+            raise ValueError(f"b must be an {int(n)} x {int(n)} array (got shape {bf.shape})")
         r = Request()
         r.psf = _pd(ps)
         r.s0, r.s1 = ps.shape
