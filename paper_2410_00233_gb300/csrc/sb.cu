@@ -708,7 +708,6 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
   if (count <= 0 || outer_steps <= 0) return KPSB_OK;
   const int P = count;
   const int n = set[0]->n;
-  const size_t N = (size_t)n * n;
   int kmax = 0;
   for (int p = 0; p < P; ++p) kmax = std::max(kmax, set[p]->kp->k);
   const bool dense = set[0]->kp->A_dense != nullptr;  // a group is all explicit or all KP
