@@ -22,6 +22,15 @@
  *    cudaStream_t passed as void*, NULL = the legacy default stream) unless stated.
  *  - The caller owns every buffer it passes.  A kpsb_kp_t handle owns its device memory
  *    until kp_free().  Handles are not thread-safe: use one per thread or lock.
+ *  - Plain pointers carry no sizes: every host or device buffer must hold at least the
+ *    entries stated for it (the Python binding checks host arrays before the call).
+ *
+ * Environment switches (read once per process; none changes results):
+ *   KPSB_TRACE=1        host phase trace of batched solves on stderr (plan ready, graph
+ *                       instantiated and uploaded, launch, done; per stream)
+ *   KPSB_TUNE_LOG=1     the tensor-core apply autotuner's timings on stderr
+ *   KPSB_TC_VARIANT=v   pin the tensor-core apply variant (0 two-stage, 1 fused 64-column,
+ *                       2 fused 32-column, 3 resident n = 128) instead of autotuning
  */
 #ifndef KPSB_H
 #define KPSB_H
