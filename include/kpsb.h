@@ -25,7 +25,8 @@
  *  - Plain pointers carry no sizes: every host or device buffer must hold at least the
  *    entries stated for it (the Python binding checks host arrays before the call).
  *
- * Environment switches (read once per process; none changes results):
+ * Environment switches (the first two only print; the third picks which kernel computes
+ * the apply, whose results agree with the others' within the TF32 tolerances):
  *   KPSB_TRACE=1        host phase trace of batched solves on stderr (plan ready, graph
  *                       instantiated and uploaded, launch, done; per stream)
  *   KPSB_TUNE_LOG=1     the tensor-core apply autotuner's timings on stderr
