@@ -239,8 +239,9 @@ kpsb_status kp_blur_dev(const double* psf, int s0, int s1, int n, int bc, const 
 
 /* Matrix-free block apply of R(A) (eq. (2.2), R(A) = Kx P^T Ky^T through the index map):
  * U = R(A) V (transpose = 0) or U = R(A)^T V (1).  psf device FP32 s0 x s1; V, U device
- * n^2 x nb FP32 with leading dimension ldv, ldu >= n^2 (must not overlap).  Uses library
- * scratch memory owned per device (allocated on first use).  Async. */
+ * n^2 x nb FP32 with leading dimension ldv, ldu >= n^2 (must not overlap).  Its scratch
+ * (per-tile partial sums, tap weights, counters) is allocated and freed on every call from the
+ * stream-ordered pool (cudaMallocAsync / cudaFreeAsync on `stream`).  Async. */
 kpsb_status kp_ra_apply_dev(const float* psf, int s0, int s1, int n, int bc, const float* V,
                             int ldv, int nb, float* U, int ldu, int transpose, void* stream);
 
@@ -251,10 +252,12 @@ kpsb_status kp_ra_apply_dev(const float* psf, int s0, int s1, int n, int bc, con
  * kp_ra_apply_dev.  Scratch comes from one fixed 4 MiB array in device memory that every
  * device using the library keeps until the process exits; requests needing more
  * (n = 1024 with more than 15 vectors, n = 512 with more than 60) fail with KPSB_EINVAL
- * and a message.  The first call on a device looks up the array's address on that device:
- * make that first call before any stream capture.  All calls share the array and it keeps
- * the last call's contents (the call clears what must start at zero), so calls that
- * overlap on the GPU (different streams, different host threads) race: serialise them. */
+ * and a message.  Every call looks up the array's address on the current device; the first
+ * call on a device also loads the library's device code there, so make that first call
+ * before any stream capture.  `stream` must belong to the current device (KPSB_EINVAL
+ * otherwise).  All calls share the array and it keeps the last call's contents (the call
+ * clears what must start at zero), so calls that overlap on the GPU (different streams,
+ * different host threads) race: serialise them. */
 kpsb_status kp_ra_apply_noalloc_dev(const float* psf, int s0, int s1, int n, int bc,
                                     const float* V, int ldv, int nb, float* U, int ldu,
                                     int transpose, void* stream);
@@ -344,6 +347,16 @@ kpsb_status kpsb_timer_stats(int category, unsigned long long* launches, double*
  * number that differ (0 expected).  Blocking; KPSB_ECUDA on a CUDA error. */
 kpsb_status kpsb_conversion_check(unsigned long long n_random, unsigned long long seed,
                                   unsigned long long* mismatches);
+
+/* Self-test of the bounded device waits behind KPSB_ETIMEOUT (the paper has no counterpart):
+ * one thread waits on an mbarrier that nothing arrives at, through the same bounded-wait
+ * routine as the tensor-core kernels, with a limit of about limit_us microseconds of SM clock
+ * (1 .. 1000000) instead of their one second.  The wait runs out, the kernel records the
+ * error flag as a timed-out GEMM pipeline does and returns, and the call returns KPSB_ETIMEOUT
+ * with the pipeline's time-out message: that is the expected result, and the device stays
+ * usable.  KPSB_OK would mean the wait completed; KPSB_EINVAL for a limit out of range.
+ * Blocking; uses the current device. */
+kpsb_status kpsb_wait_selftest(unsigned int limit_us);
 
 /* Thread-local message for the last error of this thread ("" if none). */
 const char* kpsb_last_error(void);

@@ -101,15 +101,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: about a second of SM clock at most.
-static constexpr long long TC_WAIT_CYCLES = 2000000000LL;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait: gives up after limit_cycles of SM clock (false).
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, uint32_t parity, long long limit_cycles) {
   if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit_cycles) return false;
   }
   return true;
+}
+// The pipelines' waits: about a second of SM clock at most.
+static constexpr long long TC_WAIT_CYCLES = 2000000000LL;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_limit(bar, parity, TC_WAIT_CYCLES);
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
@@ -369,6 +373,19 @@ __device__ int g_tc_error = 0;  // set on a timed-out wait (read by the host aft
 // Work actually performed by the applies of this file: [0] sum of k n^3 over active
 // problems, [1] active problem-applies (one increment per problem per apply).
 __device__ unsigned long long g_tc_work[2] = {0, 0};
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing arrives at, with
+// a short limit; the timed-out wait records the error flag exactly as a GEMM kernel does.
+__global__ void tc_wait_selftest_kernel(long long limit_cycles, int* __restrict__ out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const bool ok = mbar_wait_limit(&bar, 0, limit_cycles);
+    if (!ok) atomicExch(&g_tc_error, 1);
+    *out = ok ? 1 : 0;
+  }
+}
 
 __device__ __forceinline__ void count_apply_work(int k, int n) {
   atomicAdd(&g_tc_work[0], (unsigned long long)k * n * n * n);
@@ -1241,19 +1258,22 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
 }
 
 // ---- variant autotuner ----------------------------------------------------------------------
-// The first plan of each (n, precision, k_max, batch-size bucket, split mode) times every
-// valid variant on its own operands (one warm-up and two timed forward applies, CUDA events
-// on the plan's stream, activity flags ignored) and keeps the fastest for the process.
+// The apply variant is a function of (n, precision) alone, fixed for the process: the first
+// plan of each (n, precision) times every valid variant on a canonical batch that does not
+// depend on the caller's batch (the plan's first problem repeated once per SM: one warm-up
+// and two timed forward applies, CUDA events on the plan's stream, activity flags ignored)
+// and keeps the fastest.  Every later plan of that (n, precision) - a request alone, in a
+// batch of any size, or in a serving round - runs the same kernel, so a problem's bits do
+// not depend on what it is batched with.  The copies of the canonical batch write the same
+// bits to the same buffers, which the plan overwrites before use.
 // KPSB_TC_VARIANT=v forces variant v where valid; KPSB_TUNE_LOG=1 prints the choices.
 struct TuneKey {
-  int n, prec, kmax, pbucket, ext;
-  bool operator<(const TuneKey& o) const {
-    return std::tie(n, prec, kmax, pbucket, ext) < std::tie(o.n, o.prec, o.kmax, o.pbucket, o.ext);
-  }
+  int n, prec;
+  bool operator<(const TuneKey& o) const { return std::tie(n, prec) < std::tie(o.n, o.prec); }
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, int> g_tune;
-static kpsb_status launch_variant(const TCPlan* P, const TCJob* jobs, int variant, cudaStream_t st);
+static kpsb_status launch_variant(const TCPlan* P, const TCJob* jobs, int njobs, int variant, cudaStream_t st);
 
 static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStream_t st) {
   const int n = P->n;
@@ -1266,22 +1286,24 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
   std::vector<int> cand;
   for (int v = 0; v < TCV_COUNT; ++v)
     if (variant_ok(v, n)) cand.push_back(v);
-  if (cand.size() == 1) { P->variant = cand[0]; return KPSB_OK; }
-  int pb = 1;
-  while (pb < P->njobs) pb <<= 1;
-  const TuneKey key{n, P->prec, P->kmax, pb, P->ext_split ? 1 : 0};
+  if (cand.size() == 1 || P->njobs == 0) { P->variant = cand[0]; return KPSB_OK; }
+  const TuneKey key{n, P->prec};
   std::lock_guard<std::mutex> lk(g_tune_mu);  // one tuner at a time; later plans reuse the choice
   auto it = g_tune.find(key);
   if (it != g_tune.end()) { P->variant = it->second; return KPSB_OK; }
-  // operands as planned, without the activity flags (a new problem is not active yet)
-  std::vector<TCJob> tj(hf);
+  int dev = 0, sms = 0;
+  KPSB_TRY_CUDA(cudaGetDevice(&dev));
+  KPSB_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int R = std::max(1, sms);
+  // canonical batch: the first problem, once per SM, without its activity flag
+  std::vector<TCJob> tj((size_t)R, hf[0]);
   for (auto& J : tj) J.active = nullptr;
   TCJob* dj = nullptr;
   unsigned long long saved[2] = {0, 0};
   cudaEvent_t a = nullptr, b = nullptr;
   kpsb_status s = KPSB_OK;
-  cudaError_t e = cudaMallocAsync((void**)&dj, sizeof(TCJob) * P->njobs, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dj, tj.data(), sizeof(TCJob) * P->njobs, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMallocAsync((void**)&dj, sizeof(TCJob) * R, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dj, tj.data(), sizeof(TCJob) * R, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaMemcpyFromSymbol(saved, g_tc_work, sizeof(saved));  // tuning is not work
   if (e == cudaSuccess) e = cudaEventCreate(&a);
@@ -1289,9 +1311,9 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
   int best = cand[0];
   float best_ms = 0.f;
   for (size_t c = 0; c < cand.size() && e == cudaSuccess && s == KPSB_OK; ++c) {
-    s = launch_variant(P, dj, cand[c], st);
+    s = launch_variant(P, dj, R, cand[c], st);
     if (s == KPSB_OK) e = cudaEventRecord(a, st);
-    for (int r = 0; r < 2 && s == KPSB_OK && e == cudaSuccess; ++r) s = launch_variant(P, dj, cand[c], st);
+    for (int r = 0; r < 2 && s == KPSB_OK && e == cudaSuccess; ++r) s = launch_variant(P, dj, R, cand[c], st);
     if (s == KPSB_OK && e == cudaSuccess) e = cudaEventRecord(b, st);
     if (s == KPSB_OK && e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
@@ -1301,8 +1323,8 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
       best_ms = ms;
     }
     if (getenv("KPSB_TUNE_LOG") && e == cudaSuccess)
-      fprintf(stderr, "[kpsb tune] n=%d prec=%d kmax=%d jobs<=%d variant %d: %.3f ms\n", n, P->prec, P->kmax, pb,
-              cand[c], ms / 2);
+      fprintf(stderr, "[kpsb tune] n=%d prec=%d k=%d canonical jobs=%d variant %d: %.3f ms\n", n, P->prec,
+              hf[0].k, R, cand[c], ms / 2);
   }
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_work, saved, sizeof(saved));
   if (a) cudaEventDestroy(a);
@@ -1415,22 +1437,22 @@ static kpsb_status launch_gemm(const TCJob* jobs, int njobs, int n, int kmax, cu
   return KPSB_OK;
 }
 
-static kpsb_status launch_variant(const TCPlan* P, const TCJob* jobs, int variant, cudaStream_t st) {
+static kpsb_status launch_variant(const TCPlan* P, const TCJob* jobs, int njobs, int variant, cudaStream_t st) {
   const int n = P->n;
   const bool x3 = P->prec == KPSB_P_TF32X3;
   switch (variant) {
-    case TCV_RESIDENT: return x3 ? launch_resident<2>(jobs, P->njobs, P->queue, st)
-                                 : launch_resident<1>(jobs, P->njobs, P->queue, st);
-    case TCV_FUSED64: return x3 ? launch_fused<64, 2>(jobs, P->njobs, n, st) : launch_fused<64, 1>(jobs, P->njobs, n, st);
-    case TCV_FUSED32: return x3 ? launch_fused<32, 2>(jobs, P->njobs, n, st) : launch_fused<32, 1>(jobs, P->njobs, n, st);
+    case TCV_RESIDENT: return x3 ? launch_resident<2>(jobs, njobs, P->queue, st)
+                                 : launch_resident<1>(jobs, njobs, P->queue, st);
+    case TCV_FUSED64: return x3 ? launch_fused<64, 2>(jobs, njobs, n, st) : launch_fused<64, 1>(jobs, njobs, n, st);
+    case TCV_FUSED32: return x3 ? launch_fused<32, 2>(jobs, njobs, n, st) : launch_fused<32, 1>(jobs, njobs, n, st);
     default: break;
   }
   if (x3) {
-    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 2>(jobs, P->njobs, n, P->kmax, st)));
-    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 2>(jobs, P->njobs, n, P->kmax, st)));
+    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 2>(jobs, njobs, n, P->kmax, st)));
+    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 2>(jobs, njobs, n, P->kmax, st)));
   } else {
-    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 1>(jobs, P->njobs, n, P->kmax, st)));
-    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 1>(jobs, P->njobs, n, P->kmax, st)));
+    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 1>(jobs, njobs, n, P->kmax, st)));
+    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 1>(jobs, njobs, n, P->kmax, st)));
   }
   return KPSB_OK;
 }
@@ -1443,7 +1465,7 @@ kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
     tc_split_kernel<<<gs, 256, 0, st>>>(jobs);
     KPSB_CHECK_LAUNCH();
   }
-  return launch_variant(P, jobs, P->variant, st);
+  return launch_variant(P, jobs, P->njobs, P->variant, st);
 }
 
 kpsb_status tc_work(unsigned long long* out, bool reset) {
@@ -1488,3 +1510,32 @@ kpsb_status tc_apply_batch(kpsb_kp** kps, const KPJob* jobs_d, const KPJob* jobs
 }
 
 }  // namespace kpsb
+
+using namespace kpsb;
+
+extern "C" kpsb_status kpsb_wait_selftest(unsigned int limit_us) {
+  clear_error();
+  KPSB_REQUIRE(limit_us >= 1 && limit_us <= 1000000u, "limit_us must be in [1, 1000000] (got %u)", limit_us);
+  int dev = 0, khz = 0;
+  KPSB_TRY_CUDA(cudaGetDevice(&dev));
+  KPSB_TRY_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+  if (khz <= 0) khz = 2000000;
+  int* d = nullptr;
+  KPSB_TRY_CUDA(cudaMalloc((void**)&d, sizeof(int)));
+  tc_wait_selftest_kernel<<<1, 32>>>((long long)limit_us * (khz / 1000), d);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  int h = -1;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    set_error("kpsb_wait_selftest: %s", cudaGetErrorString(e));
+    return KPSB_ECUDA;
+  }
+  kpsb_status s = tc_check_error();  // KPSB_ETIMEOUT once the wait has run out
+  if (s == KPSB_OK && h != 1) {
+    set_error("kpsb_wait_selftest: the wait neither completed nor recorded a time-out");
+    return KPSB_ECUDA;
+  }
+  return s;
+}

@@ -9,8 +9,6 @@
 // start-up, or runs under a strict memory budget, has no allocator to spare for a
 // library.  Those callers pass their own inputs and outputs, and the scratch comes from
 // here.
-#include <mutex>
-
 #include "kpsb_internal.cuh"
 
 namespace kpsb {
@@ -19,29 +17,30 @@ namespace kpsb {
 static constexpr size_t NOALLOC_SCRATCH_BYTES = 4u << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-static constexpr int NOALLOC_MAX_DEVICES = 64;
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
-
-// Device address of the scratch array on the current device, looked up once per device.
-// In host code g_noalloc_scratch names a host-side shadow, not device memory, so only the
-// address returned by cudaGetSymbolAddress may be handed to a kernel.
-static kpsb_status noalloc_scratch(void** out) {
+// Device address of the scratch array on the device that owns `st`.  In host code
+// g_noalloc_scratch names a host-side shadow, not device memory, so only the address that
+// cudaGetSymbolAddress returns may be handed to a kernel.  The address is looked up on every
+// call (a table lookup once the module is loaded), so it follows the current context even
+// after a cudaDeviceReset.  The first lookup on a device loads the module there, which is
+// why the first call belongs before any stream capture.
+static kpsb_status noalloc_scratch(cudaStream_t st, void** out) {
   int dev = 0;
   KPSB_TRY_CUDA(cudaGetDevice(&dev));
-  KPSB_REQUIRE(dev >= 0 && dev < NOALLOC_MAX_DEVICES, "device ordinal %d not supported", dev);
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error("cudaGetSymbolAddress of the scratch array failed on device %d: %s", dev,
-                cudaGetErrorString(e));
-      return KPSB_ECUDA;
-    }
-    g_noalloc_ptr[dev] = p;
+  if (st) {
+    int sdev = -1;
+    KPSB_TRY_CUDA(cudaStreamGetDevice(st, &sdev));
+    KPSB_REQUIRE(sdev == dev,
+                 "kp_ra_apply_noalloc_dev: the stream belongs to device %d but device %d is current",
+                 sdev, dev);
   }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error("cudaGetSymbolAddress of the scratch array failed on device %d: %s", dev,
+              cudaGetErrorString(e));
+    return KPSB_ECUDA;
+  }
+  *out = p;
   return KPSB_OK;
 }
 
@@ -63,9 +62,9 @@ extern "C" kpsb_status kp_ra_apply_noalloc_dev(const float* psf, int s0, int s1,
                "kp_ra_apply_noalloc_dev: n=%d, nb=%d, s=%d needs %zu bytes of scratch, more than "
                "the fixed %zu (use fewer vectors per call, or kp_ra_apply_dev)",
                n, nb, s_exp, need, (size_t)NOALLOC_SCRATCH_BYTES);
-  void* base = nullptr;
-  KPSB_TRY(noalloc_scratch(&base));
   cudaStream_t st = (cudaStream_t)stream;
+  void* base = nullptr;
+  KPSB_TRY(noalloc_scratch(st, &base));
   RAScratch scr = ra_scratch_carve(base, n, nb, s_exp);
   // the array keeps the previous call's contents: the counters must start at zero
   KPSB_TRY_CUDA(cudaMemsetAsync(scr.counters, 0, sizeof(unsigned int) * nb, st));

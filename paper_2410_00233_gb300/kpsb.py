@@ -122,6 +122,7 @@ _SIGS = {
     "kpsb_timer_stats": (C.c_int, [C.c_int, C.POINTER(C.c_ulonglong), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "kpsb_apply_counts": (C.c_int, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
     "kpsb_conversion_check": (C.c_int, [C.c_ulonglong, C.c_ulonglong, C.POINTER(C.c_ulonglong)]),
+    "kpsb_wait_selftest": (C.c_int, [C.c_uint]),
 }
 
 
@@ -554,3 +555,9 @@ def kpsb_small_svd(A):
     sw = C.c_int()
     _check("kpsb_small_svd", lib().kpsb_small_svd(m, nc, _pd(Af), _pd(U), _pd(S), _pd(V), C.byref(sw)))
     return U, S, V, sw.value
+
+
+def kpsb_wait_selftest(limit_us: int = 50):
+    """Runs the bounded-wait self-test; raises KpsbError (code -4, ETIMEOUT) when the wait ran
+    out as designed."""
+    _check("kpsb_wait_selftest", lib().kpsb_wait_selftest(int(limit_us)))

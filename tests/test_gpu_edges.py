@@ -109,3 +109,30 @@ def test_largest_size_build_and_tensor_core_apply():
         ref_y = O.kp_apply_t(op, X) if t else O.kp_apply(op, X)
         y = K.kp_apply(kp2, X, t, K.P_TF32X3)
         assert np.linalg.norm(y - ref_y) <= 1e-4 * np.linalg.norm(ref_y), t
+
+
+def test_bounded_wait_times_out_and_the_device_stays_usable():
+    """The tensor-core pipelines bound every mbarrier wait; a wait that runs out records an
+    error flag that the host maps to KPSB_ETIMEOUT.  The self-test drives that branch with a
+    wait on an mbarrier nothing arrives at (a limit of microseconds, not the pipelines' one
+    second); afterwards the flag is clear and an apply on the same device is still exact."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    for limit_us in (20, 200):
+        with pytest.raises(K.KpsbError) as e:
+            K.kpsb_wait_selftest(limit_us)
+        assert e.value.code == -4 and "timed out" in str(e.value)
+    with pytest.raises(K.KpsbError) as e:
+        K.kpsb_wait_selftest(0)
+    assert e.value.code == -1
+    n, k = 128, 3
+    g = I.rng(17)
+    Ax = g.standard_normal((k, n, n)).astype(np.float32)
+    Ay = g.standard_normal((k, n, n)).astype(np.float32)
+    sig = np.array([2.0, 1.0, 0.5])
+    kp = K.kp_from_factors(Ax, Ay, sig)
+    X = g.standard_normal((n, n))
+    ref = O.kp_apply(O.KPSum(Ax=Ax.astype(np.float64), Ay=Ay.astype(np.float64), sigma=sig), X)
+    y = K.kp_apply(kp, X, 0, K.P_TF32X3)
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-4

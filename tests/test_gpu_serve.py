@@ -83,3 +83,47 @@ def test_server_refuses_what_never_fits_and_admits_within_budget():
     assert st["completed"] == 6 and st["peak_bytes"] <= 6 << 20
     for x, _, _ in res[1:]:
         assert np.array_equal(x, res[0][0])
+
+
+@pytest.mark.parametrize("n,P", [(128, 200), (256, 40)])
+def test_same_bits_alone_in_a_large_batch_and_served(n, P):
+    """One request solved three ways gives the same bits: alone, inside a batch of P other
+    problems (cut into concurrent parts), and in a server round with other requests.  The
+    tensor-core apply variant is fixed per (n, precision) for the process, whatever the batch
+    that first needed it, and every kernel treats a problem on its own with fixed-order
+    reductions.  The batch runs first, so the variant is chosen on it, not on the lone solve."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    g = I.rng(4242 + n)
+    jobs = []
+    for p in range(P):
+        k = 3 + p % 9
+        kp = K.kp_from_factors((g.standard_normal((k, n, n)) / n).astype(np.float32),
+                               (g.standard_normal((k, n, n)) / n).astype(np.float32),
+                               np.sort(g.random(k))[::-1] + 0.1)
+        jobs.append(dict(kp=kp, b=g.standard_normal((n, n)), mu=1.0, lam=0.1,
+                         tv=K.ISO if p % 2 else K.ANISO, iters=2))
+    outs, stats = K.sb_solve_batched(jobs, prec=K.P_TF32X2)
+    psf, b = _request(31, n)
+    kp_t = K.kp_build(psf, n, K.BC_REFLEXIVE, 6, K.EGKB, seed=777)
+    x_alone, st_alone = K.sb_solve(kp_t, b, 1.0, 0.1, K.ISO, 2, prec=K.P_TF32X2)
+    # the same request inside a batch with the P others
+    outs2, stats2 = K.sb_solve_batched(jobs[:P // 2] + [dict(kp=kp_t, b=b, mu=1.0, lam=0.1, tv=K.ISO, iters=2)]
+                                       + jobs[P // 2:], prec=K.P_TF32X2)
+    assert np.array_equal(outs2[P // 2], x_alone) and stats2[P // 2].iota_total == st_alone.iota_total
+    for a, c in zip(outs[:3] + outs[-3:], outs2[:3] + outs2[-3:]):
+        assert np.array_equal(a, c)
+    # and served, with other requests in the same rounds
+    srv = K.Server(budget_bytes=8 << 30, max_active=16, round_steps=1)
+    ids = []
+    for i in range(6):
+        psf_i, b_i = _request(40 + i, n)
+        ids.append(srv.submit(psf_i, n, K.BC_REFLEXIVE, 6, b_i, 1.0, 0.1, K.ANISO, 2, prec=K.P_TF32X2,
+                              psf_key=500 + i))
+    tid = srv.submit(psf, n, K.BC_REFLEXIVE, 6, b, 1.0, 0.1, K.ISO, 2, prec=K.P_TF32X2, psf_key=777)
+    x_srv, st_srv, _ = srv.poll(tid, timeout_us=60_000_000)
+    for i in ids:
+        srv.poll(i, timeout_us=60_000_000)
+    srv.close()
+    assert np.array_equal(x_srv, x_alone) and st_srv.iota_total == st_alone.iota_total
