@@ -60,8 +60,9 @@ typedef enum {
 enum { KPSB_BC_ZERO = 0, KPSB_BC_REFLEXIVE = 1 };
 enum { KPSB_EGKB = 0, KPSB_RSVD = 1 };
 enum { KPSB_ANISO = 0, KPSB_ISO = 1 };
-/* Arithmetic of the Kronecker-sum GEMMs inside sb_solve / kp_apply.  Vectors, stopping
- * tests and shrinkage are FP64 in every mode.
+/* Arithmetic of the Kronecker-sum GEMMs inside sb_solve / kp_apply (Sec. 4.2; the paper's
+ * single precision, Sec. 4.4, carried to the tensor cores with split-precision recovery).
+ * Vectors, stopping tests and shrinkage are FP64 in every mode.
  *  FP64  : FP64 FMA of the FP32 factors (exact in FP64) with FP64 images.
  *  FP32  : FP32 FMA, images rounded to FP32, FP32 accumulation.
  *  TF32X3: tensor cores (tcgen05 kind::tf32), each operand split into two TF32 parts,
@@ -70,9 +71,17 @@ enum { KPSB_ANISO = 0, KPSB_ISO = 1 };
  *          operator in the forward and transpose applies, so the adjoint stays exact; the
  *          change of A_k is ~5e-4 relative, far below the KP truncation error) and the
  *          image is split into two TF32 parts: two products, half the factor traffic.
- *  The tensor-core modes run where the kernel tiles the image (n a multiple of 128);
- *  other sizes run the FP32 CUDA-core GEMM. */
-enum { KPSB_P_FP64 = 0, KPSB_P_FP32 = 1, KPSB_P_TF32X3 = 2, KPSB_P_TF32X2 = 3 };
+ *  BF16X3: tensor cores (tcgen05 kind::f16, BF16 operands, FP32 accumulation); each
+ *          operand split into two BF16 parts (16 significant bits), three products
+ *          (hi*hi + hi*lo + lo*hi): ~1e-5 relative per product, 1.5 TF32-product times
+ *          of tensor work, 2-byte planes.
+ *  BF16X2: tensor cores; the factors rounded once to BF16 (~4e-3 relative change of A_k,
+ *          the same rounded operator in both directions), the image split into two BF16
+ *          parts: two BF16 products, the smallest factor traffic.
+ *  The tensor-core modes run for n >= 64 (image sides that are not a multiple of the
+ *  128-row tile are masked); smaller sizes run the FP32 CUDA-core GEMM. */
+enum { KPSB_P_FP64 = 0, KPSB_P_FP32 = 1, KPSB_P_TF32X3 = 2, KPSB_P_TF32X2 = 3, KPSB_P_BF16X3 = 4,
+       KPSB_P_BF16X2 = 5 };
 /* Shrinkage threshold of the d-subproblem argmin lambda^2||d-c||^2 + beta||d||_1
  * (Sec. 3.2-3.3): EXACT = beta/(2 lambda^2) (its exact minimiser), PAPER = beta/lambda^2
  * (the printed 1/gamma, which minimises with 2*beta). */

@@ -194,7 +194,7 @@ extern "C" kpsb_status kp_apply_dev(kpsb_kp_t kp, const double* X, double* Y, in
                                     void* stream) {
   clear_error();
   KPSB_REQUIRE(kp && X && Y && X != Y, "null or aliased pointer");
-  KPSB_REQUIRE(prec >= KPSB_P_FP64 && prec <= KPSB_P_TF32X2, "unknown precision %d", prec);
+  KPSB_REQUIRE(prec_valid(prec), "unknown precision %d", prec);
   cudaStream_t st = (cudaStream_t)stream;
   const int n = kp->n, k = kp->k;
   if (kp->A_dense) {  // explicit operator: FP64 products
@@ -220,7 +220,7 @@ extern "C" kpsb_status kp_apply_dev(kpsb_kp_t kp, const double* X, double* Y, in
     return s;
   }
   const bool tc = tc_supported(kp->n, prec);
-  if ((prec == KPSB_P_TF32X3 || prec == KPSB_P_TF32X2) && !tc) prec = KPSB_P_FP32;  // untiled sizes
+  if (prec_is_tc(prec) && !tc) prec = KPSB_P_FP32;  // sizes below the tensor-core tiles
   size_t zb = tc ? 0 : kp_z_bytes(n, k, prec);
   char* buf = nullptr;
   KPSB_TRY_CUDA(cudaMallocAsync((void**)&buf, zb + 256, st));

@@ -14,6 +14,13 @@
 // Both stages are "C = A B^T" with both operands K-major (rows contiguous in K), which is
 // the canonical tcgen05 operand form; the tables T1, T2 are built once per handle.
 //
+// BF16 modes (BF16X3, BF16X2) run the same two-stage kernel with BF16 planes (2 bytes, a
+// 128-byte row holds 64 K values) and tcgen05.mma kind::f16 (K = 16 per instruction); the
+// split is a_hi = bf16(a), a_lo = bf16(a - a_hi).  Image sides that are not a multiple of
+// the tiles are handled by TMA's zero fill beyond the tensor extents (every leading
+// dimension is padded to a multiple of 8 elements so the strides stay 16-byte multiples) and
+// by masked epilogue stores.
+//
 // Kernel anatomy (128 threads, one 128 x BN output tile per CTA): warp 0 allocates BN TMEM
 // columns; lane 0 of warp 0 issues TMA loads of 32-wide K slices (128-byte swizzle) into a
 // ring of shared-memory stages; lane 0 of warp 1 issues tcgen05.mma (kind::tf32, M = 128,
@@ -21,12 +28,14 @@
 // warps read their 32 TMEM lanes with tcgen05.ld and run the epilogue.  Every wait is
 // bounded: on timeout the CTA records an error code, drains and frees TMEM, and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <stdio.h>
 #include <stdlib.h>
 
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "kpsb_internal.cuh"
 
@@ -54,14 +63,16 @@ static PFN_encodeTiled_t encode_fn() {
   return fn;
 }
 
-// Row-major FP32 planes: dims (innermost first) {K, rows, planes[, terms]}, box {32, box_rows}.
-static kpsb_status make_map(CUtensorMap* m, const float* base, int rank, const cuuint64_t* dims,
-                            const cuuint64_t* strides_bytes, int box_rows) {
+// Row-major planes: dims (innermost first) {K, rows, planes[, terms]}, box {128 bytes of K,
+// box_rows}: 32 FP32 (TF32) values or 64 BF16 values.
+static kpsb_status make_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims,
+                            const cuuint64_t* strides_bytes, int box_rows, bool bf16 = false) {
   PFN_encodeTiled_t enc = encode_fn();
   KPSB_REQUIRE(enc, "cuTensorMapEncodeTiled unavailable");
-  cuuint32_t box[4] = {32, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t box[4] = {bf16 ? 64u : 32u, (cuuint32_t)box_rows, 1, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, (void*)base, dims,
+  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   (cuuint32_t)rank, (void*)base, dims,
                    strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -151,6 +162,20 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor: kind::f16 with BF16 A and B, D = F32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accum) {
   asm volatile(
@@ -227,6 +252,18 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
+// Two-part split of an FP32 value into the plane element type E: float planes hold TF32
+// values (hi = tf32(v), lo = tf32(v - hi)); BF16 planes hold hi = bf16(v), lo = bf16(v - hi)
+// (round to nearest even).
+__device__ __forceinline__ void split2(float v, float& h, float& l) {
+  h = tf32_round(v);
+  l = tf32_round(v - h);
+}
+__device__ __forceinline__ void split2(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  l = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
 // ------------------------------------------------------------------------------------------
 // Jobs
 // ------------------------------------------------------------------------------------------
@@ -240,40 +277,63 @@ struct alignas(128) TCJob {
   CUtensorMap m2B;   // Zt planes: {k n, n, 2}
   const double* X;   // input image (n x n FP64, column-major)
   double* Y;         // output image
-  float* Xt;         // [2][n][n]
-  float* Zt;         // [2][n][ldz]
-  int n, k, ldz;
+  void* Xt;          // [2][n][ldx] (float TF32 values or BF16)
+  void* Zt;          // [2][n][ldz]
+  int n, k, ldz, ldx;
   const int* active;
   float* Yf;         // when set (fused kernel): FP32 output instead of Y
 };
 
-// Tensor-core tables of one handle: [k][2][n][n] for stage 1, [2][n][k n] for stage 2,
-// forward and transpose.
+// Leading dimensions of the planes: K extents padded to 8 elements, so every TMA stride is a
+// multiple of 16 bytes for FP32 and BF16 planes alike.
+static inline int pad8(long long x) { return (int)((x + 7) / 8 * 8); }
+static inline bool prec_bf16(int prec) { return prec == KPSB_P_BF16X3 || prec == KPSB_P_BF16X2; }
+// planes of the factor operand: 2 (split factors, three products) or 1 (rounded once)
+static inline int prec_fpl(int prec) { return (prec == KPSB_P_TF32X3 || prec == KPSB_P_BF16X3) ? 2 : 1; }
+
+// Tensor-core tables of one handle: [k][2][n][ld1] for stage 1, [2][n][ld2] for stage 2,
+// forward and transpose; TF32 values in FP32 storage and, when a BF16 mode is used, BF16.
 struct TCTables {
   float* T1f = nullptr;
   float* T1t = nullptr;
   float* T2f = nullptr;
   float* T2t = nullptr;
-  int n = 0, k = 0;
+  __nv_bfloat16* B1f = nullptr;
+  __nv_bfloat16* B1t = nullptr;
+  __nv_bfloat16* B2f = nullptr;
+  __nv_bfloat16* B2t = nullptr;
+  int n = 0, k = 0, ld1 = 0, ld2 = 0;
 };
 
 void tc_free(TCTables* t) {
   if (!t) return;
   if (t->T1f) cudaFree(t->T1f);
+  if (t->B1f) cudaFree(t->B1f);
   delete t;
 }
 
-// Full 128-row tiles in both stages (M = 128, BN | 128, K slices of 32).
-bool tc_supported(int n, int prec) {
-  return (prec == KPSB_P_TF32X3 || prec == KPSB_P_TF32X2) && n >= 128 && n % 128 == 0;
+// The two-stage kernel masks partial tiles, so any n >= 64 runs on the tensor cores; the
+// fused and resident kernels need n a multiple of 128 (TF32 modes).
+bool tc_supported(int n, int prec) { return prec_is_tc(prec) && n >= 64; }
+
+size_t tc_table_bytes(int n, int k, int prec) {
+  const size_t per = (size_t)2 * k * n * pad8(n) + (size_t)2 * n * pad8((long long)k * n);
+  return per * 2 * (prec_bf16(prec) ? sizeof(__nv_bfloat16) : sizeof(float));
+}
+
+size_t tc_plan_ws_bytes(int n, int k, int prec) {
+  const size_t es = prec_bf16(prec) ? sizeof(__nv_bfloat16) : sizeof(float);
+  return es * ((size_t)2 * n * pad8(n) + (size_t)2 * n * pad8((long long)k * n)) + 1024;
 }
 
 // ---- table build ---------------------------------------------------------------------------
+template <typename E>
 __global__ void tc_tables_kernel(const float* __restrict__ Ax, const float* __restrict__ Ay,
-                                 const double* __restrict__ sigma, int n, int k, float* T1f,
-                                 float* T1t, float* T2f, float* T2t) {
+                                 const double* __restrict__ sigma, int n, int k, int ld1, int ld2, E* T1f,
+                                 E* T1t, E* T2f, E* T2t) {
   const long long nn = (long long)n * n;
   const long long total = nn * k;
+  const size_t pl1 = (size_t)n * ld1, pl2 = (size_t)n * ld2;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     int i = (int)(e / nn);
@@ -285,84 +345,119 @@ __global__ void tc_tables_kernel(const float* __restrict__ Ax, const float* __re
     // stage 1 tables: T1_i[c][m]
     float f = sg * ax[row + (size_t)col * n];   // forward: sigma Ax_i(c = row, m = col)
     float t = sg * ax[col + (size_t)row * n];   // transpose: sigma Ax_i(m = col, c = row)
-    size_t o1 = ((size_t)i * 2) * nn + (size_t)row * n + col;
-    float h = tf32_round(f);
+    size_t o1 = (size_t)i * 2 * pl1 + (size_t)row * ld1 + col;
+    E h, l;
+    split2(f, h, l);
     T1f[o1] = h;
-    T1f[o1 + nn] = tf32_round(f - h);
-    h = tf32_round(t);
+    T1f[o1 + pl1] = l;
+    split2(t, h, l);
     T1t[o1] = h;
-    T1t[o1 + nn] = tf32_round(t - h);
+    T1t[o1 + pl1] = l;
     // stage 2 tables: T2[a][i n + r], a = row, r = col
     float f2 = ay[row + (size_t)col * n];       // forward: Ay_i(a, r)
     float t2 = ay[col + (size_t)row * n];       // transpose: Ay_i(r, a)
-    size_t plane = (size_t)n * k * n;
-    size_t o2 = (size_t)row * k * n + (size_t)i * n + col;
-    h = tf32_round(f2);
+    size_t o2 = (size_t)row * ld2 + (size_t)i * n + col;
+    split2(f2, h, l);
     T2f[o2] = h;
-    T2f[o2 + plane] = tf32_round(f2 - h);
-    h = tf32_round(t2);
+    T2f[o2 + pl2] = l;
+    split2(t2, h, l);
     T2t[o2] = h;
-    T2t[o2 + plane] = tf32_round(t2 - h);
+    T2t[o2 + pl2] = l;
   }
 }
 
-static kpsb_status tc_tables(kpsb_kp* kp, cudaStream_t st, TCTables** out) {
+static kpsb_status tc_tables(kpsb_kp* kp, cudaStream_t st, bool bf, TCTables** out) {
   std::lock_guard<std::mutex> lk(kp->mu);
   if (!kp->tc) {
-    const size_t per = (size_t)2 * kp->k * kp->n * kp->n;  // floats per table
     TCTables* t = new TCTables();
     t->n = kp->n;
     t->k = kp->k;
-    cudaError_t e = cudaMalloc((void**)&t->T1f, sizeof(float) * per * 4);
+    t->ld1 = pad8(kp->n);
+    t->ld2 = pad8((long long)kp->k * kp->n);
+    kp->tc = t;
+  }
+  TCTables* t = kp->tc;
+  const int n = t->n, k = t->k;
+  const size_t per1 = (size_t)2 * k * n * t->ld1, per2 = (size_t)2 * n * t->ld2;  // elements per table
+  const long long total = (long long)k * n * n;
+  const int nb = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+  cudaError_t e = cudaSuccess;
+  if (!bf && !t->T1f) {
+    float* b = nullptr;
+    e = cudaMalloc((void**)&b, sizeof(float) * 2 * (per1 + per2));
     if (e != cudaSuccess) {
-      delete t;
-      set_error("tensor-core tables (%zu bytes): %s", sizeof(float) * per * 4, cudaGetErrorString(e));
+      set_error("tensor-core tables (%zu bytes): %s", sizeof(float) * 2 * (per1 + per2), cudaGetErrorString(e));
       return KPSB_ENOMEM;
     }
-    t->T1t = t->T1f + per;
-    t->T2f = t->T1t + per;
-    t->T2t = t->T2f + per;
-    long long total = (long long)kp->k * kp->n * kp->n;
-    int nb = (int)std::min<long long>((total + 255) / 256, 152 * 8);
-    tc_tables_kernel<<<nb, 256, 0, st>>>(kp->Ax, kp->Ay, kp->sigma_d, kp->n, kp->k, t->T1f, t->T1t,
-                                         t->T2f, t->T2t);
+    tc_tables_kernel<float><<<nb, 256, 0, st>>>(kp->Ax, kp->Ay, kp->sigma_d, n, k, t->ld1, t->ld2, b, b + per1,
+                                                b + 2 * per1, b + 2 * per1 + per2);
     count_launch();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
-      tc_free(t);
+      cudaFree(b);
       set_error("tensor-core tables: %s", cudaGetErrorString(e));
       return KPSB_ECUDA;
     }
-    kp->tc = t;
+    t->T1f = b;
+    t->T1t = b + per1;
+    t->T2f = b + 2 * per1;
+    t->T2t = b + 2 * per1 + per2;
   }
-  *out = kp->tc;
+  if (bf && !t->B1f) {
+    __nv_bfloat16* b = nullptr;
+    e = cudaMalloc((void**)&b, sizeof(__nv_bfloat16) * 2 * (per1 + per2));
+    if (e != cudaSuccess) {
+      set_error("BF16 tables (%zu bytes): %s", sizeof(__nv_bfloat16) * 2 * (per1 + per2), cudaGetErrorString(e));
+      return KPSB_ENOMEM;
+    }
+    tc_tables_kernel<__nv_bfloat16><<<nb, 256, 0, st>>>(kp->Ax, kp->Ay, kp->sigma_d, n, k, t->ld1, t->ld2, b,
+                                                        b + per1, b + 2 * per1, b + 2 * per1 + per2);
+    count_launch();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cudaFree(b);
+      set_error("BF16 tables: %s", cudaGetErrorString(e));
+      return KPSB_ECUDA;
+    }
+    t->B1f = b;
+    t->B1t = b + per1;
+    t->B2f = b + 2 * per1;
+    t->B2t = b + 2 * per1 + per2;
+  }
+  *out = t;
   return KPSB_OK;
 }
 
 // ---- split + transpose of the input image -----------------------------------------------------
-// Xt[r][m] = X(r, m) as hi/lo TF32 planes.  grid = (tiles of 32x32, problems).
+// Xt[r][m] = X(r, m) as hi/lo planes of E (row-major, leading dimension ldx), any n.
+// grid = (32 x 32 tiles, problems).
+template <typename E>
 __global__ void tc_split_kernel(const TCJob* __restrict__ jobs) {
   const TCJob& J = jobs[blockIdx.y];
   if (J.active && !*J.active) return;
   const int n = J.n;
-  const int tiles = n / 32;
+  const int tiles = (n + 31) / 32;
   const int tr = blockIdx.x % tiles, tm = blockIdx.x / tiles;
   if (tm >= tiles) return;
   __shared__ float t[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   for (int j = ty; j < 32; j += 8) {
     int r = tr * 32 + tx, m = tm * 32 + j;
-    t[j][tx] = (float)J.X[r + (size_t)m * n];  // coalesced along r
+    t[j][tx] = (r < n && m < n) ? (float)J.X[r + (size_t)m * n] : 0.f;  // coalesced along r
   }
   __syncthreads();
-  const size_t nn = (size_t)n * n;
+  E* xt = (E*)J.Xt;
+  const size_t plane = (size_t)n * J.ldx;
   for (int j = ty; j < 32; j += 8) {
     int r = tr * 32 + j, m = tm * 32 + tx;
-    float v = t[tx][j];
-    float h = tf32_round(v);
-    J.Xt[(size_t)r * n + m] = h;  // coalesced along m
-    J.Xt[nn + (size_t)r * n + m] = tf32_round(v - h);
+    if (r < n && m < n) {
+      E h, l;
+      split2(t[tx][j], h, l);
+      xt[(size_t)r * J.ldx + m] = h;  // coalesced along m
+      xt[plane + (size_t)r * J.ldx + m] = l;
+    }
   }
 }
 
@@ -394,9 +489,10 @@ __device__ __forceinline__ void count_apply_work(int k, int n) {
 
 // FPL = planes of the factor operand (2: split factors, three products per K slice;
 // 1: factors rounded once to TF32, two products).  The iterate operand always has two.
-template <int BN, int STAGES, int STAGE, int FPL>
+template <int BN, int STAGES, int STAGE, int FPL, bool BF = false>
 struct TCCfg {
-  static constexpr int A_BYTES = 128 * 128;  // 128 rows x 32 fp32
+  static constexpr int KS = BF ? 64 : 32;     // K values in one 128-byte row
+  static constexpr int A_BYTES = 128 * 128;  // 128 rows x 128 bytes
   static constexpr int B_BYTES = BN * 128;
   static constexpr int A_PLANES = STAGE == 1 ? 2 : FPL;  // stage 1: A = iterate, stage 2: A = factors
   static constexpr int B_PLANES = STAGE == 1 ? FPL : 2;
@@ -405,9 +501,10 @@ struct TCCfg {
   static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
 };
 
-template <int BN, int STAGES, int STAGE, int FPL>
+template <int BN, int STAGES, int STAGE, int FPL, bool BF>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict__ jobs, int tiles_m) {
-  using C = TCCfg<BN, STAGES, STAGE, FPL>;
+  using C = TCCfg<BN, STAGES, STAGE, FPL, BF>;
+  using E = typename std::conditional<BF, __nv_bfloat16, float>::type;
   const TCJob& J = jobs[blockIdx.z];
   const int term = STAGE == 1 ? (int)blockIdx.y : 0;
   if (term >= J.k) return;
@@ -417,8 +514,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
   const int m0 = (blockIdx.x % tiles_m) * 128;
   const int c0 = (blockIdx.x / tiles_m) * BN;
   if (m0 >= n || c0 >= n) return;
-  const int KT = STAGE == 1 ? n : J.k * n;  // K extent
-  const int nkb = KT / 32;
+  const int KT = STAGE == 1 ? n : J.k * n;  // K extent (zero-filled past it)
+  const int nkb = (KT + C::KS - 1) / C::KS;
 
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -466,7 +563,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
       }
       unsigned char* st = smem + s * C::STAGE_BYTES;
       mbar_expect_tx(&full[s], C::STAGE_BYTES);
-      const int kx = kb * 32;
+      const int kx = kb * C::KS;
       unsigned char* sb = st + C::A_PLANES * C::A_BYTES;
       if (STAGE == 1) {
         tma_load_3d(st, &J.m1A, &full[s], kx, m0, 0);
@@ -482,7 +579,11 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
-    constexpr uint32_t idesc = idesc_tf32(128, BN);
+    constexpr uint32_t idesc = BF ? idesc_bf16(128, BN) : idesc_tf32(128, BN);
+    auto mma = [&](uint64_t a, uint64_t b, uint32_t acc) {
+      if (BF) mma_bf16(tmem, a, b, idesc, acc);
+      else mma_tf32(tmem, a, b, idesc, acc);
+    };
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES, round = kb / STAGES;
@@ -497,15 +598,13 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
       const uint32_t b_hi = sa + C::A_PLANES * C::A_BYTES;
       const uint32_t b_lo = b_hi + (C::B_PLANES == 2 ? C::B_BYTES : 0);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {  // four K = 8 slices of 32 bytes in the 128-byte row
+      for (int kk = 0; kk < 4; ++kk) {  // four 32-byte K steps (8 TF32 / 16 BF16) per row
         const uint32_t off = kk * 32;
         const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
         // small cross terms first, the hi x hi product last
-        if (C::A_PLANES == 2) mma_tf32(tmem, sdesc_sw128(a_lo + off), sdesc_sw128(b_hi + off), idesc, acc0);
-        if (C::B_PLANES == 2)
-          mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_lo + off), idesc,
-                   C::A_PLANES == 2 ? 1u : acc0);
-        mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), idesc, 1u);
+        if (C::A_PLANES == 2) mma(sdesc_sw128(a_lo + off), sdesc_sw128(b_hi + off), acc0);
+        if (C::B_PLANES == 2) mma(sdesc_sw128(a_hi + off), sdesc_sw128(b_lo + off), C::A_PLANES == 2 ? 1u : acc0);
+        mma(sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), 1u);
       }
       mma_commit(&empty[s]);  // stage s free once these MMAs have read it
     }
@@ -528,14 +627,16 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
         if (STAGE == 1) {
           // D1[r][c] = Z_term(r, c) -> Zt[c][term n + r], hi/lo planes
           const size_t plane = (size_t)n * J.ldz;
+          E* zt = (E*)J.Zt;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int c = c0 + cc + j;
             if (c < n) {
-              float h = tf32_round(v[j]);
+              E h, l;
+              split2(v[j], h, l);
               size_t o = (size_t)c * J.ldz + (size_t)term * n + row;
-              J.Zt[o] = h;
-              J.Zt[plane + o] = tf32_round(v[j] - h);
+              zt[o] = h;
+              zt[plane + o] = l;
             }
           }
         } else {
@@ -1135,9 +1236,10 @@ enum { TCV_TWO_STAGE = 0, TCV_FUSED64 = 1, TCV_FUSED32 = 2, TCV_RESIDENT = 3, TC
 struct TCPlan {
   TCJob* d_fwd = nullptr;
   TCJob* d_bwd = nullptr;
-  float* work = nullptr;  // Xt and Zt of every problem
+  char* work = nullptr;   // Xt and Zt of every problem
   int njobs = 0, n = 0, kmax = 0;
   int prec = KPSB_P_TF32X3;
+  bool bf = false;         // BF16 planes (BF16X3 / BF16X2)
   bool fused = false;      // single-launch apply (the variant is not the two-stage pair)
   int variant = 0;         // TCV_* chosen for this plan (autotuned, section below)
   bool ext_split = false;  // the caller writes the split planes (xt_ext)
@@ -1186,13 +1288,16 @@ static kpsb_status launch_resident(const TCJob* jobs, int njobs, int* queue, cud
   return KPSB_OK;
 }
 
-// n = 128 runs the resident kernel (KPSB_FUSED_TILED=1 selects the tiled fused kernel).
-static bool variant_ok(int v, int n) {
+// n = 128 runs the resident kernel (KPSB_FUSED_TILED=1 selects the tiled fused kernel).  The
+// fused and resident kernels are TF32 kernels for n a multiple of 128; the two-stage kernel
+// runs every tensor-core precision and any n.
+static bool variant_ok(int v, int n, int prec) {
+  const bool tf = !prec_bf16(prec) && n % 128 == 0;
   switch (v) {
     case TCV_TWO_STAGE: return true;
-    case TCV_FUSED64: return n % 128 == 0 && (n / 128 + 2) * 64 <= 512;
-    case TCV_FUSED32: return n % 128 == 0 && n <= 768;
-    case TCV_RESIDENT: return n == 128;
+    case TCV_FUSED64: return tf && (n / 128 + 2) * 64 <= 512;
+    case TCV_FUSED32: return tf && n <= 768;
+    case TCV_RESIDENT: return tf && n == 128;
     default: return false;
   }
 }
@@ -1200,18 +1305,20 @@ static bool variant_ok(int v, int n) {
 // Fused kernel where its TMEM fits (R + 2) x BN columns: n <= 768 with BN = 64.
 static bool fused_ok(int n) { return n % 128 == 0 && (n / 128 + 2) * FUSED_BN <= 512 && !getenv("KPSB_TWO_STAGE"); }
 
-int tc_fused_tiles(int n, int prec) { return (tc_supported(n, prec) && fused_ok(n)) ? n / FUSED_BN : 0; }
+int tc_fused_tiles(int n, int prec) {
+  return (tc_supported(n, prec) && !prec_bf16(prec) && fused_ok(n)) ? n / FUSED_BN : 0;
+}
 
-template <int BN, int STAGES, int STAGE, int FPL>
+template <int BN, int STAGES, int STAGE, int FPL, bool BF>
 static kpsb_status prepare_gemm() {
-  using C = TCCfg<BN, STAGES, STAGE, FPL>;
-  KPSB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, STAGE, FPL>,
+  using C = TCCfg<BN, STAGES, STAGE, FPL, BF>;
+  KPSB_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, STAGE, FPL, BF>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   return KPSB_OK;
 }
 
-static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int transpose, float* Xt,
-                            float* Zt) {
+static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int transpose, bool bf, void* Xt,
+                            int ldx, void* Zt) {
   const int n = src.n, k = src.k;
   J.X = src.X;
   J.Y = src.Y;
@@ -1219,41 +1326,31 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
   J.Zt = Zt;
   J.n = n;
   J.k = k;
-  J.ldz = k * n;
+  J.ldz = T->ld2;
+  J.ldx = ldx;
   J.active = src.active;
   J.Yf = src.yf;
-  const cuuint64_t fb = sizeof(float);
+  const cuuint64_t es = bf ? sizeof(__nv_bfloat16) : sizeof(float);
+  const cuuint64_t l1 = (cuuint64_t)T->ld1, l2 = (cuuint64_t)T->ld2, lx = (cuuint64_t)ldx;
+  const void* t1 = bf ? (const void*)(transpose ? T->B1t : T->B1f) : (const void*)(transpose ? T->T1t : T->T1f);
+  const void* t2 = bf ? (const void*)(transpose ? T->B2t : T->B2f) : (const void*)(transpose ? T->T2t : T->T2f);
   {  // Xt: {n, n, 2}
     cuuint64_t d[3] = {(cuuint64_t)n, (cuuint64_t)n, 2};
-    cuuint64_t s[2] = {fb * n, fb * n * n};
-    KPSB_TRY(make_map(&J.m1A, Xt, 3, d, s, 128));
+    cuuint64_t s[2] = {es * lx, es * lx * n};
+    KPSB_TRY(make_map(&J.m1A, Xt, 3, d, s, 128, bf));
   }
-  {  // T1: {n, n, 2, k}
-    cuuint64_t d[4] = {(cuuint64_t)n, (cuuint64_t)n, 2, (cuuint64_t)k};
-    cuuint64_t s[3] = {fb * n, fb * n * n, fb * 2 * n * n};
-    KPSB_TRY(make_map(&J.m1B, transpose ? T->T1t : T->T1f, 4, d, s, S1_BN));
+  cuuint64_t d1[4] = {(cuuint64_t)n, (cuuint64_t)n, 2, (cuuint64_t)k};
+  cuuint64_t s1[3] = {es * l1, es * l1 * n, es * 2 * l1 * n};
+  KPSB_TRY(make_map(&J.m1B, t1, 4, d1, s1, S1_BN, bf));  // T1: {n, n, 2, k}
+  if (!bf && n % 128 == 0) {  // T1 with 64-, 32- and 128-row boxes (fused and resident kernels)
+    KPSB_TRY(make_map(&J.m1F, t1, 4, d1, s1, 64));
+    KPSB_TRY(make_map(&J.m1G, t1, 4, d1, s1, 32));
+    KPSB_TRY(make_map(&J.m1R, t1, 4, d1, s1, 128));
   }
-  {  // T1 again with 64- and 32-row boxes (fused kernel)
-    cuuint64_t d[4] = {(cuuint64_t)n, (cuuint64_t)n, 2, (cuuint64_t)k};
-    cuuint64_t s[3] = {fb * n, fb * n * n, fb * 2 * n * n};
-    KPSB_TRY(make_map(&J.m1F, transpose ? T->T1t : T->T1f, 4, d, s, 64));
-    KPSB_TRY(make_map(&J.m1G, transpose ? T->T1t : T->T1f, 4, d, s, 32));
-  }
-  {  // T1 with 128-row boxes (resident kernel)
-    cuuint64_t d[4] = {(cuuint64_t)n, (cuuint64_t)n, 2, (cuuint64_t)k};
-    cuuint64_t s[3] = {fb * n, fb * n * n, fb * 2 * n * n};
-    KPSB_TRY(make_map(&J.m1R, transpose ? T->T1t : T->T1f, 4, d, s, 128));
-  }
-  {  // T2: {k n, n, 2}
-    cuuint64_t d[3] = {(cuuint64_t)k * n, (cuuint64_t)n, 2};
-    cuuint64_t s[2] = {fb * k * n, fb * (cuuint64_t)k * n * n};
-    KPSB_TRY(make_map(&J.m2A, transpose ? T->T2t : T->T2f, 3, d, s, 128));
-  }
-  {  // Zt: {k n, n, 2}
-    cuuint64_t d[3] = {(cuuint64_t)k * n, (cuuint64_t)n, 2};
-    cuuint64_t s[2] = {fb * k * n, fb * (cuuint64_t)k * n * n};
-    KPSB_TRY(make_map(&J.m2B, Zt, 3, d, s, S2_BN));
-  }
+  cuuint64_t d2[3] = {(cuuint64_t)k * n, (cuuint64_t)n, 2};
+  cuuint64_t s2[2] = {es * l2, es * l2 * n};
+  KPSB_TRY(make_map(&J.m2A, t2, 3, d2, s2, 128, bf));    // T2: {k n, n, 2}
+  KPSB_TRY(make_map(&J.m2B, Zt, 3, d2, s2, S2_BN, bf));  // Zt: {k n, n, 2}
   return KPSB_OK;
 }
 
@@ -1280,12 +1377,12 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
   if (getenv("KPSB_TWO_STAGE")) { P->variant = TCV_TWO_STAGE; return KPSB_OK; }
   if (const char* f = getenv("KPSB_TC_VARIANT")) {
     const int v = atoi(f);
-    if (variant_ok(v, n)) { P->variant = v; return KPSB_OK; }
+    if (variant_ok(v, n, P->prec)) { P->variant = v; return KPSB_OK; }
   }
-  if (n == 128 && getenv("KPSB_FUSED_TILED")) { P->variant = TCV_FUSED64; return KPSB_OK; }
+  if (n == 128 && !P->bf && getenv("KPSB_FUSED_TILED")) { P->variant = TCV_FUSED64; return KPSB_OK; }
   std::vector<int> cand;
   for (int v = 0; v < TCV_COUNT; ++v)
-    if (variant_ok(v, n)) cand.push_back(v);
+    if (variant_ok(v, n, P->prec)) cand.push_back(v);
   if (cand.size() == 1 || P->njobs == 0) { P->variant = cand[0]; return KPSB_OK; }
   const TuneKey key{n, P->prec};
   std::lock_guard<std::mutex> lk(g_tune_mu);  // one tuner at a time; later plans reuse the choice
@@ -1344,12 +1441,20 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
 
 kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h, int njobs, int n,
                            int prec, cudaStream_t st, TCPlan** out) {
-  KPSB_REQUIRE(tc_supported(n, prec), "tensor-core path needs n %% 128 == 0 (n = %d)", n);
+  KPSB_REQUIRE(tc_supported(n, prec), "no tensor-core kernel for n = %d, precision %d", n, prec);
+  const bool bf = prec_bf16(prec);
+  // a caller's split planes are TF32 planes with leading dimension n (fused CGLS path)
+  for (int p = 0; p < njobs; ++p)
+    KPSB_REQUIRE(!fwd_h[p].xt_ext || (!bf && n % 128 == 0), "caller-split planes need a TF32 mode and n %% 128 == 0");
   // kernel attributes are set here, before any graph capture that replays the applies
-  KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 2>()));
-  KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 2>()));
-  KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 1>()));
-  KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 1>()));
+  KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 2, false>()));
+  KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 2, false>()));
+  KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 1, false>()));
+  KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 1, false>()));
+  KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 2, true>()));
+  KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 2, true>()));
+  KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 1, true>()));
+  KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 1, true>()));
   KPSB_TRY((prepare_fused<FUSED_BN, 1>()));
   KPSB_TRY((prepare_fused<FUSED_BN, 2>()));
   KPSB_TRY((prepare_fused<32, 1>()));
@@ -1360,37 +1465,41 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
   P->njobs = njobs;
   P->n = n;
   P->prec = prec;
-  P->fused = fused_ok(n);  // the states carry split planes and FP32 outputs for a one-launch apply
+  P->bf = bf;
+  P->fused = !bf && fused_ok(n);  // the states carry split planes and FP32 outputs for a one-launch apply
+  const size_t es = bf ? sizeof(__nv_bfloat16) : sizeof(float);
+  const int ldx = pad8(n);
   std::vector<TCTables*> tabs(njobs);
-  size_t floats = 0;
+  size_t bytes = 0;
+  auto a256 = [](size_t x) { return (x + 255) / 256 * 256; };
   for (int p = 0; p < njobs; ++p) {
-    kpsb_status s = tc_tables(kps[p], st, &tabs[p]);
+    kpsb_status s = tc_tables(kps[p], st, bf, &tabs[p]);
     if (s) {
       delete P;
       return s;
     }
     P->kmax = std::max(P->kmax, kps[p]->k);
-    floats += (fwd_h[p].xt_ext ? 0 : (size_t)2 * n * n) + (size_t)2 * n * kps[p]->k * n;
+    bytes += (fwd_h[p].xt_ext ? 0 : a256(es * 2 * n * ldx)) + a256(es * 2 * n * tabs[p]->ld2);
   }
-  cudaError_t e = cudaMallocAsync((void**)&P->work, sizeof(float) * floats + 2 * sizeof(TCJob) * njobs + 512, st);
+  cudaError_t e = cudaMallocAsync((void**)&P->work, bytes + 2 * sizeof(TCJob) * njobs + 512, st);
   if (e != cudaSuccess) {
     delete P;
     set_error("tensor-core workspace: %s", cudaGetErrorString(e));
     return KPSB_ENOMEM;
   }
   std::vector<TCJob> hf(njobs), hb(njobs);
-  float* q = P->work;
+  char* q = P->work;
   P->ext_split = njobs > 0 && fwd_h[0].xt_ext != nullptr;
   for (int p = 0; p < njobs; ++p) {
-    float* Xt = fwd_h[p].xt_ext;
+    void* Xt = fwd_h[p].xt_ext;
     if (!Xt) {
       Xt = q;
-      q += (size_t)2 * n * n;
+      q += a256(es * 2 * n * ldx);
     }
-    float* Zt = q;
-    q += (size_t)2 * n * kps[p]->k * n;
-    kpsb_status s = fill_job(hf[p], fwd_h[p], tabs[p], 0, Xt, Zt);
-    if (!s) s = fill_job(hb[p], bwd_h[p], tabs[p], 1, Xt, Zt);
+    void* Zt = q;
+    q += a256(es * 2 * n * tabs[p]->ld2);
+    kpsb_status s = fill_job(hf[p], fwd_h[p], tabs[p], 0, bf, Xt, ldx, Zt);
+    if (!s) s = fill_job(hb[p], bwd_h[p], tabs[p], 1, bf, Xt, ldx, Zt);
     if (s) {
       cudaFreeAsync(P->work, st);
       delete P;
@@ -1427,42 +1536,47 @@ void tc_plan_free(TCPlan* P, cudaStream_t st) {
   delete P;
 }
 
-template <int BN, int STAGES, int STAGE, int FPL>
+template <int BN, int STAGES, int STAGE, int FPL, bool BF>
 static kpsb_status launch_gemm(const TCJob* jobs, int njobs, int n, int kmax, cudaStream_t st) {
-  using C = TCCfg<BN, STAGES, STAGE, FPL>;
+  using C = TCCfg<BN, STAGES, STAGE, FPL, BF>;
   const int tiles_m = (n + 127) / 128, tiles_n = (n + BN - 1) / BN;
   dim3 grid(tiles_m * tiles_n, STAGE == 1 ? kmax : 1, njobs);
-  tc_gemm_kernel<BN, STAGES, STAGE, FPL><<<grid, 128, C::SMEM, st>>>(jobs, tiles_m);
+  tc_gemm_kernel<BN, STAGES, STAGE, FPL, BF><<<grid, 128, C::SMEM, st>>>(jobs, tiles_m);
   KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
+}
+
+template <int FPL, bool BF>
+static kpsb_status launch_two_stage(const TCJob* jobs, int njobs, int n, int kmax, cudaStream_t st) {
+  KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, FPL, BF>(jobs, njobs, n, kmax, st)));
+  KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, FPL, BF>(jobs, njobs, n, kmax, st)));
   return KPSB_OK;
 }
 
 static kpsb_status launch_variant(const TCPlan* P, const TCJob* jobs, int njobs, int variant, cudaStream_t st) {
   const int n = P->n;
-  const bool x3 = P->prec == KPSB_P_TF32X3;
+  const bool two = prec_fpl(P->prec) == 2;
   switch (variant) {
-    case TCV_RESIDENT: return x3 ? launch_resident<2>(jobs, njobs, P->queue, st)
-                                 : launch_resident<1>(jobs, njobs, P->queue, st);
-    case TCV_FUSED64: return x3 ? launch_fused<64, 2>(jobs, njobs, n, st) : launch_fused<64, 1>(jobs, njobs, n, st);
-    case TCV_FUSED32: return x3 ? launch_fused<32, 2>(jobs, njobs, n, st) : launch_fused<32, 1>(jobs, njobs, n, st);
+    case TCV_RESIDENT: return two ? launch_resident<2>(jobs, njobs, P->queue, st)
+                                  : launch_resident<1>(jobs, njobs, P->queue, st);
+    case TCV_FUSED64: return two ? launch_fused<64, 2>(jobs, njobs, n, st) : launch_fused<64, 1>(jobs, njobs, n, st);
+    case TCV_FUSED32: return two ? launch_fused<32, 2>(jobs, njobs, n, st) : launch_fused<32, 1>(jobs, njobs, n, st);
     default: break;
   }
-  if (x3) {
-    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 2>(jobs, njobs, n, P->kmax, st)));
-    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 2>(jobs, njobs, n, P->kmax, st)));
-  } else {
-    KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, 1>(jobs, njobs, n, P->kmax, st)));
-    KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, 1>(jobs, njobs, n, P->kmax, st)));
-  }
-  return KPSB_OK;
+  if (P->bf) return two ? launch_two_stage<2, true>(jobs, njobs, n, P->kmax, st)
+                        : launch_two_stage<1, true>(jobs, njobs, n, P->kmax, st);
+  return two ? launch_two_stage<2, false>(jobs, njobs, n, P->kmax, st)
+             : launch_two_stage<1, false>(jobs, njobs, n, P->kmax, st);
 }
 
 kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st) {
   const TCJob* jobs = transpose ? P->d_bwd : P->d_fwd;
   const int n = P->n;
   if (!P->ext_split) {
-    dim3 gs((n / 32) * (n / 32), P->njobs);
-    tc_split_kernel<<<gs, 256, 0, st>>>(jobs);
+    const int t = (n + 31) / 32;
+    dim3 gs(t * t, P->njobs);
+    if (P->bf) tc_split_kernel<__nv_bfloat16><<<gs, 256, 0, st>>>(jobs);
+    else tc_split_kernel<float><<<gs, 256, 0, st>>>(jobs);
     KPSB_CHECK_LAUNCH();
   }
   return launch_variant(P, jobs, P->njobs, P->variant, st);
@@ -1494,8 +1608,7 @@ kpsb_status tc_apply_batch(kpsb_kp** kps, const KPJob* jobs_d, const KPJob* jobs
                            int kmax, int transpose, int prec, cudaStream_t st) {
   (void)jobs_d;
   (void)kmax;
-  KPSB_REQUIRE(prec == KPSB_P_TF32X3 || prec == KPSB_P_TF32X2,
-               "precision %d has no tensor-core kernel", prec);
+  KPSB_REQUIRE(prec_is_tc(prec), "precision %d has no tensor-core kernel", prec);
   TCPlan* P = nullptr;
   KPSB_TRY(tc_plan_create(kps, jobs_h, jobs_h, njobs, n, prec, st, &P));
   kpsb_status s = tc_plan_apply(P, transpose, st);

@@ -169,7 +169,16 @@ kpsb_status tc_work(unsigned long long* out, bool reset);
 // Tensor-core path (kpgemm_tc.cu).  A plan holds the tensor maps and workspaces of one
 // batch (forward and transpose jobs); applies reuse it.
 struct TCPlan;
+// Precisions that run on the tensor cores (TF32 and BF16 split modes).
+inline bool prec_is_tc(int prec) {
+  return prec == KPSB_P_TF32X3 || prec == KPSB_P_TF32X2 || prec == KPSB_P_BF16X3 || prec == KPSB_P_BF16X2;
+}
+inline bool prec_valid(int prec) { return prec >= KPSB_P_FP64 && prec <= KPSB_P_BF16X2; }
 bool tc_supported(int n, int prec);
+// Device bytes of a handle's tensor-core tables for one precision family, and of the
+// per-problem workspace of a plan (split input planes and intermediate).
+size_t tc_table_bytes(int n, int k, int prec);
+size_t tc_plan_ws_bytes(int n, int k, int prec);
 void tc_free(TCTables* t);
 kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h, int njobs, int n,
                            int prec, cudaStream_t st, TCPlan** out);

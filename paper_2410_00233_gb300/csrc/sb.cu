@@ -606,7 +606,7 @@ size_t sb_state_bytes(int n, int k, int prec) {
   const size_t N = (size_t)n * n;
   const int gp = gemm_prec_for(n, prec);
   const size_t zbytes = tc_supported(n, gp) ? 0 : a256(kp_z_bytes(n, k, gp));
-  size_t tc_ws = tc_supported(n, gp) ? a256(sizeof(float) * ((size_t)2 * N + (size_t)2 * n * k * n)) : 0;
+  size_t tc_ws = tc_supported(n, gp) ? a256(tc_plan_ws_bytes(n, k, gp)) : 0;
   return a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
          a256(sizeof(double) * sb_blocks(n) * 2) + 256 + tc_ws + a256(sizeof(float) * 4 * N) + 256;
 }
@@ -909,7 +909,7 @@ kpsb_status sb_fill_defaults(const kpsb_sb_opts* opts, kpsb_sb_opts& o) {
   if (o.tau_cgls <= 0.0) o.tau_cgls = 1e-4;
   if (o.i_max <= 0) o.i_max = 100;
   KPSB_REQUIRE(o.sub_batches >= 0, "sub_batches must be >= 0 (got %d)", o.sub_batches);
-  KPSB_REQUIRE(o.prec >= KPSB_P_FP64 && o.prec <= KPSB_P_TF32X2, "unknown precision %d", o.prec);
+  KPSB_REQUIRE(prec_valid(o.prec), "unknown precision %d", o.prec);
   KPSB_REQUIRE(o.threshold_rule == KPSB_THR_EXACT || o.threshold_rule == KPSB_THR_PAPER,
                "unknown threshold rule %d", o.threshold_rule);
   return KPSB_OK;

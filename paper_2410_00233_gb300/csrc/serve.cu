@@ -110,7 +110,7 @@ static int est_k(const kpsb_request& r) { return r.rank_or_tol >= 1.0 ? (int)r.r
 // Device bytes of the factors of a handle (Ax, Ay; tensor-core tables when used).
 static size_t factor_bytes(int n, int k, int prec) {
   size_t b = sizeof(float) * (size_t)2 * k * n * n;
-  if (tc_supported(n, prec)) b += sizeof(float) * (size_t)8 * k * n * n;
+  if (tc_supported(n, prec)) b += tc_table_bytes(n, k, prec);
   return b;
 }
 
@@ -386,7 +386,7 @@ extern "C" kpsb_status srv_submit(kpsb_server_t s, const kpsb_request* r, unsign
   KPSB_REQUIRE(r->rank_or_tol > 0.0, "rank_or_tol must be > 0");
   KPSB_REQUIRE(r->mu > 0.0 && r->lambda > 0.0 && r->iters >= 1, "mu, lambda > 0 and iters >= 1 required");
   KPSB_REQUIRE(r->tv == KPSB_ANISO || r->tv == KPSB_ISO, "unknown TV type %d", r->tv);
-  KPSB_REQUIRE(r->prec >= KPSB_P_FP64 && r->prec <= KPSB_P_TF32X2, "unknown precision %d", r->prec);
+  KPSB_REQUIRE(prec_valid(r->prec), "unknown precision %d", r->prec);
   SrvReq* q = new SrvReq();
   q->r = *r;
   q->psf.assign(r->psf, r->psf + (size_t)r->s0 * r->s1);

@@ -24,7 +24,7 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 BC_ZERO, BC_REFLEXIVE = 0, 1
 EGKB, RSVD = 0, 1
 ANISO, ISO = 0, 1
-P_FP64, P_FP32, P_TF32X3, P_TF32X2 = 0, 1, 2, 3
+P_FP64, P_FP32, P_TF32X3, P_TF32X2, P_BF16X3, P_BF16X2 = 0, 1, 2, 3, 4, 5
 THR_EXACT, THR_PAPER = 0, 1
 
 

@@ -1,0 +1,111 @@
+"""BF16 split-precision KP GEMMs (tcgen05 kind::f16, FP32 accumulation) and the tensor-core
+path at image sides that are not a multiple of the 128-row tile, against the oracle.
+
+BF16X2 uses the factors rounded once to BF16 (sigma folded in FP32 first): against the
+oracle applied with those same rounded factors only the split of the image (two BF16 parts,
+2^-18 relative), the split intermediate and the FP32 accumulation remain: bound 1e-4
+relative.  BF16X3 splits both operands in two BF16 parts and drops the lo*lo product
+(2^-18 relative per product): against the FP32 factors the bound is 1e-4.  The TF32 modes
+keep their own bounds (1e-4 TF32X3; 1e-4 TF32X2 against its rounded factors) at the
+masked sizes.
+"""
+import numpy as np
+import pytest
+
+from oracle import kpsb_oracle as O
+from paper_2410_00233_gb300 import inputs as I
+from tests.gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    """Round to BF16 (8 significant bits), to nearest with ties to even (finite values)."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32)
+
+
+def _tf32(a):
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return u.view(np.float32)
+
+
+def _rand_factors(n, k, seed):
+    g = I.rng(seed)
+    Ax = g.standard_normal((k, n, n)).astype(np.float32)
+    Ay = g.standard_normal((k, n, n)).astype(np.float32)
+    for i in range(k):
+        Ax[i] /= np.linalg.norm(Ax[i])
+        Ay[i] /= np.linalg.norm(Ay[i])
+    sig = np.sort(g.uniform(0.1, 3.0, size=k))[::-1].copy()
+    return Ax, Ay, sig
+
+
+def _op(Ax, Ay, sig, rnd=None):
+    k = Ax.shape[0]
+    sx = np.stack([np.float32(sig[i]) * Ax[i] for i in range(k)])
+    if rnd is not None:
+        sx, Ay = rnd(sx), rnd(Ay)
+    return O.KPSum(Ax=sx.astype(np.float64), Ay=np.asarray(Ay).astype(np.float64), sigma=np.ones(k))
+
+
+@pytest.mark.parametrize("n,k", [(64, 5), (100, 3), (128, 12), (200, 7), (256, 1), (384, 4)])
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_kp_apply_bf16_modes(n, k, transpose):
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    Ax, Ay, sig = _rand_factors(n, k, 13 * n + k)
+    kp = K.kp_from_factors(Ax, Ay, sig)
+    X = I.rng(9 + k).standard_normal((n, n))
+    ap = O.kp_apply_t if transpose else O.kp_apply
+    ref32 = ap(_op(Ax, Ay, sig), X)
+    ref_b = ap(_op(Ax, Ay, sig, _bf16), X)
+    y3 = K.kp_apply(kp, X, transpose, K.P_BF16X3)
+    y2 = K.kp_apply(kp, X, transpose, K.P_BF16X2)
+    e3 = np.linalg.norm(y3 - ref32) / np.linalg.norm(ref32)
+    e2 = np.linalg.norm(y2 - ref_b) / np.linalg.norm(ref_b)
+    assert e3 < 1e-4, e3
+    assert e2 < 1e-4, e2
+    # element-wise: no tile garbage in the masked rows and columns
+    assert np.abs(y3 - ref32).max() <= 1e-3 * np.abs(ref32).max()
+    assert np.abs(y2 - ref_b).max() <= 1e-3 * np.abs(ref_b).max()
+    # BF16X2's rounded factors move the operator by ~2^-9 relative
+    assert np.linalg.norm(y2 - ref32) / np.linalg.norm(ref32) < 1e-2
+
+
+@pytest.mark.parametrize("n,k", [(64, 5), (100, 3), (200, 7)])
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_kp_apply_tf32_modes_at_masked_sizes(n, k, transpose):
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    Ax, Ay, sig = _rand_factors(n, k, 17 * n + k)
+    kp = K.kp_from_factors(Ax, Ay, sig)
+    X = I.rng(3 + k).standard_normal((n, n))
+    ap = O.kp_apply_t if transpose else O.kp_apply
+    ref32 = ap(_op(Ax, Ay, sig), X)
+    ref_t = ap(_op(Ax, Ay, sig, _tf32), X)
+    y3 = K.kp_apply(kp, X, transpose, K.P_TF32X3)
+    y2 = K.kp_apply(kp, X, transpose, K.P_TF32X2)
+    assert np.linalg.norm(y3 - ref32) / np.linalg.norm(ref32) < 1e-4
+    assert np.linalg.norm(y2 - ref_t) / np.linalg.norm(ref_t) < 1e-4
+    assert np.abs(y3 - ref32).max() <= 5e-4 * np.abs(ref32).max()
+
+
+def test_bf16_and_masked_apply_count_their_work():
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    for n, k, prec in ((100, 3, K.P_BF16X3), (64, 4, K.P_TF32X2), (256, 2, K.P_BF16X2)):
+        Ax, Ay, sig = _rand_factors(n, k, n + 5 * k)
+        kp = K.kp_from_factors(Ax, Ay, sig)
+        X = I.rng(1).standard_normal((n, n))
+        K.kpsb_gemm_timing(True)
+        try:
+            K.kp_apply(kp, X, 0, prec)
+            assert K.kpsb_apply_counts() == (1, k * n ** 3)
+        finally:
+            K.kpsb_gemm_timing(False)

@@ -208,7 +208,7 @@ def test_kp_apply_tensor_core_tf32x2(n, k, transpose):
     assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 2e-3
 
 
-@pytest.mark.parametrize("prec_name", ["P_TF32X3", "P_TF32X2"])
+@pytest.mark.parametrize("prec_name", ["P_TF32X3", "P_TF32X2", "P_BF16X3", "P_BF16X2"])
 def test_tensor_core_sb_isnr_within_0p1_db(prec_name):
     need_gpu()
     from paper_2410_00233_gb300 import kpsb as K
@@ -279,8 +279,8 @@ def test_lambda_sweep_on_shared_factors_equals_single_solves():
 
 
 def test_uneven_batch_equals_alone():
-    """Problems of several sizes (and GEMM paths: n = 64 on CUDA cores, n = 128 / 256 on the
-    tensor cores) in one batched call, each equal to its solve alone."""
+    """Problems of several sizes (tensor-core paths: n = 64 on the masked two-stage kernel,
+    n = 128 resident, n = 256 two-stage) in one batched call, each equal to its solve alone."""
     need_gpu()
     from paper_2410_00233_gb300 import kpsb as K
 

@@ -5,17 +5,22 @@ keeps every CGLS vector, reduction and update in FP64 except the two sums of squ
 values (||z1||^2 of the apply's FP32 output and ||w||^2 of the FP32 value that is split).
 Against the oracle run on the SAME rounded operator, what is left is per-apply rounding:
 the iterate rounded to FP32 and split in two TF32 parts (2^-22 relative), the split
-intermediate (2^-22), the tensor-core FP32 accumulation (measured up to 2.8e-5 relative at
-K = 3072, smaller at the K <= 1536 used here) and the FP32 output (2^-24): a per-apply
-relative error e_a <= 3e-5.  Split Bregman with a fixed inner count turns a per-apply
+intermediate (2^-22), the tensor-core FP32 accumulation (about sqrt(K) 2^-24, K <= 1536
+here) and the FP32 output (2^-24): a per-apply relative error e_a of a few 1e-6 for these
+smooth, positive operators.  Split Bregman with a fixed inner count turns a per-apply
 relative perturbation e_a into at most ~5 e_a of max|x| element-wise over 3 outer x 10 inner
-steps (measured on the CPU by perturbing the oracle's own applies at n = 128 and 256), so
-the bound is 20 e_a = 6e-4 of max|x| element-wise and 2e-4 relative in the Frobenius norm.
+steps (measured on the CPU by perturbing the oracle's own applies at n = 128 and 256), i.e.
+~1e-5; the bounds keep a factor 10: 1e-4 of max|x| element-wise and 5e-5 relative in the
+Frobenius norm.  The BF16 modes split in two BF16 parts (2^-18 relative for the image and the
+intermediate, and BF16X3 drops the lo*lo product, 2^-18): e_a ~6e-6, bounds 3e-4 and 1e-4.
+n = 200 runs the masked two-stage kernel.  (Measured on GB300: at most 3.3e-6 element-wise
+for the TF32 modes and 7.9e-6 for the BF16 modes.)
 
 The rounded operators:
   TF32X2: Ax_i' = tf32(fl32(sigma_i) * Ax_i), Ay_i' = tf32(Ay_i), sigma' = 1 (the tables the
           kernels read; tf32 = round to nearest, ties away, 10 explicit mantissa bits);
-  TF32X3: Ax_i' = fl32(fl32(sigma_i) * Ax_i), Ay_i' = Ay_i (FP32-class products).
+  BF16X2: the same with bf16 (round to nearest even, 8 significant bits);
+  TF32X3, BF16X3: Ax_i' = fl32(fl32(sigma_i) * Ax_i), Ay_i' = Ay_i (FP32-class products).
 The factors come from the oracle's own TSVD (Alg. 1) of a synthetic PSF, rounded to FP32.
 The FP64 path is held to 1e-10 at the headline size n = 128 (8 reduction chunks).
 """
@@ -59,21 +64,33 @@ def _problem(n, seed):
     return _CACHE[key]
 
 
+def _bf16(a):
+    """Round to BF16 (8 significant bits), to nearest with ties to even (finite values)."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32)
+
+
 def _rounded_operator(Ax, Ay, sig, prec_name):
     k = Ax.shape[0]
     sx = [np.float32(sig[i]) * Ax[i] for i in range(k)]  # sigma folded in FP32, as the tables do
-    if prec_name == "P_TF32X2":
-        Axr = np.stack([_tf32(a) for a in sx]).astype(np.float64)
-        Ayr = _tf32(Ay).astype(np.float64)
+    rnd = {"P_TF32X2": _tf32, "P_BF16X2": _bf16}.get(prec_name)
+    if rnd is not None:
+        Axr = np.stack([rnd(a) for a in sx]).astype(np.float64)
+        Ayr = rnd(Ay).astype(np.float64)
     else:
         Axr = np.stack(sx).astype(np.float64)
         Ayr = Ay.astype(np.float64)
     return O.KPSum(Ax=Axr, Ay=Ayr, sigma=np.ones(k))
 
 
-@pytest.mark.parametrize("prec_name", ["P_TF32X2", "P_TF32X3"])
+_BOUNDS = {"P_TF32X2": (1e-4, 5e-5), "P_TF32X3": (1e-4, 5e-5), "P_BF16X3": (3e-4, 1e-4),
+           "P_BF16X2": (3e-4, 1e-4)}
+
+
+@pytest.mark.parametrize("prec_name", ["P_TF32X2", "P_TF32X3", "P_BF16X3", "P_BF16X2"])
 @pytest.mark.parametrize("iso", [False, True])
-@pytest.mark.parametrize("n", [128, 256])
+@pytest.mark.parametrize("n", [128, 256, 200])
 def test_tensor_core_sb_matches_oracle_elementwise(n, iso, prec_name):
     need_gpu()
     from paper_2410_00233_gb300 import kpsb as K
@@ -90,8 +107,9 @@ def test_tensor_core_sb_matches_oracle_elementwise(n, iso, prec_name):
     scale = np.abs(ref.x).max()
     err_max = np.abs(x - ref.x).max() / scale
     err_fro = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
-    assert err_max < 6e-4, (err_max, err_fro)
-    assert err_fro < 2e-4, (err_max, err_fro)
+    b_max, b_fro = _BOUNDS[prec_name]
+    assert err_max < b_max, (err_max, err_fro)
+    assert err_fro < b_fro, (err_max, err_fro)
     # the outer stopping quantity follows the same iterates
     assert abs(st.rc_sb - ref.rc_sb) <= 1e-3 * ref.rc_sb
 
