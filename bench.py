@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=256)
-    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "fp32", "tf32x3", "tf32x2"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "fp32", "tf32x3", "tf32x2", "bf16x3", "bf16x2"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--outer", type=int, default=OUTER, help="split Bregman outer steps (profiling runs only)")
@@ -233,7 +233,8 @@ def serve_main(args):
 
     torch.cuda.set_device(0)
     K.lib()
-    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "tf32x2": K.P_TF32X2}
+    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "tf32x2": K.P_TF32X2,
+             "bf16x3": K.P_BF16X3, "bf16x2": K.P_BF16X2}
     prec = precs[args.prec if args.prec != "auto" else "tf32x2"]
     sizes = [int(x) for x in args.sizes.split(",")]
     g = I.rng(5000)
@@ -320,7 +321,8 @@ def batched96_main(args):
 
     torch.cuda.set_device(0)
     K.lib()
-    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "tf32x2": K.P_TF32X2}
+    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "tf32x2": K.P_TF32X2,
+             "bf16x3": K.P_BF16X3, "bf16x2": K.P_BF16X2}
     prec = precs[args.prec if args.prec != "auto" else "tf32x2"]
     prs = [I.problem_batched(i) for i in range(96)]
     bs = [_blur_data(K, torch, pr, pr.psf.shape[0], pr.psf.shape[1], pr.n) for pr in prs]
@@ -366,7 +368,8 @@ def sweep_main(args):
 
     torch.cuda.set_device(0)
     K.lib()
-    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "tf32x2": K.P_TF32X2}
+    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "tf32x2": K.P_TF32X2,
+             "bf16x3": K.P_BF16X3, "bf16x2": K.P_BF16X2}
     prec = precs[args.prec if args.prec != "auto" else "tf32x2"]
     pr = I.problem_medium(0)
     b = _blur_data(K, torch, pr, PSF_S, PSF_S, N_IMG)
@@ -593,7 +596,8 @@ def main():
 
         B.build()
     K.lib()
-    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "tf32x2": K.P_TF32X2}
+    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "tf32x2": K.P_TF32X2,
+             "bf16x3": K.P_BF16X3, "bf16x2": K.P_BF16X2}
     prec_name = args.prec
     if prec_name == "auto":
         prec_name = os.environ.get("KPSB_BENCH_PREC", "tf32x2")

@@ -26,7 +26,7 @@
  *    entries stated for it (the Python binding checks host arrays before the call).
  *
  * Environment switches (the first two only print; the third picks which kernel computes
- * the apply, whose results agree with the others' within the TF32 tolerances):
+ * the apply; every variant gives the same bits, only the time changes):
  *   KPSB_TRACE=1        host phase trace of batched solves on stderr (plan ready, graph
  *                       instantiated and uploaded, launch, done; per stream)
  *   KPSB_TUNE_LOG=1     the tensor-core apply autotuner's timings on stderr
@@ -234,8 +234,9 @@ typedef struct {
 /* Solves `count` jobs together: jobs with the same n share every launch (grouped GEMMs
  * and vector kernels over problems, each problem with its own k and stopping state).
  * on_device = 1: b and x are device pointers.  opts gives the shared settings (tau,
- * i_max, prec, rule, stream).  The result of each job equals its sb_solve alone, up to
- * the GEMM's rounding (identical in FP64/FP32 modes). */
+ * i_max, prec, rule, stream).  The result of each job is bit-identical to its sb_solve
+ * alone, in every precision: the kernels treat each problem on its own, reductions have a
+ * fixed order, and every tensor-core apply variant issues the same MMAs per output element. */
 kpsb_status sb_solve_batched(int count, const kpsb_sb_job* jobs, int on_device,
                              const kpsb_sb_opts* opts);
 

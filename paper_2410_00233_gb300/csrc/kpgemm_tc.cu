@@ -601,10 +601,18 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
       for (int kk = 0; kk < 4; ++kk) {  // four 32-byte K steps (8 TF32 / 16 BF16) per row
         const uint32_t off = kk * 32;
         const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-        // small cross terms first, the hi x hi product last
-        if (C::A_PLANES == 2) mma(sdesc_sw128(a_lo + off), sdesc_sw128(b_hi + off), acc0);
-        if (C::B_PLANES == 2) mma(sdesc_sw128(a_hi + off), sdesc_sw128(b_lo + off), C::A_PLANES == 2 ? 1u : acc0);
-        mma(sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), 1u);
+        // Product order shared by every apply kernel: iterate lo x factor hi, iterate hi x
+        // factor lo (split factors only), then hi x hi.  The iterate (X or Z, two planes) is
+        // the A operand in stage 1 and the B operand in stage 2.
+        const uint64_t a_h = sdesc_sw128(a_hi + off), b_h = sdesc_sw128(b_hi + off);
+        if (STAGE == 1) {
+          mma(sdesc_sw128(a_lo + off), b_h, acc0);
+          if (FPL == 2) mma(a_h, sdesc_sw128(b_lo + off), 1u);
+        } else {
+          mma(a_h, sdesc_sw128(b_lo + off), acc0);
+          if (FPL == 2) mma(sdesc_sw128(a_lo + off), b_h, 1u);
+        }
+        mma(a_h, b_h, 1u);
       }
       mma_commit(&empty[s]);  // stage s free once these MMAs have read it
     }
@@ -1070,7 +1078,7 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
     int si = 0, g = 0, j = 0;  // ring slot, CTA-wide term, problem
     bool ok = true;
     const uint32_t x_hi = smem_u32(xs), x_lo = x_hi + 4 * C::TILE;
-    // S1 of CTA-wide term gi: D1 = T1 Xt^T, products (small first) T1lo*Xhi, T1hi*Xlo, T1hi*Xhi
+    // S1 of CTA-wide term gi: D1 = T1 Xt^T, products T1hi*Xlo, T1lo*Xhi, T1hi*Xhi
     auto stage1 = [&](int gi) -> bool {
       if (gi >= 1) {
         if (!fwait(d1_free, (gi - 1) & 1, s_fail)) return false;
@@ -1084,9 +1092,10 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
         const uint32_t xh = x_hi + kb * C::TILE, xl = x_lo + kb * C::TILE;
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
+          // same product order as the other kernels: X lo x T hi, X hi x T lo, hi x hi
           const uint32_t off = kk * 32, acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-          if (FPL == 2) mma_tf32(t_d1, sdesc_sw128(t_lo + off), sdesc_sw128(xh + off), idesc, acc0);
-          mma_tf32(t_d1, sdesc_sw128(t_hi + off), sdesc_sw128(xl + off), idesc, FPL == 2 ? 1u : acc0);
+          mma_tf32(t_d1, sdesc_sw128(t_hi + off), sdesc_sw128(xl + off), idesc, acc0);
+          if (FPL == 2) mma_tf32(t_d1, sdesc_sw128(t_lo + off), sdesc_sw128(xh + off), idesc, 1u);
           mma_tf32(t_d1, sdesc_sw128(t_hi + off), sdesc_sw128(xh + off), idesc, 1u);
         }
         mma_commit(&empty[q]);
@@ -1355,18 +1364,18 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
 }
 
 // ---- variant autotuner ----------------------------------------------------------------------
-// The apply variant is a function of (n, precision) alone, fixed for the process: the first
-// plan of each (n, precision) times every valid variant on a canonical batch that does not
-// depend on the caller's batch (the plan's first problem repeated once per SM: one warm-up
+// Every variant computes each output element with the same sequence of MMAs (same K order,
+// same order of the split products, same rounding of the intermediate), so all variants give
+// the same bits and the choice only moves time.  The first plan of each (n, precision, k_max,
+// batch-size bucket, split mode) times every valid variant on its own operands (one warm-up
 // and two timed forward applies, CUDA events on the plan's stream, activity flags ignored)
-// and keeps the fastest.  Every later plan of that (n, precision) - a request alone, in a
-// batch of any size, or in a serving round - runs the same kernel, so a problem's bits do
-// not depend on what it is batched with.  The copies of the canonical batch write the same
-// bits to the same buffers, which the plan overwrites before use.
-// KPSB_TC_VARIANT=v forces variant v where valid; KPSB_TUNE_LOG=1 prints the choices.
+// and keeps the fastest for the process.  KPSB_TC_VARIANT=v forces variant v where valid;
+// KPSB_TUNE_LOG=1 prints the choices.
 struct TuneKey {
-  int n, prec;
-  bool operator<(const TuneKey& o) const { return std::tie(n, prec) < std::tie(o.n, o.prec); }
+  int n, prec, kmax, pbucket, ext;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n, prec, kmax, pbucket, ext) < std::tie(o.n, o.prec, o.kmax, o.pbucket, o.ext);
+  }
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, int> g_tune;
@@ -1384,16 +1393,15 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
   for (int v = 0; v < TCV_COUNT; ++v)
     if (variant_ok(v, n, P->prec)) cand.push_back(v);
   if (cand.size() == 1 || P->njobs == 0) { P->variant = cand[0]; return KPSB_OK; }
-  const TuneKey key{n, P->prec};
+  int pb = 1;
+  while (pb < P->njobs) pb <<= 1;
+  const TuneKey key{n, P->prec, P->kmax, pb, P->ext_split ? 1 : 0};
   std::lock_guard<std::mutex> lk(g_tune_mu);  // one tuner at a time; later plans reuse the choice
   auto it = g_tune.find(key);
   if (it != g_tune.end()) { P->variant = it->second; return KPSB_OK; }
-  int dev = 0, sms = 0;
-  KPSB_TRY_CUDA(cudaGetDevice(&dev));
-  KPSB_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int R = std::max(1, sms);
-  // canonical batch: the first problem, once per SM, without its activity flag
-  std::vector<TCJob> tj((size_t)R, hf[0]);
+  // operands as planned, without the activity flags (a new problem is not active yet)
+  const int R = P->njobs;
+  std::vector<TCJob> tj(hf);
   for (auto& J : tj) J.active = nullptr;
   TCJob* dj = nullptr;
   unsigned long long saved[2] = {0, 0};
@@ -1420,8 +1428,8 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
       best_ms = ms;
     }
     if (getenv("KPSB_TUNE_LOG") && e == cudaSuccess)
-      fprintf(stderr, "[kpsb tune] n=%d prec=%d k=%d canonical jobs=%d variant %d: %.3f ms\n", n, P->prec,
-              hf[0].k, R, cand[c], ms / 2);
+      fprintf(stderr, "[kpsb tune] n=%d prec=%d kmax=%d jobs<=%d variant %d: %.3f ms\n", n, P->prec, P->kmax, pb,
+              cand[c], ms / 2);
   }
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_work, saved, sizeof(saved));
   if (a) cudaEventDestroy(a);

@@ -232,9 +232,10 @@ def test_tensor_core_sb_isnr_within_0p1_db(prec_name):
 @pytest.mark.parametrize("prec_name", ["P_TF32X3", "P_TF32X2"])
 @pytest.mark.parametrize("transpose", [0, 1])
 def test_resident_fused_and_two_stage_tensor_core_paths_agree(prec_name, transpose, monkeypatch):
-    """n = 128 runs the resident kernel (iterate in shared memory, intermediate in tensor
-    memory), n <= 768 the tiled fused kernel, larger n the two-stage kernels; all compute the
-    same split products, so they agree to accumulation-order rounding and match the oracle."""
+    """n = 128 can run the resident kernel (iterate in shared memory, intermediate in tensor
+    memory), n <= 768 the tiled fused kernel, any n the two-stage kernels.  All issue the same
+    MMAs for each output element (same K order, same order of the split products, same split of
+    the intermediate), so they give the same bits, and match the oracle."""
     need_gpu()
     from paper_2410_00233_gb300 import kpsb as K
 
@@ -259,7 +260,7 @@ def test_resident_fused_and_two_stage_tensor_core_paths_agree(prec_name, transpo
                 monkeypatch.delenv(env)
         for name, y in ys.items():
             assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < tol, (n, k, name)
-            assert np.linalg.norm(y - ys["two_stage"]) / np.linalg.norm(ref) < 1e-4, (n, k, name)
+            assert np.array_equal(y, ys["two_stage"]), (n, k, name)
 
 
 def test_lambda_sweep_on_shared_factors_equals_single_solves():

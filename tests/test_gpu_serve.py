@@ -86,12 +86,13 @@ def test_server_refuses_what_never_fits_and_admits_within_budget():
 
 
 @pytest.mark.parametrize("n,P", [(128, 200), (256, 40)])
-def test_same_bits_alone_in_a_large_batch_and_served(n, P):
+def test_same_bits_alone_in_a_large_batch_and_served(n, P, monkeypatch):
     """One request solved three ways gives the same bits: alone, inside a batch of P other
-    problems (cut into concurrent parts), and in a server round with other requests.  The
-    tensor-core apply variant is fixed per (n, precision) for the process, whatever the batch
-    that first needed it, and every kernel treats a problem on its own with fixed-order
-    reductions.  The batch runs first, so the variant is chosen on it, not on the lone solve."""
+    problems (cut into concurrent parts), and in a server round with other requests.  The lone
+    solve is forced onto the two-stage apply kernel while the batch runs whatever the tuner
+    picks for its size (the resident or tiled fused kernel): every apply variant issues the
+    same MMAs for each output element, and every vector kernel treats a problem on its own with
+    fixed-order reductions."""
     need_gpu()
     from paper_2410_00233_gb300 import kpsb as K
 
@@ -107,7 +108,9 @@ def test_same_bits_alone_in_a_large_batch_and_served(n, P):
     outs, stats = K.sb_solve_batched(jobs, prec=K.P_TF32X2)
     psf, b = _request(31, n)
     kp_t = K.kp_build(psf, n, K.BC_REFLEXIVE, 6, K.EGKB, seed=777)
+    monkeypatch.setenv("KPSB_TC_VARIANT", "0")  # two-stage kernels for the lone solve
     x_alone, st_alone = K.sb_solve(kp_t, b, 1.0, 0.1, K.ISO, 2, prec=K.P_TF32X2)
+    monkeypatch.delenv("KPSB_TC_VARIANT")
     # the same request inside a batch with the P others
     outs2, stats2 = K.sb_solve_batched(jobs[:P // 2] + [dict(kp=kp_t, b=b, mu=1.0, lam=0.1, tv=K.ISO, iters=2)]
                                        + jobs[P // 2:], prec=K.P_TF32X2)
