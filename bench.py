@@ -66,7 +66,11 @@ def parse():
                     help="profiling run: the timed steps only (no replay, e2e, plain or CPU legs), "
                          "with the library's host-driven loop (ncu cannot profile kernels inside "
                          "graphs with conditional nodes)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving block of the default run")
+    ap.add_argument("--no-large", action="store_true", help="skip the n = 512 block of the default run")
+    ap.add_argument("--serve-count", type=int, default=12, help="serving block: requests per arrival rate")
     ap.add_argument("--cpu-worker", type=float, default=0.0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-samples", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -74,67 +78,98 @@ def parse():
 # CPU oracle (baseline / reference arm): a bounded sample in a single-threaded process
 # ---------------------------------------------------------------------------------------
 
-def cpu_worker(seconds: float) -> dict:
-    import numpy as np
-
+def cpu_worker(seconds: float, samples: int = 1) -> list:
+    """`samples` bounded samples of one medium request on the CPU oracle: the full EGKB build,
+    then as many of the 100 split Bregman outer steps as fit in `seconds` (at least one),
+    extrapolated to the full solve.  One outer step is probed first to size the sample."""
     from oracle import kpsb_oracle as O
     from paper_2410_00233_gb300 import inputs as I
 
     pr = I.problem_medium(0)
-    t0 = time.perf_counter()
-    Kop, ts = O.kp_build(pr.psf, pr.n, pr.bc, pr.k, pr.p, "egkb", tau=pr.tau, start=pr.start)
-    t_build = time.perf_counter() - t0
     b_true = O.blur(pr.psf, pr.x_true, pr.bc)
     b = b_true + I.noise_vector(b_true, pr.eta, pr.zeta)
-    # the first m outer steps of the real solve, m sized from a one-step probe to the budget
-    A = lambda X: O.kp_apply(Kop, X)  # noqa: E731
-    AT = lambda Y: O.kp_apply_t(Kop, Y)  # noqa: E731
-    t1 = time.perf_counter()
-    O.split_bregman(A, AT, b, MU, LAM, LAM * LAM / 2, True, 1)
-    probe = time.perf_counter() - t1
-    done = int(min(OUTER, max(1, (seconds - t_build - probe) / max(probe, 1e-3))))
-    t1 = time.perf_counter()
-    O.split_bregman(A, AT, b, MU, LAM, LAM * LAM / 2, True, done)
-    t_outer = (time.perf_counter() - t1) / done
-    total = t_build + t_outer * OUTER
-    return dict(value=1.0 / total, t_build=t_build, t_outer=t_outer, outer_timed=done, k=ts.k,
-                sample=(f"1 request (n=128): full EGKB(FP64 oracle, k={ts.k}) + the first {done} of {OUTER} "
-                        f"split Bregman outer steps (CGLS to RC<1e-4), extrapolated to the full solve"))
+    probe = None
+    out = []
+    for _ in range(samples):
+        t0 = time.perf_counter()
+        Kop, ts = O.kp_build(pr.psf, pr.n, pr.bc, pr.k, pr.p, "egkb", tau=pr.tau, start=pr.start)
+        t_build = time.perf_counter() - t0
+        A = lambda X: O.kp_apply(Kop, X)  # noqa: E731
+        AT = lambda Y: O.kp_apply_t(Kop, Y)  # noqa: E731
+        if probe is None:
+            t1 = time.perf_counter()
+            O.split_bregman(A, AT, b, MU, LAM, LAM * LAM / 2, True, 1)
+            probe = time.perf_counter() - t1
+        done = int(min(OUTER, max(1, (seconds - t_build) / max(probe, 1e-3))))
+        t1 = time.perf_counter()
+        O.split_bregman(A, AT, b, MU, LAM, LAM * LAM / 2, True, done)
+        t_outer = (time.perf_counter() - t1) / done
+        total = t_build + t_outer * OUTER
+        out.append(dict(value=1.0 / total, wall_s=t_build + t_outer * done, t_build=t_build, t_outer=t_outer,
+                        outer_timed=done, k=ts.k,
+                        sample=(f"1 request (n=128): full EGKB(FP64 oracle, k={ts.k}) + the first {done} of {OUTER} "
+                                f"split Bregman outer steps (CGLS to RC<1e-4), extrapolated to the full solve")))
+    return out
 
 
-def run_cpu_baseline(seconds: float) -> dict:
+def host_cpu() -> dict:
+    """The host's CPU model and logical core count (reported beside the CPU baseline)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    if low.startswith("model name"):
+                        break
+    except OSError:
+        pass
+    import platform
+
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "machine": platform.machine()}
+
+
+def run_cpu_baseline(seconds: float, samples: int = 1) -> list:
+    """Runs cpu_worker in a fresh single-threaded process (no GPU visible)."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(seconds)],
-                       capture_output=True, text=True, env=env, timeout=600)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(seconds),
+                        "--cpu-samples", str(samples)],
+                       capture_output=True, text=True, env=env, timeout=60 + 3 * seconds * samples + 120)
     if r.returncode != 0:
         raise RuntimeError("cpu worker failed: " + r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    d["cores"] = 1
-    return d
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    for d in out:
+        d["cores"] = 1
+    return out
 
 
 def reference_arm(args):
+    """The CPU oracle on the headline workload: each step is one bounded sample (the full
+    EGKB build and the first outer steps that fit in about 6 s, extrapolated to the full
+    solve); value = mean extrapolated deblurs/s over the timed steps, ms_per_step = mean
+    measured wall time of a sample."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    vals = []
-    last = None
-    for i in range(args.warmup + args.steps):
-        d = run_cpu_baseline(20.0)
-        if i >= args.warmup:
-            vals.append(d["value"])
-        last = d
-    v = statistics.mean(vals)
+    res = run_cpu_baseline(6.0, args.warmup + args.steps)[args.warmup:]
+    v = statistics.mean(d["value"] for d in res)
+    wall = statistics.mean(d["wall_s"] for d in res)
+    host = host_cpu()
     line = {
         "impl": "reference", "metric": "deblurs/sec + p50/p99 latency, mixed-precision vs plain path, equal ISNR",
         "value": v, "unit": "deblurs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": 1000.0 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch": 1, "parallelism": "host, 1 thread"},
-        "cpu_baseline": {"value": v, "unit": "deblurs/s", "cores": 1, "kind": "oracle", "sample": last["sample"]},
+        "config": {"workload": WORKLOAD, "batch": 1, "parallelism": "host, 1 thread",
+                   "step": "one bounded sample: full EGKB build + the first outer steps within ~6 s, "
+                           "extrapolated to 100 outer steps (value); ms_per_step is the sample's wall time"},
+        "cpu_baseline": {"value": v, "unit": "deblurs/s", "cores": 1, "kind": "oracle", "sample": res[-1]["sample"],
+                         **host},
         "e2e": {"value": v, "unit": "deblurs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -292,6 +327,245 @@ def serve_main(args):
            "makespan_s": t_all, "isnr_db_mean": statistics.mean(isnrs), "server": sst,
            "gpu_launches": K.kpsb_kernel_launches() - launches0}
     print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# Blocks of the default run: serving (Poisson arrivals, mixed sizes) and the n = 512 case
+# ---------------------------------------------------------------------------------------
+
+SERVE_SIZES = (128, 256, 512, 1024)
+SERVE_RATES = (10.0, 50.0, 500.0)
+
+
+def _isnr(x, b, xt):
+    import numpy as np
+
+    return 20 * math.log10(np.linalg.norm(b - xt) / np.linalg.norm(x - xt))
+
+
+def _pct(vals, q):
+    v = sorted(vals)
+    return v[min(len(v) - 1, int(q * len(v)))]
+
+
+def serving_trace(K, I, torch, seed: int, count: int, rate: float, sizes=SERVE_SIZES):
+    """Requests of the serving workload: n uniform in `sizes`, a 31 x 31 turbulence-like or
+    two-Gaussian-mixture PSF (30 % of requests reuse an earlier PSF of the same size, a KP
+    cache hit), noise U[1 %, 5 %], iso/aniso 50/50, reflexive boundary; Poisson arrival times.
+    Blurred data comes from the library's exact blur (outside any timed region)."""
+    import numpy as np
+
+    g = I.rng(seed)
+    pool, reqs = [], []
+    for i in range(count):
+        n = sizes[int(g.integers(len(sizes)))]
+        reuse = [p for p in pool if p[2] == n]
+        if reuse and g.uniform() < 0.3:
+            psf, key, _ = reuse[int(g.integers(len(reuse)))]
+        else:
+            psf = I.psf_turbulence(31, g) if g.uniform() < 0.5 else I.psf_gaussian_mixture(31, g)
+            key = seed * 1000 + i + 1
+            pool.append((psf, key, n))
+        xt = I.image_piecewise_constant(n, g)
+        eta = float(g.uniform(0.01, 0.05))
+        reqs.append(dict(n=n, psf=psf, key=key, xt=xt, eta=eta, zeta=I.gaussian((n, n), g),
+                         tv=K.ISO if g.uniform() < 0.5 else K.ANISO))
+    for r in reqs:
+        n = r["n"]
+        psf_d = torch.from_numpy(np.asfortranarray(r["psf"]).reshape(-1, order="F").copy()).cuda()
+        x_d = torch.from_numpy(r["xt"].reshape(-1, order="F").copy()).cuda()
+        bt_d = torch.empty_like(x_d)
+        K.kp_blur_dev(psf_d.data_ptr(), 31, 31, n, K.BC_REFLEXIVE, x_d.data_ptr(), bt_d.data_ptr())
+        torch.cuda.synchronize()
+        bt = bt_d.cpu().numpy().reshape(n, n, order="F")
+        r["b"] = bt + I.noise_vector(bt, r["eta"], r["zeta"])
+    arrivals = np.cumsum(g.exponential(1.0 / rate, size=count))
+    return reqs, arrivals
+
+
+def serve_trace_run(K, reqs, arrivals, prec, round_steps=5):
+    """Feeds a trace to a fresh continuous-batching server at its arrival times; returns the
+    per-request results, latencies (submit to result) and the makespan."""
+    srv = K.Server(budget_bytes=64 << 30, max_active=256, round_steps=round_steps)
+    launches0 = K.kpsb_kernel_launches()
+    t0 = time.perf_counter()
+    ids = []
+    for r, ta in zip(reqs, arrivals):
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(r["psf"], r["n"], K.BC_REFLEXIVE, 20, r["b"], MU, LAM, r["tv"], OUTER,
+                              prec=prec, psf_key=r["key"]))
+    outs = [srv.poll(i, timeout_us=-1) for i in ids]
+    t_all = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    return dict(x=[o[0] for o in outs], stats=[o[1] for o in outs], lat=[o[2] for o in outs], makespan=t_all,
+                server=st, launches=K.kpsb_kernel_launches() - launches0)
+
+
+def plain_service_times(K, I, torch, seed: int):
+    """Per-size service time of the plain path (FP32 EGKB build, FP64 split Bregman), one
+    request per size alone: the build in full and the first m outer steps timed (m = 3 for
+    n <= 256, 1 above), extrapolated to 100 outer steps by the CGLS iteration count of the
+    same request on the mixed path (BF16X3: the CGLS iteration is the unit of work)."""
+    out = {}
+    for n in SERVE_SIZES:
+        reqs, _ = serving_trace(K, I, torch, seed + n, 1, 1.0, sizes=(n,))
+        r = reqs[0]
+        m = 3 if n <= 256 else 1
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kp = K.kp_build(r["psf"], n, K.BC_REFLEXIVE, 20, K.EGKB, seed=r["key"])
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, st_m = K.sb_solve(kp, r["b"], MU, LAM, r["tv"], m, prec=K.P_FP64)
+        t_m = time.perf_counter() - t0
+        _, st_mix_m = K.sb_solve(kp, r["b"], MU, LAM, r["tv"], m, prec=K.P_BF16X3)
+        _, st_mix = K.sb_solve(kp, r["b"], MU, LAM, r["tv"], OUTER, prec=K.P_BF16X3)
+        kp.close()
+        scale = st_mix.iota_total / max(1, st_mix_m.iota_total)
+        out[n] = dict(build_s=t_build, sb_first_outer_s=t_m, outer_timed=m, iota_timed=st_m.iota_total,
+                      iota_full_est=round(st_m.iota_total * scale), service_s=t_build + t_m * scale)
+    return out
+
+
+def fifo(arrivals, service):
+    """Latencies and makespan of one server taking requests one at a time in arrival order."""
+    t, lat = 0.0, []
+    for a, sv in zip(arrivals, service):
+        t = max(t, a) + sv
+        lat.append(t - a)
+    return lat, t
+
+
+def serving_block(K, I, torch, count: int):
+    """Configuration 5: Poisson arrivals at several rates, mixed sizes, the mixed path (BF16X3
+    Kronecker GEMMs, FP64 split Bregman) through the continuous-batching server against the
+    plain path one request at a time on the same traces."""
+    import numpy as np
+
+    prec = K.P_BF16X3
+    # warm-up: every size once through the server (tables, tuner choices, graph paths)
+    reqs, arr = serving_trace(K, I, torch, 6999, 4, 1000.0)
+    serve_trace_run(K, reqs, arr * 0, prec)
+    plain = plain_service_times(K, I, torch, 7100)
+    rates = []
+    isnr_pairs = []
+    for ri, rate in enumerate(SERVE_RATES):
+        reqs, arrivals = serving_trace(K, I, torch, 7000 + ri, count, rate)
+        res = serve_trace_run(K, reqs, arrivals, prec)
+        lat_plain, mk_plain = fifo(arrivals, [plain[r["n"]]["service_s"] for r in reqs])
+        isnr = [_isnr(x, r["b"], r["xt"]) for x, r in zip(res["x"], reqs)]
+        rates.append({"rate_per_s": rate, "requests": count, "sizes": [r["n"] for r in reqs],
+                      "deblurs_per_s": count / res["makespan"], "p50_ms": 1e3 * _pct(res["lat"], 0.5),
+                      "p99_ms": 1e3 * _pct(res["lat"], 0.99), "makespan_s": res["makespan"],
+                      "isnr_db_mean": statistics.mean(isnr), "cache_hits": res["server"]["cache_hits"],
+                      "peak_device_bytes": res["server"]["peak_bytes"], "gpu_launches": res["launches"],
+                      "plain_fifo": {"deblurs_per_s": count / mk_plain, "p50_ms": 1e3 * _pct(lat_plain, 0.5),
+                                     "p99_ms": 1e3 * _pct(lat_plain, 0.99)}})
+        if ri == 0:  # equal ISNR: every n = 128 request of the first trace solved alone in FP64
+            for x, r in zip(res["x"], reqs):
+                if r["n"] == 128:
+                    kp = K.kp_build(r["psf"], 128, K.BC_REFLEXIVE, 20, K.EGKB, seed=r["key"])
+                    x64, _ = K.sb_solve(kp, r["b"], MU, LAM, r["tv"], OUTER, prec=K.P_FP64)
+                    kp.close()
+                    isnr_pairs.append((_isnr(x, r["b"], r["xt"]), _isnr(x64, r["b"], r["xt"])))
+    # equal ISNR at every size: 5 outer steps, mixed vs FP64, one request per size
+    short = []
+    for n in SERVE_SIZES:
+        reqs, _ = serving_trace(K, I, torch, 7200 + n, 1, 1.0, sizes=(n,))
+        r = reqs[0]
+        kp = K.kp_build(r["psf"], n, K.BC_REFLEXIVE, 20, K.EGKB, seed=r["key"])
+        xm, _ = K.sb_solve(kp, r["b"], MU, LAM, r["tv"], 5, prec=prec)
+        x64, _ = K.sb_solve(kp, r["b"], MU, LAM, r["tv"], 5, prec=K.P_FP64)
+        kp.close()
+        short.append({"n": n, "isnr_abs_diff_db": abs(_isnr(xm, r["b"], r["xt"]) - _isnr(x64, r["b"], r["xt"]))})
+    head = rates[0]
+    return {
+        "workload": "configuration 5: Poisson arrivals at %s req/s, %d requests per rate, n uniform in %s, "
+                    "31x31 turbulence/mixture PSFs with 30%% reuse (KP cache), noise U[1%%,5%%], iso/aniso 50/50, "
+                    "k=20, 100 outer steps" % (list(SERVE_RATES), count, list(SERVE_SIZES)),
+        "mixed_path": "continuous-batching server, BF16X3 Kronecker GEMMs + FP64 split Bregman, rounds of 5 "
+                      "outer steps, size groups concurrent",
+        "plain_path": "FP32 EGKB + FP64 split Bregman one request at a time (FIFO on the same arrival trace); "
+                      "per-size service times measured with the first outer steps and extrapolated by CGLS count",
+        "deblurs_per_s": head["deblurs_per_s"], "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
+        "rates": rates, "plain_service_s": plain,
+        "isnr_abs_diff_db_max_full_n128": max((abs(a - b) for a, b in isnr_pairs), default=None),
+        "isnr_pairs_full_n128": len(isnr_pairs),
+        "isnr_abs_diff_db_5_outer": short,
+    }
+
+
+def large_block(K, I, torch, peaks):
+    """Configuration 3 (n = 512, 63 x 63 turbulence-like PSF, zero boundary, k = 20): the TSVD
+    (EGKB with k_p = 40 and full reorthogonalisation; RSVD with p = 10, q = 1) with the
+    achieved bandwidth of its R(A) products and CGS2 passes (CUDA events around every call,
+    algorithmic bytes), the singular values against the FP64 TSVD on the GPU, then split
+    Bregman iso and aniso for 100 outer steps in every Kronecker-GEMM precision, with ISNR
+    against the FP64 path (10 outer steps for the comparison: FP64 GEMMs at this size are
+    slow on GB300's FP64 pipe)."""
+    import numpy as np
+
+    pr = I.problem_large(0)
+    n = pr.n
+    b = _blur_data(K, torch, pr, 63, 63, n)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {"workload": "configuration 3: n=512, 63x63 turbulence-like PSF, zero boundary, k=20, 1% noise"}
+    tsvd = {}
+    sig64 = None
+    for name, method, p, fp64 in (("egkb_fp64", K.EGKB, 20, True), ("egkb", K.EGKB, 20, False),
+                                  ("rsvd", K.RSVD, 10, False)):
+        K.kp_build(pr.psf, n, pr.bc, 20, method, p=p, seed=pr.seed, fp64=fp64).close()  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kp = K.kp_build(pr.psf, n, pr.bc, 20, method, p=p, seed=pr.seed, fp64=fp64)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        sig = K.kp_info(kp)["sigma"]
+        kp.close()
+        if fp64:
+            sig64 = sig
+            tsvd[name] = {"build_ms": 1e3 * t_build, "k": len(sig)}
+            continue
+        K.kpsb_gemm_timing(True)
+        K.kp_build(pr.psf, n, pr.bc, 20, method, p=p, seed=pr.seed).close()
+        row = {"build_ms": 1e3 * t_build, "k": len(sig),
+               "sigma_err_vs_fp64_over_sigma1": float(np.max(np.abs(sig - sig64[:len(sig)])) / sig64[0])}
+        for tname, cat in K.TSVD_TIMERS.items():
+            calls, ms, nbytes = K.kpsb_timer_stats(cat)
+            if calls:
+                row[tname] = {"calls": calls, "ms": ms, "algorithmic_bytes": nbytes,
+                              "achieved_gbs": nbytes / (ms / 1e3) / 1e9,
+                              "frac_of_hbm": nbytes / (ms / 1e3) / 1e9 / hbm}
+        K.kpsb_gemm_timing(False)
+        tsvd[name] = row
+    out["tsvd"] = tsvd
+    out["hbm_peak_gbs"] = hbm
+    kp = K.kp_build(pr.psf, n, pr.bc, 20, K.EGKB, p=20, seed=pr.seed)
+    k = K.kp_info(kp)["k"]
+    precs = (("fp32", K.P_FP32), ("tf32x3", K.P_TF32X3), ("tf32x2", K.P_TF32X2), ("bf16x3", K.P_BF16X3),
+             ("bf16x2", K.P_BF16X2))
+    sb = {}
+    for tvn, tv in (("iso", K.ISO), ("aniso", K.ANISO)):
+        x64, _ = K.sb_solve(kp, b, MU, LAM, tv, 10, prec=K.P_FP64)
+        ref10 = _isnr(x64, b, pr.x_true)
+        rows = {}
+        for pname, prec in precs:
+            x10, _ = K.sb_solve(kp, b, MU, LAM, tv, 10, prec=prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, st = K.sb_solve(kp, b, MU, LAM, tv, OUTER, prec=prec)
+            t = time.perf_counter() - t0
+            rows[pname] = {"sb_100_outer_s": t, "iota_total": st.iota_total, "isnr_db": _isnr(x, b, pr.x_true),
+                           "isnr_abs_diff_db_vs_fp64_10_outer": abs(_isnr(x10, b, pr.x_true) - ref10)}
+        sb[tvn] = {"fp64_isnr_db_10_outer": ref10, "precisions": rows}
+    kp.close()
+    out["k"] = k
+    out["split_bregman"] = sb
+    return out
 
 
 # ---------------------------------------------------------------------------------------
@@ -551,7 +825,7 @@ def dense_tsvd_main(args):
 def main():
     args = parse()
     if args.cpu_worker > 0:
-        print(json.dumps(cpu_worker(args.cpu_worker)), flush=True)
+        print(json.dumps(cpu_worker(args.cpu_worker, args.cpu_samples)), flush=True)
         return
     if args.impl == "reference":
         reference_arm(args)
@@ -699,6 +973,31 @@ def main():
         isnr_mixed.append(20 * math.log10(np.linalg.norm(r["b"] - r["pr"].x_true) /
                                           np.linalg.norm(x - r["pr"].x_true)))
 
+    # equal ISNR over the timed step: the plain arithmetic (FP64 Kronecker GEMMs, same factors
+    # builder, same split Bregman) on every 8th request of the first timed step, batched for
+    # time, against the mixed path's result of the same request
+    isnr_cmp = None
+    if not args.no_plain:
+        sample = list(range(0, len(reqs), 8))
+        kps_p = K.kp_build_batched([dict(psf=reqs[i]["pr"].psf, n=N_IMG, bc=reqs[i]["pr"].bc,
+                                         rank_or_tol=reqs[i]["pr"].tau, method=K.EGKB, p=reqs[i]["pr"].p,
+                                         seed=reqs[i]["pr"].seed) for i in sample])
+        xs = [torch.zeros_like(reqs[i]["b_d"]) for i in sample]
+        K.sb_solve_batched([dict(kp=kp, b=reqs[i]["b_d"].data_ptr(), x=x.data_ptr(), mu=MU, lam=LAM, tv=K.ISO,
+                                 iters=args.outer) for kp, i, x in zip(kps_p, sample, xs)],
+                           on_device=True, prec=K.P_FP64)
+        torch.cuda.synchronize()
+        diffs = []
+        for i, x in zip(sample, xs):
+            r = reqs[i]
+            xp = x.cpu().numpy().reshape(N_IMG, N_IMG, order="F")
+            diffs.append(abs(_isnr(xp, r["b"], r["pr"].x_true) - isnr_mixed[i]))
+        del kps_p
+        isnr_cmp = {"isnr_abs_diff_db_max": max(diffs), "isnr_abs_diff_db_mean": statistics.mean(diffs),
+                    "requests": len(sample),
+                    "sample": "every 8th request of the first timed step, FP64 Kronecker GEMMs (the plain "
+                              "arithmetic) batched, against the mixed result of the same request"}
+
     # end to end through the host-pointer C ABI (pinned host buffers), every step
     e2e = None
     if True:
@@ -774,6 +1073,9 @@ def main():
         if prec in (K.P_TF32X3, K.P_TF32X2):
             peak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
             roof = {"bound": "tensor", "peak_note": "TF32 = measured sustained bf16 x 1.1/2.25 (of measured)"}
+        elif prec in (K.P_BF16X3, K.P_BF16X2):
+            peak = peaks.get("bf16_tflops_sustained", 1700.0)
+            roof = {"bound": "tensor", "peak_note": "measured sustained bf16 (of measured)"}
         elif prec == K.P_FP32:
             peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             roof = {"bound": "alu", "peak_note": "FP32 FMA: 152 SM x 128 lanes x 2 x max SM clock"}
@@ -792,11 +1094,23 @@ def main():
         cpu = None
         if not args.no_cpu:
             try:
-                d = run_cpu_baseline(20.0)
+                d = run_cpu_baseline(20.0)[0]
                 cpu = {"value": d["value"], "unit": "deblurs/s", "cores": d["cores"], "kind": "oracle",
-                       "sample": d["sample"]}
+                       "sample": d["sample"], **host_cpu()}
             except Exception as e:  # reported, not fatal
                 cpu = {"value": None, "unit": "deblurs/s", "cores": 1, "kind": "oracle", "sample": str(e)[:200]}
+        serving = None
+        if not args.no_serve:
+            try:
+                serving = serving_block(K, I, torch, args.serve_count)
+            except Exception as e:  # reported, not fatal
+                serving = {"error": str(e)[:300]}
+        large = None
+        if not args.no_large:
+            try:
+                large = large_block(K, I, torch, peaks)
+            except Exception as e:  # reported, not fatal
+                large = {"error": str(e)[:300]}
         lat = sorted(times)
         out = {
             "metric": "deblurs/sec + p50/p99 latency, mixed-precision vs plain path, equal ISNR",
@@ -809,10 +1123,13 @@ def main():
                        "sub_batches": "auto: %d concurrent parts of the batch" % max(1, min(4, B // 64)),
                        "parallelism": f"dp{world} (independent requests per GPU)"},
             "p50_ms": 1000.0 * lat[len(lat) // 2], "p99_ms": 1000.0 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "isnr_db_mean": statistics.mean(isnr_mixed),
+            "latency_note": "p50/p99: per-request latency of the batched step (every request of a step completes "
+                            "with the step); per-request latencies under arrivals are in serving",
+            "isnr_db_mean": statistics.mean(isnr_mixed), "equal_isnr": isnr_cmp,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
             "plain": plain, "clocks": clk,
             "phases_instrumented_step": phases,
+            "serving": serving, "large_n512": large,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -344,8 +344,13 @@ kpsb_status kpsb_apply_counts(unsigned long long* problem_applies, unsigned long
 /* Totals of one timer category (same meaning as kpsb_gemm_stats; flops 0 for the vector
  * kernels): 0 KP applies, 1 CGLS ||z||^2 (Alg. 5 steps 3-4), 2 x and r updates with
  * RC_CGLS (steps 5-6), 3 f = Ahat^T r and tau (steps 7-9), 4 w = f + delta w (step 10),
- * 5 outer-step kernels (CGLS start, shrinkage of Alg. 3/4).  KPSB_EINVAL for another
- * category. */
+ * 5 outer-step kernels (CGLS start, shrinkage of Alg. 3/4).  TSVD steps of kp_build /
+ * kp_build_dense (Alg. 1 steps 3-6, Alg. 2): 6 R(A) products, 7 CGS2 reorthogonalisation
+ * of the EGKB bases, 8 SVQB orthonormalisation of the RSVD blocks; for these three the
+ * first value counts calls and the third holds ALGORITHMIC BYTES instead of flops (R(A):
+ * the vectors read and written plus the PSF, or 4 n^4 per pass over an explicit A; CGS2:
+ * 2 (2m + 3) N elements for m basis vectors; SVQB2: 10 m N elements).  KPSB_EINVAL for
+ * another category. */
 kpsb_status kpsb_timer_stats(int category, unsigned long long* launches, double* ms, double* flops);
 
 /* Self-check of the exact integer binary32 <-> binary64 conversions that the split Bregman

@@ -31,7 +31,10 @@ enum TimerCategory {
   TIMER_SB_F = 3,      // f = Ahat^T r and its norm (steps 7-9)
   TIMER_SB_W = 4,      // w = f + delta w (step 10)
   TIMER_SB_OUTER = 5,  // outer-step kernels: start of an outer step, shrinkage
-  TIMER_CATEGORIES = 6
+  TIMER_RA = 6,        // R(A) products of the TSVD (index map or explicit matrix)
+  TIMER_REORTH = 7,    // CGS2 reorthogonalisation of the EGKB bases
+  TIMER_QR = 8,        // SVQB orthonormalisation of the RSVD blocks
+  TIMER_CATEGORIES = 9
 };
 int timer_begin(cudaStream_t st);
 void timer_end(int slot, cudaStream_t st, int cat, double flops, int launches);

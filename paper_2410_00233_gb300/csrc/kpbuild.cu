@@ -196,21 +196,37 @@ struct BuildWork {
   const float* A32 = nullptr;  // general operator: explicit A in FP32 (no PSF), or null
 };
 
+// Algorithmic bytes of one R(A) product of nb vectors (element size el): the index-map form
+// reads V, writes U (and reads prev when given) and reads the PSF; the explicit form streams
+// A (4 n^4 bytes) once per group of up to 8 vectors.  Counted by the TSVD timers.
+static double rop_bytes(bool dense, long long N, int nb, size_t el, bool prev, int s0, int s1) {
+  const double vec = (double)el * N * nb * (prev ? 3.0 : 2.0);
+  if (dense) return vec + 4.0 * (double)N * N * ((nb + 7) / 8);
+  return vec + (double)el * s0 * s1;
+}
+
 // R(A) products of the build: the PSF's index map, or the explicit matrix when one is given
 // (SP only).
 static kpsb_status rop_apply(const BuildWork<float>& w, int s0, int s1, int n, int bc, const float* V, int ldv,
                              int nb, float* U, int ldu, int transpose, const float* prev, int ldp,
                              const double* beta_dev, float beta_host, const int* skip, cudaStream_t st) {
-  if (w.A32)
-    return ra_dense_apply(w.A32, n, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host, skip, st);
-  return ra_apply(w.psf, s0, s1, n, bc, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host, skip,
-                  w.ra, st);
+  const int slot = timer_begin(st);
+  kpsb_status s =
+      w.A32 ? ra_dense_apply(w.A32, n, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host, skip, st)
+            : ra_apply(w.psf, s0, s1, n, bc, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host, skip,
+                       w.ra, st);
+  timer_end(slot, st, TIMER_RA, rop_bytes(w.A32 != nullptr, (long long)n * n, nb, sizeof(float), prev != nullptr,
+                                          s0, s1), 1);
+  return s;
 }
 static kpsb_status rop_apply(const BuildWork<double>& w, int s0, int s1, int n, int bc, const double* V,
                              int ldv, int nb, double* U, int ldu, int transpose, const double* prev, int ldp,
                              const double* beta_dev, double beta_host, const int* skip, cudaStream_t st) {
-  return ra_apply(w.psf, s0, s1, n, bc, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host, skip,
-                  w.ra, st);
+  const int slot = timer_begin(st);
+  kpsb_status s = ra_apply(w.psf, s0, s1, n, bc, V, ldv, nb, U, ldu, transpose, prev, ldp, beta_dev, beta_host,
+                           skip, w.ra, st);
+  timer_end(slot, st, TIMER_RA, rop_bytes(false, (long long)n * n, nb, sizeof(double), prev != nullptr, s0, s1), 1);
+  return s;
 }
 
 template <typename T> constexpr double eps_of();
@@ -260,8 +276,8 @@ struct HostPsf {
 
 // CGS2: two passes of v -= B (B^T v) against m columns; the second pass also gives ||v||.
 template <typename T>
-static kpsb_status cgs2(const T* B, int ldb, int m, T* v, long long N, double* h,
-                        double* norm_out, const RedScratch& red, const int* gate, cudaStream_t st) {
+static kpsb_status cgs2_run(const T* B, int ldb, int m, T* v, long long N, double* h,
+                            double* norm_out, const RedScratch& red, const int* gate, cudaStream_t st) {
   if (m > 0) {
     KPSB_TRY(la_dot_block(B, ldb, m, v, N, h, red, gate, st));
     KPSB_TRY(la_update(B, ldb, m, h, v, N, nullptr, red, gate, st));
@@ -271,6 +287,16 @@ static kpsb_status cgs2(const T* B, int ldb, int m, T* v, long long N, double* h
     KPSB_TRY(la_norm(v, N, norm_out, red, gate, st));
   }
   return KPSB_OK;
+}
+
+template <typename T>
+static kpsb_status cgs2(const T* B, int ldb, int m, T* v, long long N, double* h,
+                        double* norm_out, const RedScratch& red, const int* gate, cudaStream_t st) {
+  // algorithmic bytes: per pass the basis twice (dot, update) and v three times
+  const int slot = timer_begin(st);
+  const kpsb_status s = cgs2_run(B, ldb, m, v, N, h, norm_out, red, gate, st);
+  timer_end(slot, st, TIMER_REORTH, m > 0 ? 2.0 * (2.0 * m + 3.0) * N * sizeof(T) : (double)N * sizeof(T), 1);
+  return s;
 }
 
 // ---- EGKB ------------------------------------------------------------------------------------
@@ -478,7 +504,18 @@ static kpsb_status build_egkb(const float* A32, const T* psf_host, int s0, int s
 // Orthonormalise the m columns of Y (N x m) in place by SVQB twice (Gram matrix, its
 // eigen-decomposition, Y <- Y D^{-1/2} W Lambda^{-1/2}); null directions become zero.
 template <typename T>
+static kpsb_status svqb2_run(BuildWork<T>& w, T* Y, long long N, int m, cudaStream_t st);
+// Timed wrapper; algorithmic bytes per pass: the Gram read, the transform's read and write,
+// and the copy back (read and write) of the N x m block.
+template <typename T>
 static kpsb_status svqb2(BuildWork<T>& w, T* Y, long long N, int m, cudaStream_t st) {
+  const int slot = timer_begin(st);
+  const kpsb_status s = svqb2_run(w, Y, N, m, st);
+  timer_end(slot, st, TIMER_QR, 2.0 * 5.0 * (double)m * N * sizeof(T), 1);
+  return s;
+}
+template <typename T>
+static kpsb_status svqb2_run(BuildWork<T>& w, T* Y, long long N, int m, cudaStream_t st) {
   double* G = w.small;
   double* Gs = G + 64 * 64;
   double* d = Gs + 64 * 64;

@@ -1514,6 +1514,22 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
       return s;
     }
   }
+  // Descriptors in decreasing k: the resident kernel's CTAs claim problems in this order, so
+  // the largest problems start first and the last claims are the smallest (longest-first
+  // scheduling evens out the CTAs' loads).  Each problem's arithmetic does not depend on
+  // which CTA takes it; the other variants index descriptors by block and ignore the order.
+  {
+    std::vector<int> ord(njobs);
+    for (int p = 0; p < njobs; ++p) ord[p] = p;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return hf[a].k > hf[b].k; });
+    std::vector<TCJob> sf(njobs), sb(njobs);
+    for (int p = 0; p < njobs; ++p) {
+      sf[p] = hf[ord[p]];
+      sb[p] = hb[ord[p]];
+    }
+    hf.swap(sf);
+    hb.swap(sb);
+  }
   char* jb = (char*)(((uintptr_t)q + 255) & ~(uintptr_t)255);
   P->d_fwd = (TCJob*)jb;
   P->d_bwd = P->d_fwd + njobs;

@@ -4,7 +4,8 @@
 // builder thread provides their KP factors (TSVD of R(A) + Terms), from a cache keyed by
 // the PSF when the same PSF was seen before; a worker thread keeps the split Bregman state
 // of every admitted request resident and advances all of them together, a few outer steps
-// per round, so requests that arrive while others run join at the next round and finished
+// per round (each (image size, precision) group on its own stream, the groups at the same
+// time), so requests that arrive while others run join at the next round and finished
 // ones leave.  Each request's arithmetic is exactly that of sb_solve alone: the kernels
 // are per problem and their reductions have a fixed order, and splitting the outer steps
 // into rounds changes nothing.
@@ -224,6 +225,9 @@ static void worker_main(kpsb_server* s) {
   cudaSetDevice(s->device);
   cudaStream_t st = nullptr;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  std::vector<cudaStream_t> gstreams;  // one per concurrently advanced (n, precision) group
+  cudaEvent_t joined = nullptr;        // the joins of a round, awaited by every group stream
+  cudaEventCreateWithFlags(&joined, cudaEventDisableTiming);
   for (;;) {
     std::vector<SrvReq*> joining;
     std::vector<kpsb_kp*> evicted;
@@ -299,34 +303,68 @@ static void worker_main(kpsb_server* s) {
       act = s->active;
     }
     if (act.empty()) continue;
-    // one round: every (n, precision) group advances round_steps outer steps
+    // one round: every (n, precision) group advances round_steps outer steps.  The groups
+    // run at the same time, each on its own stream from its own host thread (small, latency-
+    // bound groups overlap the large ones); they start after the joins queued on st.
     std::map<std::pair<int, int>, std::vector<SBState*>> groups;
     std::map<SBState*, SrvReq*> owner;
     for (SrvReq* q : act) {
       groups[{q->r.n, q->r.prec}].push_back(&q->sb);
       owner[&q->sb] = q;
     }
-    for (auto& g : groups) {
+    std::vector<std::pair<std::pair<int, int>, std::vector<SBState*>>> glist(groups.begin(), groups.end());
+    const size_t G = glist.size();
+    std::vector<kpsb_status> gstat(G, KPSB_OK);
+    std::vector<std::vector<kpsb_sb_stats>> gstats(G);
+    std::vector<std::vector<int>> gdone(G);
+    std::vector<std::string> gmsg(G);
+    while (gstreams.size() < G) {
+      cudaStream_t gs = nullptr;
+      if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess) break;
+      gstreams.push_back(gs);
+    }
+    cudaError_t je = cudaEventRecord(joined, st);
+    auto run_group = [&](size_t gi) {
+      cudaStream_t gs = gstreams.empty() ? st : gstreams[gi % gstreams.size()];
+      std::vector<SBState*>& set = glist[gi].second;
       kpsb_sb_opts o;
       sb_fill_defaults(nullptr, o);
-      o.prec = g.first.second;
-      SRV_LOG("round start n=%d prec=%d count=%d", g.first.first, g.first.second, (int)g.second.size());
-      kpsb_status rs = sb_advance(g.second.data(), (int)g.second.size(), s->round_steps, o, st);
+      o.prec = glist[gi].first.second;
+      SRV_LOG("round start n=%d prec=%d count=%d", glist[gi].first.first, o.prec, (int)set.size());
+      kpsb_status rs = je == cudaSuccess && cudaStreamWaitEvent(gs, joined, 0) == cudaSuccess ? KPSB_OK : KPSB_ECUDA;
+      if (rs == KPSB_OK) rs = sb_advance(set.data(), (int)set.size(), s->round_steps, o, gs);
       SRV_LOG("round end status=%d %s", (int)rs, rs ? kpsb_last_error() : "");
-      std::vector<kpsb_sb_stats> stv;
-      std::vector<int> done;
-      if (rs == KPSB_OK) rs = sb_state_read(g.second.data(), (int)g.second.size(), stv, done, st);
-      std::string msg = rs ? std::string(kpsb_last_error()) : std::string();
-      for (size_t i = 0; i < g.second.size(); ++i) {
-        SrvReq* q = owner[g.second[i]];
-        if (rs == KPSB_OK && !done[i]) continue;
-        if (rs == KPSB_OK) {
+      if (rs == KPSB_OK) rs = sb_state_read(set.data(), (int)set.size(), gstats[gi], gdone[gi], gs);
+      if (rs == KPSB_OK && cudaStreamSynchronize(gs) != cudaSuccess) rs = KPSB_ECUDA;
+      if (rs != KPSB_OK) gmsg[gi] = kpsb_last_error();
+      gstat[gi] = rs;
+    };
+    if (G == 1 || gstreams.size() < G) {
+      for (size_t gi = 0; gi < G; ++gi) run_group(gi);
+    } else {
+      std::vector<std::thread> th;
+      for (size_t gi = 0; gi < G; ++gi)
+        th.emplace_back([&, gi] {
+          cudaSetDevice(s->device);
+          run_group(gi);
+        });
+      for (auto& t : th) t.join();
+    }
+    // retirement (every group's work has completed: each thread synchronised its stream)
+    for (size_t gi = 0; gi < G; ++gi) {
+      kpsb_status rs = gstat[gi];
+      const std::vector<SBState*>& set = glist[gi].second;
+      for (size_t i = 0; i < set.size(); ++i) {
+        SrvReq* q = owner[set[i]];
+        if (rs == KPSB_OK && !gdone[gi][i]) continue;
+        kpsb_status qs = rs;
+        if (qs == KPSB_OK) {
           const size_t NN = (size_t)q->r.n * q->r.n;
           q->x.resize(NN);
           cudaError_t e = cudaMemcpyAsync(q->x.data(), q->dev + NN, sizeof(double) * NN, cudaMemcpyDeviceToHost, st);
           if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-          if (e != cudaSuccess) rs = KPSB_ECUDA;
-          q->stats = stv[i];
+          if (e != cudaSuccess) qs = KPSB_ECUDA;
+          q->stats = gstats[gi][i];
         }
         sb_state_free(&q->sb, st);
         cudaFreeAsync(q->dev, st);
@@ -337,8 +375,8 @@ static void worker_main(kpsb_server* s) {
         auto it = s->cache.find(q->key);
         if (it != s->cache.end() && it->second.kp == q->kp) it->second.refs--;
         s->active.erase(std::find(s->active.begin(), s->active.end(), q));
-        if (rs != KPSB_OK) {
-          fail(s, q, rs, msg);
+        if (qs != KPSB_OK) {
+          fail(s, q, qs, qs == rs ? gmsg[gi] : std::string("copying the result back failed"));
         } else {
           q->state = RQ_DONE;
           q->t_done = now_s();
@@ -352,6 +390,8 @@ static void worker_main(kpsb_server* s) {
     s->st.rounds++;
   }
   cudaStreamSynchronize(st);
+  for (cudaStream_t gs : gstreams) cudaStreamDestroy(gs);
+  if (joined) cudaEventDestroy(joined);
   cudaStreamDestroy(st);
 }
 
