@@ -62,7 +62,7 @@ def test_invalid_arguments_fail_without_touching_the_gpu():
     with pytest.raises(K.KpsbError):
         K.kp_build(np.ones((40, 40)), 8, K.BC_REFLEXIVE, 2, K.EGKB)  # overhang > image
     with pytest.raises(K.KpsbError) as e:
-        K.kpsb_timer_stats(len(K.TIMER_NAMES))  # unknown timer category
+        K.kpsb_timer_stats(len(K.TIMER_NAMES) + len(K.TSVD_TIMERS))  # unknown timer category
     assert e.value.code == -1
     with pytest.raises(K.KpsbError) as e:
         K.kp_build(np.ones((3, 3)), 16385, K.BC_ZERO, 2, K.EGKB)  # n above KPSB_MAX_N
