@@ -153,7 +153,8 @@ kpsb_status kp_build(const double* psf, int s0, int s1, int n, int bc, double ra
 kpsb_status kp_info(kpsb_kp_t kp, int* n, int* k, int* kp_size, double* sigma);
 
 /* Host copies of the factors: Ax, Ay are k x (n x n) column-major FP32 (unit Frobenius
- * norm each; the largest-magnitude entry of each Ay_i is positive), sigma FP64 (k).
+ * norm each; the first entry of largest magnitude of vec(Ay_i), in column-major order, is
+ * positive), sigma FP64 (k).
  * Any pointer may be NULL. */
 kpsb_status kp_get_factors(kpsb_kp_t kp, float* Ax, float* Ay, double* sigma);
 

@@ -106,6 +106,25 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
   return r;
 }
 
+// Sum of `count` values p[0], p[stride], ... by the whole block in a fixed order: thread t
+// adds entries t, t + blockDim.x, ... in turn, then block_sum combines the threads.  Used by
+// the last block of a grid reduction, so the partials are read with __ldcg; many loads are in
+// flight at once instead of one thread walking all partials.  All threads get the result.
+__device__ __forceinline__ double block_sum_strided(const double* p, long long stride, int count,
+                                                    double* sh) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) t += __ldcg(p + (long long)i * stride);
+  return block_sum<double>(t, sh);
+}
+
+// The same by one warp (lanes stride, then the butterfly, whose lanes all end with the same
+// bits: each level adds the same two values in either order).
+__device__ __forceinline__ double warp_sum_strided(const double* p, long long stride, int count) {
+  double t = 0.0;
+  for (int i = threadIdx.x & 31; i < count; i += 32) t += __ldcg(p + (long long)i * stride);
+  return warp_sum(t);
+}
+
 // "Last block" protocol of a deterministic grid reduction: every block writes its
 // partial results, then calls this; exactly one block (the last to arrive) gets true and
 // may read all partials (with __ldcg) in a fixed order.  The counter is reset by the

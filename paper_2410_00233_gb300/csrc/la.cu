@@ -20,37 +20,59 @@ static int red_blocks(long long N, int per_thread) {
 // precision TSVD, double for the FP64 one (reductions are FP64 in both).
 
 // ---- h = S^T v --------------------------------------------------------------------------
+// Each block owns a contiguous range of rows; for a chunk of DB columns every thread reads
+// v[r] once and the DB basis entries of its rows (each read coalesced across the warp), then
+// the chunk is reduced in a fixed order: a warp butterfly in the element type, the 8 warp
+// totals in FP64 by DB threads, the blocks' FP64 partials by the last block.  One
+// __syncthreads per chunk; FP64 work per block is O(DB * warps), not O(threads).
+static constexpr int DB = 16;
+
 template <typename T>
 __global__ void __launch_bounds__(LA_THREADS) dot_block_kernel(
     const T* __restrict__ S, int ldS, int m, const T* __restrict__ v, long long N,
     double* __restrict__ part, unsigned int* __restrict__ counter, double* __restrict__ h,
     const int* skip) {
   if (gate_skip(skip)) return;
-  __shared__ double sh[32];
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long r0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (int c0 = 0; c0 < m; c0 += 8) {
-    T acc[8];
+  __shared__ T wsum[LA_THREADS / 32][DB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long per = (N + gridDim.x - 1) / gridDim.x;
+  const long long r_lo = (long long)blockIdx.x * per;
+  const long long r_hi = r_lo + per < N ? r_lo + per : N;
+  for (int c0 = 0; c0 < m; c0 += DB) {
+    T acc[DB];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = 0;
-    for (long long r = r0; r < N; r += stride) {
-      T x = v[r];
+    for (int u = 0; u < DB; ++u) acc[u] = 0;
+    for (long long r = r_lo + threadIdx.x; r < r_hi; r += LA_THREADS) {
+      const T x = v[r];
+      const T* sr = S + r + (size_t)c0 * ldS;
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (c0 + u < m) acc[u] = fma(S[r + (size_t)(c0 + u) * ldS], x, acc[u]);
+      for (int u = 0; u < DB; ++u)
+        if (c0 + u < m) acc[u] = fma(sr[(size_t)u * ldS], x, acc[u]);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (c0 + u >= m) break;
-      double t = block_sum<double>((double)acc[u], sh);
-      if (threadIdx.x == 0) part[(size_t)blockIdx.x * m + c0 + u] = t;
+    for (int u = 0; u < DB; ++u) {
+      T t = acc[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      acc[u] = t;
     }
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < DB; ++u) wsum[warp][u] = acc[u];
+    }
+    __syncthreads();
+    if (threadIdx.x < DB && c0 + (int)threadIdx.x < m) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < LA_THREADS / 32; ++w) t += (double)wsum[w][threadIdx.x];
+      part[(size_t)blockIdx.x * m + c0 + threadIdx.x] = t;
+    }
+    __syncthreads();
   }
   if (!last_block_arrive(counter, gridDim.x)) return;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double t = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(part + (size_t)b * m + i);
-    h[i] = t;
+  for (int i = warp; i < m; i += LA_THREADS / 32) {  // one warp per column, fixed order
+    const double t = warp_sum_strided(part + i, m, (int)gridDim.x);
+    if (lane == 0) h[i] = t;
   }
 }
 
@@ -88,11 +110,8 @@ __global__ void __launch_bounds__(LA_THREADS) update_kernel(
   double t = block_sum<double>((double)ss, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
   if (!last_block_arrive(counter, gridDim.x)) return;
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) a += __ldcg(part + b);
-    *norm_out = sqrt(a);
-  }
+  const double a = block_sum_strided(part, 1, (int)gridDim.x, sh);
+  if (threadIdx.x == 0) *norm_out = sqrt(a);
 }
 
 template <typename T>
@@ -130,46 +149,75 @@ kpsb_status la_scale_inv(T* v, long long N, const double* norm, const int* skip,
 }
 
 // ---- G = Y^T Y (FP64) ----------------------------------------------------------------------
+// Blocks take contiguous ranges of 64-row tiles; a tile is staged in shared memory already
+// widened to FP64 (one conversion per element, not per product) and each thread forms its
+// pairs i <= j of the upper triangle (m (m + 1) / 2 <= 2080 pairs, at most 9 per thread).
+// Partials per block, summed in a fixed order by the last block, which mirrors the triangle.
+static constexpr int GR_ROWS = 64;
+static constexpr int GR_PAIRS = 9;  // ceil(64 * 65 / 2 / 256)
+
 template <typename T>
 __global__ void __launch_bounds__(LA_THREADS) gram_kernel(const T* __restrict__ Y, int ldy,
                                                          long long N, int m,
                                                          double* __restrict__ part,
                                                          unsigned int* __restrict__ counter,
                                                          double* __restrict__ G) {
-  __shared__ T ch[32][65];
-  const int npair = m * m;
-  double acc[16];
+  __shared__ double ch[GR_ROWS][65];
+  const int npair = m * (m + 1) / 2;
+  int pi[GR_PAIRS], pj[GR_PAIRS];
 #pragma unroll
-  for (int u = 0; u < 16; ++u) acc[u] = 0.0;
-  for (long long rb = (long long)blockIdx.x * 32; rb < N; rb += (long long)gridDim.x * 32) {
+  for (int u = 0; u < GR_PAIRS; ++u) {  // pair p -> (i, j), i <= j, column j of the triangle
+    int p = threadIdx.x + u * LA_THREADS, j = 0;
+    if (p < npair) {
+      while ((j + 1) * (j + 2) / 2 <= p) ++j;
+      pi[u] = p - j * (j + 1) / 2;
+      pj[u] = j;
+    } else {
+      pi[u] = pj[u] = 0;
+    }
+  }
+  double acc[GR_PAIRS];
+#pragma unroll
+  for (int u = 0; u < GR_PAIRS; ++u) acc[u] = 0.0;
+  const long long tiles = (N + GR_ROWS - 1) / GR_ROWS;
+  const long long per = (tiles + gridDim.x - 1) / gridDim.x;
+  const long long t_lo = (long long)blockIdx.x * per, t_hi = t_lo + per < tiles ? t_lo + per : tiles;
+  for (long long tb = t_lo; tb < t_hi; ++tb) {
+    const long long rb = tb * GR_ROWS;
     __syncthreads();
-    for (int e = threadIdx.x; e < 32 * m; e += blockDim.x) {
-      int rr = e % 32, c = e / 32;
+    for (int e = threadIdx.x; e < GR_ROWS * m; e += blockDim.x) {
+      int rr = e % GR_ROWS, c = e / GR_ROWS;
       long long r = rb + rr;
-      ch[rr][c] = r < N ? Y[r + (size_t)c * ldy] : (T)0;
+      ch[rr][c] = r < N ? (double)Y[r + (size_t)c * ldy] : 0.0;
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      int p = threadIdx.x + u * LA_THREADS;
-      if (p < npair) {
-        int i = p % m, j = p / m;
+    for (int u = 0; u < GR_PAIRS; ++u) {
+      if (threadIdx.x + u * LA_THREADS < npair) {
+        const int i = pi[u], j = pj[u];
         double a = 0.0;
-        for (int rr = 0; rr < 32; ++rr) a = fma((double)ch[rr][i], (double)ch[rr][j], a);
+#pragma unroll 8
+        for (int rr = 0; rr < GR_ROWS; ++rr) a = fma(ch[rr][i], ch[rr][j], a);
         acc[u] += a;
       }
     }
   }
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
+  for (int u = 0; u < GR_PAIRS; ++u) {
     int p = threadIdx.x + u * LA_THREADS;
     if (p < npair) part[(size_t)blockIdx.x * npair + p] = acc[u];
   }
   if (!last_block_arrive(counter, gridDim.x)) return;
-  for (int p = threadIdx.x; p < npair; p += blockDim.x) {
-    double a = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) a += __ldcg(part + (size_t)b * npair + p);
-    G[p] = a;  // column-major: p = i + j m
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int p = warp; p < npair; p += LA_THREADS / 32) {  // one warp per pair, fixed order
+    const double a = warp_sum_strided(part + p, npair, (int)gridDim.x);
+    if (lane == 0) {
+      int j = 0;
+      while ((j + 1) * (j + 2) / 2 <= p) ++j;
+      const int i = p - j * (j + 1) / 2;
+      G[i + (size_t)j * m] = a;  // column-major, both triangles
+      G[j + (size_t)i * m] = a;
+    }
   }
 }
 
@@ -177,7 +225,7 @@ template <typename T>
 kpsb_status la_gram(const T* Y, int ldy, long long N, int m, double* G, const RedScratch& red,
                     cudaStream_t st) {
   KPSB_REQUIRE(m >= 1 && m <= 64, "gram width %d outside [1,64]", m);
-  int nb = (int)std::max(1LL, std::min<long long>((N + 31) / 32, 152));
+  int nb = (int)std::max(1LL, std::min<long long>((N + GR_ROWS - 1) / GR_ROWS, 2 * 152));
   gram_kernel<T><<<nb, LA_THREADS, 0, st>>>(Y, ldy, N, m, red.part, red.counter, G);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
@@ -258,7 +306,7 @@ template kpsb_status la_convert<double, float>(const float*, double*, long long,
 // ordering visits every pair once per sweep with disjoint pairs handled by different warps.
 // After convergence the column norms are the singular values, the normalised columns the
 // left singular vectors and the accumulated rotations the right singular vectors.
-__global__ void __launch_bounds__(256) jacobi_svd_kernel(const double* __restrict__ A, int lda,
+__global__ void __launch_bounds__(1024) jacobi_svd_kernel(const double* __restrict__ A, int lda,
                                                         int m, int nc, double* __restrict__ U,
                                                         double* __restrict__ S,
                                                         double* __restrict__ V,
@@ -352,7 +400,9 @@ kpsb_status la_small_svd(const double* A, int lda, int m, int nc, double* U, dou
   size_t sm = (size_t)(m * nc + nc * nc) * sizeof(double);
   KPSB_TRY_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (128 * 64 + 64 * 64) * (int)sizeof(double)));
-  jacobi_svd_kernel<<<1, 256, sm, st>>>(A, lda, m, nc, U, S, V, sweeps, 60);
+  // one warp per column pair of a round, so every rotation of a round runs at once
+  const int warps = std::max(1, std::min(32, (nc + (nc & 1)) / 2));
+  jacobi_svd_kernel<<<1, 32 * warps, sm, st>>>(A, lda, m, nc, U, S, V, sweeps, 60);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
 }

@@ -101,14 +101,12 @@ __device__ __forceinline__ bool prob_reduce2(const SBProb& P, double a, double b
   }
   const unsigned nb = (unsigned)sb_blocks(P.n);
   if (!last_block_arrive(P.counter, nb)) return false;
+  // the whole last block sums the partials, in an order fixed by n alone
+  const double ta = block_sum_strided(P.part, 2, (int)nb, sa);
+  const double tb = block_sum_strided(P.part + 1, 2, (int)nb, sa);
   if (threadIdx.x == 0) {
-    double sa = 0.0, sb = 0.0;
-    for (unsigned i = 0; i < nb; ++i) {
-      sa += __ldcg(P.part + 2 * i);
-      sb += __ldcg(P.part + 2 * i + 1);
-    }
-    out[0] = sa;
-    out[1] = sb;
+    out[0] = ta;
+    out[1] = tb;
   }
   return true;
 }

@@ -53,7 +53,7 @@ def test_egkb_small_config_vs_oracle_and_closed_form():
     Ax, Ay, _ = K.kp_get_factors(kp)
     for i in range(inf["k"]):
         assert abs(np.linalg.norm(Ax[i]) - 1) < 1e-5 and abs(np.linalg.norm(Ay[i]) - 1) < 1e-5
-        v = Ay[i].reshape(-1)
+        v = Ay[i].reshape(-1, order="F")  # vec order: ties go to the first entry of vec(Ay_i)
         assert v[np.argmax(np.abs(v))] > 0
 
 

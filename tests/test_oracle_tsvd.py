@@ -157,5 +157,5 @@ def test_kp_terms_reproduce_truncated_R():
     np.testing.assert_allclose(Rk, ts.U @ np.diag(ts.sigma) @ ts.V.T, atol=1e-13)
     for i in range(K.k):
         assert abs(np.linalg.norm(K.Ax[i]) - 1) < 1e-12 and abs(np.linalg.norm(K.Ay[i]) - 1) < 1e-12
-        v = K.Ay[i].reshape(-1)
+        v = K.Ay[i].reshape(-1, order="F")  # vec order: ties go to the first entry of vec(Ay_i)
         assert v[np.argmax(np.abs(v))] > 0
