@@ -108,39 +108,61 @@ __global__ void egkb_init_state(EgkbState* st, EgkbParams P) {
   st->kp_target = P.k_fixed > 0 ? P.k_fixed + P.p : -1;
 }
 
-// Sign convention: the entry of largest magnitude of each Ay_i is positive (ties: first).
-__global__ void sign_fix_kernel(float* Ax, float* Ay, long long N) {
-  __shared__ float bv[256];
-  __shared__ long long bi[256];
-  float* ay = Ay + (size_t)blockIdx.x * N;
-  float* ax = Ax + (size_t)blockIdx.x * N;
-  float best = -1.f;
-  long long bidx = 0;
-  for (long long e = threadIdx.x; e < N; e += blockDim.x) {
-    float a = fabsf(ay[e]);
-    if (a > best) { best = a; bidx = e; }
+// Sign convention of Terms (Theorem 2.1 fixes each pair up to a common sign): the first
+// entry of largest magnitude of vec(Ay_i) is made positive, flipping Ax_i with it.  Pass 1:
+// every block finds its largest |Ay_i| entry (smallest index on ties) and merges it into one
+// 64-bit key per term, (bits of |v|) << 32 | ~index, with atomicMax: the largest magnitude
+// wins, then the smallest index.  Pass 2 flips the term where that entry is negative.
+__global__ void sign_key_kernel(const float* __restrict__ Ay, long long N,
+                                unsigned long long* __restrict__ keys) {
+  const float* ay = Ay + (size_t)blockIdx.y * N;
+  unsigned long long best = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
+       e += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long key =
+        ((unsigned long long)__float_as_uint(fabsf(ay[e])) << 32) | (0xFFFFFFFFull - (unsigned long long)e);
+    best = key > best ? key : best;
   }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = bidx;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      float v2 = bv[threadIdx.x + o];
-      long long i2 = bi[threadIdx.x + o];
-      if (v2 > bv[threadIdx.x] || (v2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
-        bv[threadIdx.x] = v2;
-        bi[threadIdx.x] = i2;
-      }
-    }
-    __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+    best = other > best ? other : best;
   }
-  const bool flip = ay[bi[0]] < 0.f;
-  __syncthreads();
-  if (!flip) return;
-  for (long long e = threadIdx.x; e < N; e += blockDim.x) {
+  if ((threadIdx.x & 31) == 0) atomicMax(keys + blockIdx.y, best);
+}
+
+// Between the passes: the key of term i becomes its flip flag (read before any entry moves).
+__global__ void sign_decide_kernel(const float* __restrict__ Ay, long long N, int k,
+                                   unsigned long long* __restrict__ keys) {
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const long long idx = (long long)(0xFFFFFFFFull - (keys[i] & 0xFFFFFFFFull));
+    keys[i] = Ay[(size_t)i * N + idx] < 0.f ? 1ull : 0ull;
+  }
+}
+
+__global__ void sign_flip_kernel(float* __restrict__ Ax, float* __restrict__ Ay, long long N,
+                                 const unsigned long long* __restrict__ flags) {
+  if (!flags[blockIdx.y]) return;
+  float* ay = Ay + (size_t)blockIdx.y * N;
+  float* ax = Ax + (size_t)blockIdx.y * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
+       e += (long long)gridDim.x * blockDim.x) {
     ay[e] = -ay[e];
     ax[e] = -ax[e];
   }
+}
+
+// keys: k zero-initialised 64-bit words of scratch (device).
+static kpsb_status sign_fix(float* Ax, float* Ay, long long N, int k, unsigned long long* keys, cudaStream_t st) {
+  KPSB_TRY_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * k, st));
+  const int bx = (int)std::max(1LL, std::min<long long>((N + 255) / 256, 152));
+  sign_key_kernel<<<dim3(bx, k), 256, 0, st>>>(Ay, N, keys);
+  KPSB_CHECK_LAUNCH();
+  sign_decide_kernel<<<1, 64, 0, st>>>(Ay, N, k, keys);
+  KPSB_CHECK_LAUNCH();
+  sign_flip_kernel<<<dim3(bx, k), 256, 0, st>>>(Ax, Ay, N, keys);
+  KPSB_CHECK_LAUNCH();
+  return KPSB_OK;
 }
 
 // SVQB preparation: d_i = G_ii, Gs = D^{-1/2} G D^{-1/2} (zero rows where d_i = 0).
@@ -482,9 +504,8 @@ static kpsb_status build_egkb(const float* A32, const T* psf_host, int s0, int s
     s = la_matmul_small(w.S, (int)N, N, m, dU, m, kk, h->Ax, (int)N, st);
     if (!s) s = la_matmul_small(w.Q, (int)N, N, nc, dV, nc, kk, h->Ay, (int)N, st);
     if (!s) {
-      sign_fix_kernel<<<kk, 256, 0, st>>>(h->Ax, h->Ay, N);
-      count_launch();
-      e = cudaGetLastError();
+      s = sign_fix(h->Ax, h->Ay, N, kk, (unsigned long long*)w.h, st);
+      e = s == KPSB_OK ? cudaGetLastError() : cudaSuccess;
       if (e == cudaSuccess) e = cudaMemcpyAsync(h->sigma_d, dSg, sizeof(double) * kk, cudaMemcpyDeviceToDevice, st);
       h->sigma.resize(kk);
       if (e == cudaSuccess) e = cudaMemcpyAsync(h->sigma.data(), dSg, sizeof(double) * kk, cudaMemcpyDeviceToHost, st);
@@ -611,9 +632,8 @@ static kpsb_status build_rsvd(const float* A32, const T* psf_host, int s0, int s
     s = la_matmul_small(Y, (int)N, N, kp, W, kp, kk, h->Ax, (int)N, st);  // U = Q U_H
     if (!s) s = la_matmul_small(Ht, (int)N, N, kp, T2, kp, kk, h->Ay, (int)N, st);
     if (!s) {
-      sign_fix_kernel<<<kk, 256, 0, st>>>(h->Ax, h->Ay, N);
-      count_launch();
-      e = cudaGetLastError();
+      s = sign_fix(h->Ax, h->Ay, N, kk, (unsigned long long*)w.h, st);
+      e = s == KPSB_OK ? cudaGetLastError() : cudaSuccess;
       if (e == cudaSuccess) e = cudaMemcpyAsync(h->sigma_d, sig, sizeof(double) * kk, cudaMemcpyDeviceToDevice, st);
       h->sigma.assign(hsig.begin(), hsig.begin() + kk);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -345,10 +345,21 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(const double* __restri
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (fabs(ga) > tol * sqrt(al * be) && ga != 0.0) {
-          double zeta = (be - al) / (2.0 * ga);
-          double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        // the rotation's scalars by lane 0 alone (the lanes hold the same sums), then broadcast:
+        // FP64 square roots and divisions are long sequences on GB300's narrow FP64 pipe
+        double c = 1.0, s = 0.0;
+        int rot = 0;
+        if (lane == 0 && fabs(ga) > tol * sqrt(al * be) && ga != 0.0) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = c * t;
+          rot = 1;
+        }
+        rot = __shfl_sync(0xffffffffu, rot, 0);
+        if (rot) {
+          c = __shfl_sync(0xffffffffu, c, 0);
+          s = __shfl_sync(0xffffffffu, s, 0);
           for (int r = lane; r < m; r += 32) {
             double x = a[r + p * m], y = a[r + q * m];
             a[r + p * m] = c * x - s * y;
@@ -432,13 +443,23 @@ __global__ void randn_kernel(T* __restrict__ out, long long count, uint32_t key0
     uint32_t xs[4] = {x0, x1, x2, x3};
 #pragma unroll
     for (int pr = 0; pr < 2; ++pr) {
-      double u1 = ((double)xs[2 * pr] + 1.0) * 2.3283064365386963e-10;  // (0, 1]
-      double u2 = (double)xs[2 * pr + 1] * 2.3283064365386963e-10;       // [0, 1)
-      double rad = sqrt(-2.0 * log(u1));
-      double th = 6.283185307179586 * u2;
       long long i0 = g * 4 + 2 * pr;
-      if (i0 < count) out[i0] = (T)(rad * cos(th));
-      if (i0 + 1 < count) out[i0 + 1] = (T)(rad * sin(th));
+      if (sizeof(T) == sizeof(float)) {
+        // single-precision bases: the transform in FP32 (GB300's FP64 pipe is narrow)
+        float u1 = ((float)(xs[2 * pr] >> 8) + 1.0f) * 5.9604644775390625e-08f;  // (0, 1], 24 bits
+        float u2 = (float)(xs[2 * pr + 1] >> 8) * 5.9604644775390625e-08f;        // [0, 1)
+        float rad = sqrtf(-2.0f * logf(u1)), sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        if (i0 < count) out[i0] = (T)(rad * cs);
+        if (i0 + 1 < count) out[i0 + 1] = (T)(rad * sn);
+      } else {
+        double u1 = ((double)xs[2 * pr] + 1.0) * 2.3283064365386963e-10;  // (0, 1]
+        double u2 = (double)xs[2 * pr + 1] * 2.3283064365386963e-10;       // [0, 1)
+        double rad = sqrt(-2.0 * log(u1));
+        double th = 6.283185307179586 * u2;
+        if (i0 < count) out[i0] = (T)(rad * cos(th));
+        if (i0 + 1 < count) out[i0 + 1] = (T)(rad * sin(th));
+      }
     }
   }
 }
