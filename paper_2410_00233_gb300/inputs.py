@@ -174,15 +174,17 @@ def problem_large(index: int = 0) -> Problem:
 
 
 def problem_batched(index: int) -> Problem:
-    """One of 96 uneven problems: n in {64,128,256,384}, odd s in [15,63], alternating
-    Gaussian-mixture / turbulence PSFs, boundary and TV type, k in [5,20], noise 1-5%."""
+    """One of 96 uneven problems: n = (64, 128, 256, 384)[index % 4]; boundary, TV type and
+    PSF family alternate with index // 4, index // 8 and index // 16, so every size carries
+    every combination (zero / reflexive, aniso / iso, Gaussian mixture / turbulence); odd
+    s in [15, 63], k in [5, 20], noise 1-5%."""
     g = rng(4000 + index)
     n = (64, 128, 256, 384)[index % 4]
     s = int(g.integers(7, 32)) * 2 + 1  # odd in [15, 63]
     s = min(s, n - 1 if n % 2 == 0 else n)
-    psf = psf_gaussian_mixture(s, g) if (index // 4) % 2 == 0 else psf_turbulence(s, g)
+    psf = psf_gaussian_mixture(s, g) if (index // 16) % 2 == 0 else psf_turbulence(s, g)
     k = int(g.integers(5, 21))
-    return Problem(n=n, psf=psf, bc=(index // 2) % 2, x_true=image_piecewise_constant(n, g),
+    return Problem(n=n, psf=psf, bc=(index // 4) % 2, x_true=image_piecewise_constant(n, g),
                    zeta=gaussian((n, n), g), eta=float(g.uniform(0.01, 0.05)),
                    start=gaussian(n * n, g), k=k, p=max(2, (k + 3) // 4), tau=0.0,
-                   iso=bool(index % 2), seed=4000 + index)
+                   iso=bool((index // 8) % 2), seed=4000 + index)

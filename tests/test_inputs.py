@@ -3,8 +3,8 @@ reproducible counter-based streams, PSFs normalised, odd and centred, separable 
 Kronecker rank 1 and non-separable ones of higher rank, piecewise-constant images in [0, 1]
 on a zero background, the noise scaled to exactly eta ||b_true|| (Sec. 5.3.2), and the
 workload mixes (medium: n = 128, 31 x 31, reflexive, 1 %/5 % noise, automatic rank; batched:
-n cycling 64..384, odd s in [15, 63], k in [5, 20], p = max(2, (k + 3) // 4), boundary and TV
-type alternating)."""
+n cycling 64..384, odd s in [15, 63], k in [5, 20], p = max(2, (k + 3) // 4), boundary, TV
+type and PSF family alternating independently of n)."""
 import numpy as np
 import pytest
 
@@ -80,4 +80,7 @@ def test_batched_workload_recipe():
         assert s % 2 == 1 and 15 <= s <= 63 and s <= p.n
         assert 5 <= p.k <= 20 and p.p == max(2, (p.k + 3) // 4)
         assert 0.01 <= p.eta <= 0.05
-        assert p.bc == (i // 2) % 2 and p.iso == bool(i % 2)
+        assert p.bc == (i // 4) % 2 and p.iso == bool((i // 8) % 2)
+    full = [I.problem_batched(i) for i in range(96)]
+    for n in (64, 128, 256, 384):  # every size carries every boundary / TV combination
+        assert {(p.bc, p.iso) for p in full if p.n == n} == {(0, False), (0, True), (1, False), (1, True)}
