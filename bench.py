@@ -627,7 +627,7 @@ def batched96_main(args):
                       "ms_per_step": 1000 * t / args.steps, "higher_is_better": True, "data": "synthetic",
                       "config": {"workload": "96 problems, n in {64,128,256,384} x 24, odd PSF sizes 15-63 "
                                              "(mixture / turbulence), k in [5,20], iso/aniso and zero/reflexive "
-                                             "alternating, noise 1-5%, 100 outer; host arrays through the C ABI",
+                                             "alternating independently of n, noise 1-5%, 100 outer; host arrays through the C ABI",
                                  "kp_gemm": args.prec if args.prec != "auto" else "tf32x2",
                                  "note": "every size on the tensor cores (n=64 on the masked two-stage kernel); "
                                          "size groups run concurrently; apply variants autotuned per group"},
