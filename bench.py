@@ -33,6 +33,10 @@ if ROOT not in sys.path:
 
 N_IMG = 128
 PSF_S = 31
+# DRAM bytes (read + write) per KP-apply launch with all 256 problems of the headline batch
+# active, by (precision, apply variant), from ncu captures on this workload (one part, the
+# first CGLS applies): profiles/tc_apply_dram_medium_batch256.txt.
+DRAM_BYTES_256_ACTIVE = {(3, 3): 252.3e6, (3, 1): 257.1e6, (3, 2): 258.3e6, (3, 0): 316.2e6}
 OUTER = 100
 MU, LAM = 1.0, 0.1
 WORKLOAD = ("n=128 images, 31x31 two-Gaussian-mixture PSF, reflexive boundary, EGKB(FP32) "
@@ -66,6 +70,8 @@ def parse():
                     help="profiling run: the timed steps only (no replay, e2e, plain or CPU legs), "
                          "with the library's host-driven loop (ncu cannot profile kernels inside "
                          "graphs with conditional nodes)")
+    ap.add_argument("--sub-batches", type=int, default=0,
+                    help="concurrent parts of the batched solve (0: the library's default)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving block of the default run")
     ap.add_argument("--no-large", action="store_true", help="skip the n = 512 block of the default run")
     ap.add_argument("--serve-count", type=int, default=12, help="serving block: requests per arrival rate")
@@ -244,14 +250,14 @@ def make_inputs(K, I, torch, count: int, first: int, dev):
     return reqs
 
 
-def run_step(K, reqs, prec, outer=OUTER):
+def run_step(K, reqs, prec, outer=OUTER, sub_batches=0):
     """The whole hot path for one batch: kp_build for all, one batched split Bregman."""
     probs = [dict(psf=r["pr"].psf, n=N_IMG, bc=r["pr"].bc, rank_or_tol=r["pr"].tau, method=K.EGKB,
                   p=r["pr"].p, seed=r["pr"].seed) for r in reqs]
     kps = K.kp_build_batched(probs)
     jobs = [dict(kp=kp, b=r["b_d"].data_ptr(), x=r["x_d"].data_ptr(), mu=MU, lam=LAM, tv=K.ISO, iters=outer)
             for kp, r in zip(kps, reqs)]
-    stats = K.sb_solve_batched(jobs, on_device=True, prec=prec)
+    stats = K.sb_solve_batched(jobs, on_device=True, prec=prec, sub_batches=sub_batches)
     return kps, stats
 
 
@@ -738,6 +744,14 @@ def tsvd_main(args):
 
     torch.cuda.set_device(0)
     K.lib()
+    if args.profile:  # profiling run: two single-precision builds of each method at n = 512, nothing else
+        pr = I.problem_large(0)
+        for _ in range(2):
+            K.kp_build(pr.psf, pr.n, pr.bc, 20, K.EGKB, p=pr.p, seed=pr.seed).close()
+            K.kp_build(pr.psf, pr.n, pr.bc, 20, K.RSVD, p=10, seed=pr.seed).close()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "workload": "tsvd n=512 (EGKB k_p=40, RSVD p=10), 2 builds each"}))
+        return
     rows = []
     for name, pr, rank in (("medium n=128 auto-k", I.problem_medium(0), None),
                            ("large n=512 k=20", I.problem_large(0), 20)):
@@ -784,6 +798,13 @@ def dense_tsvd_main(args):
 
     torch.cuda.set_device(0)
     K.lib()
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
     s_true = np.array([1.0, 0.5, 0.25, 0.125])
     r = len(s_true)
     rows = []
@@ -808,16 +829,23 @@ def dense_tsvd_main(args):
                 ts.append(time.perf_counter() - t0)
                 inf = K.kp_info(kp)
                 kp.close()
+            # the passes over A timed on the device: CUDA events around every R(A) product,
+            # algorithmic bytes 4 n^4 per pass (8 vectors per pass) counted by the library
+            K.kpsb_gemm_timing(True)
+            K.kp_build_dense(A, n, r, method, p=p, seed=1).close()
+            calls, ra_ms, ra_bytes = K.kpsb_timer_stats(K.TSVD_TIMERS["ra_products"])
+            K.kpsb_gemm_timing(False)
             t = min(ts)
-            kp_size = inf["kp"]
-            passes = 2 * kp_size + 1 if method == K.EGKB else 4 * ((kp_size + 7) // 8)
-            a_bytes = 4.0 * n ** 4
             sig = inf["sigma"]
             k = min(len(sig), r)
-            rows.append({"n": n, "method": mname, "k": len(sig), "k_p": kp_size, "build_ms": 1000 * t,
+            rows.append({"n": n, "method": mname, "k": len(sig), "k_p": inf["kp"], "build_ms": 1000 * t,
                          "max_sigma_err_over_s1": float(np.max(np.abs(sig[:k] - s_true[:k]))),
-                         "a_passes_est": passes, "a_gbs_effective": passes * a_bytes / t / 1e9,
-                         "note": "build time includes the host FP32 copy and upload of A"})
+                         "ra_product_calls": calls, "ra_products_device_ms": ra_ms,
+                         "ra_products_algorithmic_bytes": ra_bytes,
+                         "ra_products_gbs": ra_bytes / (ra_ms / 1e3) / 1e9 if ra_ms else None,
+                         "ra_products_frac_of_hbm": (ra_bytes / (ra_ms / 1e3) / 1e9 / hbm) if ra_ms else None,
+                         "note": "build_ms is host wall time and includes the FP32 copy and upload of A; the "
+                                 "R(A) product figures are device time of the passes over A alone"})
     print(json.dumps({"metric": "TSVD of R(A) for an explicit general operator (kp_build_dense)", "unit": "ms",
                       "n_gpus": 1, "data": "synthetic (planted KP sum + dense perturbation)", "rows": rows}),
           flush=True)
@@ -886,7 +914,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     # warm-up
     for s in range(W):
-        run_step(K, steps_in[s], prec, args.outer)
+        run_step(K, steps_in[s], prec, args.outer, args.sub_batches)
     torch.cuda.synchronize()
 
     def barrier():
@@ -907,7 +935,7 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record()
-        kps, stats = run_step(K, steps_in[s], prec, args.outer)
+        kps, stats = run_step(K, steps_in[s], prec, args.outer, args.sub_batches)
         ev1.record()
         barrier()
         times.append(ev0.elapsed_time(ev1) / 1000.0)
@@ -956,15 +984,22 @@ def main():
     gapplies = phases["cgls_zz_launches"] + phases["cgls_f_launches"]
     pa, kn3 = K.kpsb_apply_counts()  # problem-applies actually performed (active problems), sum k n^3
     phases["active_problems_per_apply"] = pa / gapplies if gapplies else None
-    # DRAM traffic of the n = 128 resident apply (TF32x2), scaled from one ncu capture of the
-    # same kernel on 4 requests with distinct operators (4.529 MB read, nothing written back:
-    # the outputs stay in L2) by the units it reads: per active problem the split iterate
-    # (128 KB) and 128 KB of tables per term, i.e. (k + 1) units; that capture held
-    # sum (k + 1) = 35 units.
+    # the apply variant the replay ran (the autotuner's choice for this batch, n = 128)
+    replay_variant = None
+    bucket = 1
+    while bucket < B:
+        bucket <<= 1
+    for t in K.kpsb_tuned_variants():
+        if t["n"] == N_IMG and t["prec"] == prec and t["bucket"] == bucket:
+            replay_variant = t["variant"]
+    # DRAM traffic per launch of that kernel: ncu captures (dram__bytes_read.sum +
+    # dram__bytes_write.sum) of each variant on this workload (256 requests, one part, every
+    # problem active: the first CGLS applies), forward and transpose alternating; inactive
+    # problems read nothing, so the launch's traffic follows its active problems.
     traffic = None
-    if prec == K.P_TF32X2 and N_IMG == 128 and gapplies and pa:
-        units_per_launch = (kn3 / N_IMG ** 3 + pa) / gapplies
-        traffic = 4529280.0 / 35.0 * units_per_launch
+    cap = DRAM_BYTES_256_ACTIVE.get((prec, replay_variant))
+    if cap is not None and gapplies and pa:
+        traffic = cap * (pa / gapplies) / 256.0
     K.kpsb_gemm_timing(False)
     # ISNR of the mixed path on the first timed step
     reqs = steps_in[W]
@@ -1085,10 +1120,13 @@ def main():
             roof = {"bound": "alu", "peak_note": "FP64 FMA: 152 SM x 2 lanes x 2 x max SM clock"}
         roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "traffic_note": "bytes per launch (DRAM read + write), scaled from an ncu capture of the "
-                                     "same kernel at 4 requests by (k + 1) units per active problem",
-                     "kernel": ("KP apply: fused tensor-core kernel, 1 launch per apply" if gl and gl == gapplies
-                                else "KP apply (%d launches per apply)" % round(gl / max(1, gapplies))),
+                     "traffic_note": "bytes per launch (DRAM read + write): ncu capture of the same kernel on "
+                                     "this workload with all 256 problems active, times the replay's mean "
+                                     "active fraction" if traffic is not None else
+                                     "no capture of this kernel variant on this workload",
+                     "kernel": "KP apply, %s tensor-core kernel (autotuned for %d jobs), %d launch(es) per apply" % (
+                         K.VARIANT_NAMES.get(replay_variant, "?"), B, round(gl / max(1, gapplies))),
+                     "tuned_variants": K.kpsb_tuned_variants(),
                      "launches": gl, "kernel_ms": gms, "instrumented_step_s": t_instr,
                      "algorithmic_flops_per_launch": (gflops / gl) if gl else None,
                      "measured": "CUDA events around every KP apply in an instrumented replay of one timed step"})
@@ -1121,7 +1159,8 @@ def main():
             "config": {"workload": WORKLOAD, "batch_per_gpu": B, "global_batch": B * world,
                        "n": N_IMG, "psf": PSF_S, "outer_iters": args.outer, "mean_k": statistics.mean(ks),
                        "kp_gemm": prec_name, "l2": "flushed (256 MB write) between timed steps",
-                       "sub_batches": "auto: %d concurrent parts of the batch" % max(1, min(4, B // 64)),
+                       "sub_batches": ("auto: %d concurrent parts of the batch" % max(1, min(4, B // 64))
+                                       if args.sub_batches <= 0 else args.sub_batches),
                        "parallelism": f"dp{world} (independent requests per GPU)"},
             "p50_ms": 1000.0 * lat[len(lat) // 2], "p99_ms": 1000.0 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "latency_note": "p50/p99: per-request latency of the batched step (every request of a step completes "

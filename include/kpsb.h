@@ -364,6 +364,13 @@ kpsb_status kpsb_timer_stats(int category, unsigned long long* launches, double*
 kpsb_status kpsb_conversion_check(unsigned long long n_random, unsigned long long seed,
                                   unsigned long long* mismatches);
 
+/* The tensor-core apply variants the autotuner has chosen in this process (every variant
+ * gives the same bits; the choice only moves time).  Writes up to max_rows rows of 6 ints
+ * (n, precision, k_max, batch-size bucket (next power of two), caller-split planes 0/1,
+ * variant: 0 two-stage, 1 fused 64-column, 2 fused 32-column, 3 resident n = 128) to rows
+ * (host, may be NULL) and returns the number of choices made. */
+int kpsb_tuned_variants(int* rows, int max_rows);
+
 /* Self-test of the bounded device waits behind KPSB_ETIMEOUT (the paper has no counterpart):
  * one thread waits on an mbarrier that nothing arrives at, through the same bounded-wait
  * routine as the tensor-core kernels, with a limit of about limit_us microseconds of SM clock

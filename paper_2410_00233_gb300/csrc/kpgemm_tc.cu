@@ -1367,8 +1367,8 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
 // Every variant computes each output element with the same sequence of MMAs (same K order,
 // same order of the split products, same rounding of the intermediate), so all variants give
 // the same bits and the choice only moves time.  The first plan of each (n, precision, k_max,
-// batch-size bucket, split mode) times every valid variant on its own operands (one warm-up
-// and two timed forward applies, CUDA events on the plan's stream, activity flags ignored)
+// batch-size bucket, split mode) times every valid variant on its own operands (two warm-up
+// and four timed forward applies, CUDA events on the plan's stream, activity flags ignored)
 // and keeps the fastest for the process.  KPSB_TC_VARIANT=v forces variant v where valid;
 // KPSB_TUNE_LOG=1 prints the choices.
 struct TuneKey {
@@ -1415,10 +1415,12 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   int best = cand[0];
   float best_ms = 0.f;
+  constexpr int TUNE_REPS = 4;  // timed applies per candidate, after two warm-up applies
   for (size_t c = 0; c < cand.size() && e == cudaSuccess && s == KPSB_OK; ++c) {
     s = launch_variant(P, dj, R, cand[c], st);
+    if (s == KPSB_OK) s = launch_variant(P, dj, R, cand[c], st);
     if (s == KPSB_OK) e = cudaEventRecord(a, st);
-    for (int r = 0; r < 2 && s == KPSB_OK && e == cudaSuccess; ++r) s = launch_variant(P, dj, R, cand[c], st);
+    for (int r = 0; r < TUNE_REPS && s == KPSB_OK && e == cudaSuccess; ++r) s = launch_variant(P, dj, R, cand[c], st);
     if (s == KPSB_OK && e == cudaSuccess) e = cudaEventRecord(b, st);
     if (s == KPSB_OK && e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
@@ -1429,7 +1431,7 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
     }
     if (getenv("KPSB_TUNE_LOG") && e == cudaSuccess)
       fprintf(stderr, "[kpsb tune] n=%d prec=%d kmax=%d jobs<=%d variant %d: %.3f ms\n", n, P->prec, P->kmax, pb,
-              cand[c], ms / 2);
+              cand[c], ms / TUNE_REPS);
   }
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_work, saved, sizeof(saved));
   if (a) cudaEventDestroy(a);
@@ -1649,6 +1651,24 @@ kpsb_status tc_apply_batch(kpsb_kp** kps, const KPJob* jobs_d, const KPJob* jobs
 }  // namespace kpsb
 
 using namespace kpsb;
+
+extern "C" int kpsb_tuned_variants(int* rows, int max_rows) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int i = 0;
+  for (const auto& kv : g_tune) {
+    if (rows && i < max_rows) {
+      int* r = rows + 6 * i;
+      r[0] = kv.first.n;
+      r[1] = kv.first.prec;
+      r[2] = kv.first.kmax;
+      r[3] = kv.first.pbucket;
+      r[4] = kv.first.ext;
+      r[5] = kv.second;
+    }
+    ++i;
+  }
+  return i;
+}
 
 extern "C" kpsb_status kpsb_wait_selftest(unsigned int limit_us) {
   clear_error();

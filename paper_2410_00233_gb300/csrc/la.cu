@@ -302,8 +302,10 @@ template kpsb_status la_matmul_small<double, float>(const double*, int, long lon
 template kpsb_status la_convert<double, float>(const float*, double*, long long, cudaStream_t);
 
 // ---- one-sided Jacobi SVD (Hestenes) in one thread block -----------------------------------
+static constexpr int JL = 8;  // lanes per column pair
 // Columns p < q are rotated so that they become orthogonal; a cyclic "round robin"
-// ordering visits every pair once per sweep with disjoint pairs handled by different warps.
+// ordering visits every pair once per sweep, the disjoint pairs of a round at the same time
+// (JL lanes each).
 // After convergence the column norms are the singular values, the normalised columns the
 // left singular vectors and the accumulated rotations the right singular vectors.
 __global__ void __launch_bounds__(1024) jacobi_svd_kernel(const double* __restrict__ A, int lda,
@@ -329,48 +331,49 @@ __global__ void __launch_bounds__(1024) jacobi_svd_kernel(const double* __restri
     if (tid == 0) rot_count = 0;
     __syncthreads();
     for (int round = 0; round < ncp - 1; ++round) {
-      for (int pi = warp; pi < ncp / 2; pi += nwarps) {
-        int pos_a = pi, pos_b = ncp - 1 - pi;
-        int p = pos_a == 0 ? 0 : 1 + (pos_a - 1 + round) % (ncp - 1);
-        int q = 1 + (pos_b - 1 + round) % (ncp - 1);
-        if (p >= nc || q >= nc) continue;
-        if (p > q) { int t = p; p = q; q = t; }
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int r = lane; r < m; r += 32) {
-          double x = a[r + p * m], y = a[r + q * m];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
+      // JL lanes per column pair, 32 / JL pairs per warp: GB300 issues FP64 instructions to a
+      // narrow pipe, so every warp instruction should carry as many useful lanes as possible
+      for (int pb = warp * (32 / JL); pb < ncp / 2; pb += nwarps * (32 / JL)) {
+        const int pi = pb + lane / JL, sl = lane % JL;
+        int p = 0, q = 0;
+        bool act = pi < ncp / 2;
+        if (act) {
+          const int pos_a = pi, pos_b = ncp - 1 - pi;
+          p = pos_a == 0 ? 0 : 1 + (pos_a - 1 + round) % (ncp - 1);
+          q = 1 + (pos_b - 1 + round) % (ncp - 1);
+          act = p < nc && q < nc;
+          if (p > q) { int t = p; p = q; q = t; }
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        // the rotation's scalars by lane 0 alone (the lanes hold the same sums), then broadcast:
-        // FP64 square roots and divisions are long sequences on GB300's narrow FP64 pipe
-        double c = 1.0, s = 0.0;
-        int rot = 0;
-        if (lane == 0 && fabs(ga) > tol * sqrt(al * be) && ga != 0.0) {
+        double al = 0.0, be = 0.0, ga = 0.0;
+        if (act) {
+          for (int r = sl; r < m; r += JL) {
+            double x = a[r + p * m], y = a[r + q * m];
+            al = fma(x, x, al);
+            be = fma(y, y, be);
+            ga = fma(x, y, ga);
+          }
+        }
+#pragma unroll
+        for (int o = JL / 2; o > 0; o >>= 1) {  // butterfly inside the JL-lane group
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (act && fabs(ga) > tol * sqrt(al * be) && ga != 0.0) {
           const double zeta = (be - al) / (2.0 * ga);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = c * t;
-          rot = 1;
-        }
-        rot = __shfl_sync(0xffffffffu, rot, 0);
-        if (rot) {
-          c = __shfl_sync(0xffffffffu, c, 0);
-          s = __shfl_sync(0xffffffffu, s, 0);
-          for (int r = lane; r < m; r += 32) {
+          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          for (int r = sl; r < m; r += JL) {
             double x = a[r + p * m], y = a[r + q * m];
             a[r + p * m] = c * x - s * y;
             a[r + q * m] = s * x + c * y;
           }
-          for (int r = lane; r < nc; r += 32) {
+          for (int r = sl; r < nc; r += JL) {
             double x = v[r + p * nc], y = v[r + q * nc];
             v[r + p * nc] = c * x - s * y;
             v[r + q * nc] = s * x + c * y;
           }
-          if (lane == 0) atomicAdd(&rot_count, 1);
+          if (sl == 0) atomicAdd(&rot_count, 1);
         }
       }
       __syncthreads();
@@ -411,8 +414,9 @@ kpsb_status la_small_svd(const double* A, int lda, int m, int nc, double* U, dou
   size_t sm = (size_t)(m * nc + nc * nc) * sizeof(double);
   KPSB_TRY_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (128 * 64 + 64 * 64) * (int)sizeof(double)));
-  // one warp per column pair of a round, so every rotation of a round runs at once
-  const int warps = std::max(1, std::min(32, (nc + (nc & 1)) / 2));
+  // JL lanes per column pair, every rotation of a round at once
+  const int pairs = (nc + (nc & 1)) / 2;
+  const int warps = std::max(1, (pairs + 32 / JL - 1) / (32 / JL));
   jacobi_svd_kernel<<<1, 32 * warps, sm, st>>>(A, lda, m, nc, U, S, V, sweeps, 60);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;

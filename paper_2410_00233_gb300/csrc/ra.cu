@@ -19,6 +19,7 @@ namespace kpsb {
 static constexpr int RA_TS = 64;            // tile side of the reduction
 static constexpr int RA_SLOTS = 256;        // 127 diagonal + 127 anti-diagonal slots (+2 pad)
 static constexpr int RA_MAX_S = 1024;       // largest PSF side handled
+static constexpr int RA_MIX_SMEM = 4096;    // PSF entries staged in shared memory for the mix (64 x 64)
 
 __device__ __forceinline__ bool ra_tile_direct(int tr, int tq, int c, int s) {
   int dlo = (tr - tq) * RA_TS - (RA_TS - 1) + c, dhi = (tr - tq) * RA_TS + (RA_TS - 1) + c;
@@ -43,6 +44,10 @@ __global__ void __launch_bounds__(256) ra_reduce_kernel(
     unsigned int* __restrict__ counters, T* __restrict__ wout) {
   __shared__ T tile[RA_TS * (RA_TS + 1)];
   __shared__ double Dsh[RA_MAX_S];
+  // the PSF, staged for the mix when it fits (single precision only: the FP64 tile and
+  // sums already take most of the static shared memory)
+  constexpr int MIX_N = sizeof(T) == sizeof(float) ? RA_MIX_SMEM : 1;
+  __shared__ T Psh[MIX_N];
   const int nt = (n + RA_TS - 1) / RA_TS;
   const int ntiles = nt * nt;
   const int tr = blockIdx.x % nt, tq = blockIdx.x / nt;
@@ -113,14 +118,21 @@ __global__ void __launch_bounds__(256) ra_reduce_kernel(
     }
     Dsh[t] = acc;
   }
+  // the mix reads every PSF tap once per output: stage the PSF in shared memory (coalesced,
+  // all threads) instead of one dependent global load per tap and output
+  const int s1 = transpose ? s_red : s_exp;
+  const bool staged = s0 * s1 <= MIX_N;
+  if (staged)
+    for (int e = threadIdx.x; e < s0 * s1; e += blockDim.x) Psh[e] = psf[e];
   __syncthreads();
+  const T* P = staged ? Psh : psf;
   // mix: R: w_b = sum_a P(a,b) D_a ; R^T: w_a = sum_b P(a,b) D_b   (P column-major s0 x s1)
   for (int o = threadIdx.x; o < s_exp; o += blockDim.x) {
     double acc = 0.0;
     if (!transpose) {
-      for (int a = 0; a < s_red; ++a) acc += (double)psf[a + o * s0] * Dsh[a];
+      for (int a = 0; a < s_red; ++a) acc += (double)P[a + o * s0] * Dsh[a];
     } else {
-      for (int b = 0; b < s_red; ++b) acc += (double)psf[o + b * s0] * Dsh[b];
+      for (int b = 0; b < s_red; ++b) acc += (double)P[o + b * s0] * Dsh[b];
     }
     wout[(size_t)col * s_exp + o] = (T)acc;
   }

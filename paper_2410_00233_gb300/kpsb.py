@@ -123,6 +123,7 @@ _SIGS = {
     "kpsb_apply_counts": (C.c_int, [C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
     "kpsb_conversion_check": (C.c_int, [C.c_ulonglong, C.c_ulonglong, C.POINTER(C.c_ulonglong)]),
     "kpsb_wait_selftest": (C.c_int, [C.c_uint]),
+    "kpsb_tuned_variants": (C.c_int, [C.POINTER(C.c_int), C.c_int]),
 }
 
 
@@ -563,3 +564,15 @@ def kpsb_wait_selftest(limit_us: int = 50):
     """Runs the bounded-wait self-test; raises KpsbError (code -4, ETIMEOUT) when the wait ran
     out as designed."""
     _check("kpsb_wait_selftest", lib().kpsb_wait_selftest(int(limit_us)))
+
+
+VARIANT_NAMES = {0: "two-stage", 1: "fused 64-column", 2: "fused 32-column", 3: "resident"}
+
+
+def kpsb_tuned_variants():
+    """The autotuner's choices so far: list of dicts (n, prec, kmax, bucket, ext, variant)."""
+    cnt = lib().kpsb_tuned_variants(None, 0)
+    buf = (C.c_int * (6 * max(1, cnt)))()
+    cnt = lib().kpsb_tuned_variants(buf, cnt)
+    keys = ("n", "prec", "kmax", "bucket", "ext", "variant")
+    return [dict(zip(keys, buf[6 * i:6 * i + 6])) for i in range(cnt)]
