@@ -101,7 +101,19 @@ __device__ __forceinline__ bool prob_reduce2(const SBProb& P, double a, double b
   }
   const unsigned nb = (unsigned)sb_blocks(P.n);
   if (!last_block_arrive(P.counter, nb)) return false;
-  // the whole last block sums the partials, in an order fixed by n alone
+  // the last block sums the partials in an order fixed by n alone: one warp up to 32 chunks
+  // (n <= 256; no block barrier on this short path), the whole block above
+  if (nb <= 32) {
+    if (threadIdx.x < 32) {
+      const double ta = warp_sum_strided(P.part, 2, (int)nb);
+      const double tb = warp_sum_strided(P.part + 1, 2, (int)nb);
+      if (threadIdx.x == 0) {
+        out[0] = ta;
+        out[1] = tb;
+      }
+    }
+    return true;
+  }
   const double ta = block_sum_strided(P.part, 2, (int)nb, sa);
   const double tb = block_sum_strided(P.part + 1, 2, (int)nb, sa);
   if (threadIdx.x == 0) {
