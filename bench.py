@@ -1106,12 +1106,13 @@ def main():
                      "iota_total": st.iota_total, "iota_total_mixed": stats_first[0].iota_total}
         # roofline of the dominant kernel (KP GEMM)
         achieved = gflops / (gms / 1000.0) / 1e12 if gms > 0 else None
+        src = "of measured" if "bf16_tflops_sustained" in peaks else "of fallback: 1700 TFLOP/s sustained bf16"
         if prec in (K.P_TF32X3, K.P_TF32X2):
             peak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
-            roof = {"bound": "tensor", "peak_note": "TF32 = measured sustained bf16 x 1.1/2.25 (of measured)"}
+            roof = {"bound": "tensor", "peak_note": "TF32 = sustained bf16 x 1.1/2.25 (%s)" % src}
         elif prec in (K.P_BF16X3, K.P_BF16X2):
             peak = peaks.get("bf16_tflops_sustained", 1700.0)
-            roof = {"bound": "tensor", "peak_note": "measured sustained bf16 (of measured)"}
+            roof = {"bound": "tensor", "peak_note": "sustained bf16 (%s)" % src}
         elif prec == K.P_FP32:
             peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             roof = {"bound": "alu", "peak_note": "FP32 FMA: 152 SM x 128 lanes x 2 x max SM clock"}
