@@ -59,13 +59,15 @@ def parse():
     ap.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
     ap.add_argument("--count", type=int, default=64, help="serving: requests")
     ap.add_argument("--sizes", default="128,256", help="serving: image sizes drawn uniformly")
+    ap.add_argument("--n", type=int, default=1024, help="single: image side")
     ap.add_argument("--workload", default="medium",
-                    choices=["medium", "batched96", "sweep", "direct", "tsvd", "dense_tsvd"],
+                    choices=["medium", "batched96", "sweep", "direct", "tsvd", "dense_tsvd", "single"],
                     help="medium: the headline batch; batched96: 96 uneven problems (n 64..384) in "
                          "one batched launch; sweep: 100 lambda values on one set of KP factors; "
                          "direct: split Bregman with the explicit A vs the KP sum on one request; "
                          "tsvd: the TSVD in single vs double precision, full vs one-sided reorthogonalisation; "
-                         "dense_tsvd: the TSVD of a general explicit operator (kp_build_dense)")
+                         "dense_tsvd: the TSVD of a general explicit operator (kp_build_dense); "
+                         "single: one serving-workload request of side --n alone (latency)")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: the timed steps only (no replay, e2e, plain or CPU legs), "
                          "with the library's host-driven loop (ncu cannot profile kernels inside "
@@ -851,6 +853,40 @@ def dense_tsvd_main(args):
           flush=True)
 
 
+def single_main(args):
+    """One request of the serving workload (side --n, k = 20, 31x31 PSF) alone: kp_build +
+    split Bregman (--outer steps) in the selected precision, device-timed; with --profile the
+    solve runs the host-driven loop (every kernel a plain launch) for ncu."""
+    import torch
+
+    from paper_2410_00233_gb300 import inputs as I
+    from paper_2410_00233_gb300 import kpsb as K
+
+    torch.cuda.set_device(0)
+    K.lib()
+    precs = {"fp64": K.P_FP64, "fp32": K.P_FP32, "tf32x3": K.P_TF32X3, "tf32x2": K.P_TF32X2,
+             "bf16x3": K.P_BF16X3, "bf16x2": K.P_BF16X2}
+    prec = precs[args.prec if args.prec != "auto" else "bf16x3"]
+    reqs, _ = serving_trace(K, I, torch, 7300 + args.n, 1, 1.0, sizes=(args.n,))
+    r = reqs[0]
+    kp = K.kp_build(r["psf"], args.n, K.BC_REFLEXIVE, 20, K.EGKB, seed=r["key"])
+    K.sb_solve(kp, r["b"], MU, LAM, r["tv"], 1, i_max=3, fixed_inner=True, prec=prec)  # warm-up
+    if args.profile:
+        K.kpsb_gemm_timing(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, st = K.sb_solve(kp, r["b"], MU, LAM, r["tv"], args.outer, prec=prec)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    if args.profile:
+        K.kpsb_gemm_timing(False)
+    print(json.dumps({"metric": "one request alone: split Bregman seconds", "value": t, "unit": "s",
+                      "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+                      "config": {"workload": "serving request, n=%d, k=20, %d outer" % (args.n, args.outer),
+                                 "kp_gemm": args.prec if args.prec != "auto" else "bf16x3"},
+                      "iota_total": st.iota_total, "isnr_db": _isnr(x, r["b"], r["xt"])}), flush=True)
+
+
 def main():
     args = parse()
     if args.cpu_worker > 0:
@@ -876,6 +912,9 @@ def main():
         return
     if args.workload == "dense_tsvd":
         dense_tsvd_main(args)
+        return
+    if args.workload == "single":
+        single_main(args)
         return
 
     import numpy as np
