@@ -1261,6 +1261,17 @@ int tc_plan_launches(const TCPlan* P) { return (P->ext_split ? 0 : 1) + (P->fuse
 
 static constexpr int S1_BN = 128, S1_STAGES = 3;
 static constexpr int S2_BN = 64, S2_STAGES = 4;
+// Stage 1 for n > 768: 256-column output tiles (one M = 128, N = 256 MMA per K step), half
+// the CTAs and twice the work per prologue and epilogue (measured at n = 1024: -4 % BF16x3,
+// -9 % TF32x2 per solve; slower at n = 512, where the CTAs no longer fill the GPU); the tile
+// width does not change any element's accumulation order, so the bits are those of the
+// 128-column tiles.
+#ifndef KPSB_S1_BN_LARGE
+#define KPSB_S1_BN_LARGE 256
+#endif
+static constexpr int S1L_BN = KPSB_S1_BN_LARGE;
+static constexpr int s1l_stages(int fpl) { return S1L_BN == 128 ? S1_STAGES : (fpl == 2 ? 2 : 3); }
+static inline bool s1_large(int n) { return n > 768; }
 
 template <int BN, int FPL>
 static kpsb_status prepare_fused() {
@@ -1350,7 +1361,7 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
   }
   cuuint64_t d1[4] = {(cuuint64_t)n, (cuuint64_t)n, 2, (cuuint64_t)k};
   cuuint64_t s1[3] = {es * l1, es * l1 * n, es * 2 * l1 * n};
-  KPSB_TRY(make_map(&J.m1B, t1, 4, d1, s1, S1_BN, bf));  // T1: {n, n, 2, k}
+  KPSB_TRY(make_map(&J.m1B, t1, 4, d1, s1, s1_large(n) ? S1L_BN : S1_BN, bf));  // T1: {n, n, 2, k}
   if (!bf && n % 128 == 0) {  // T1 with 64-, 32- and 128-row boxes (fused and resident kernels)
     KPSB_TRY(make_map(&J.m1F, t1, 4, d1, s1, 64));
     KPSB_TRY(make_map(&J.m1G, t1, 4, d1, s1, 32));
@@ -1465,6 +1476,10 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
   KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 2, true>()));
   KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 1, true>()));
   KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 1, true>()));
+  KPSB_TRY((prepare_gemm<S1L_BN, s1l_stages(2), 1, 2, false>()));
+  KPSB_TRY((prepare_gemm<S1L_BN, s1l_stages(1), 1, 1, false>()));
+  KPSB_TRY((prepare_gemm<S1L_BN, s1l_stages(2), 1, 2, true>()));
+  KPSB_TRY((prepare_gemm<S1L_BN, s1l_stages(1), 1, 1, true>()));
   KPSB_TRY((prepare_fused<FUSED_BN, 1>()));
   KPSB_TRY((prepare_fused<FUSED_BN, 2>()));
   KPSB_TRY((prepare_fused<32, 1>()));
@@ -1574,7 +1589,8 @@ static kpsb_status launch_gemm(const TCJob* jobs, int njobs, int n, int kmax, cu
 
 template <int FPL, bool BF>
 static kpsb_status launch_two_stage(const TCJob* jobs, int njobs, int n, int kmax, cudaStream_t st) {
-  KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, FPL, BF>(jobs, njobs, n, kmax, st)));
+  if (s1_large(n)) KPSB_TRY((launch_gemm<S1L_BN, s1l_stages(FPL), 1, FPL, BF>(jobs, njobs, n, kmax, st)));
+  else KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, FPL, BF>(jobs, njobs, n, kmax, st)));
   KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, FPL, BF>(jobs, njobs, n, kmax, st)));
   return KPSB_OK;
 }

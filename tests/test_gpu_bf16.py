@@ -51,7 +51,7 @@ def _op(Ax, Ay, sig, rnd=None):
     return O.KPSum(Ax=sx.astype(np.float64), Ay=np.asarray(Ay).astype(np.float64), sigma=np.ones(k))
 
 
-@pytest.mark.parametrize("n,k", [(64, 5), (100, 3), (128, 12), (200, 7), (256, 1), (384, 4)])
+@pytest.mark.parametrize("n,k", [(64, 5), (100, 3), (128, 12), (200, 7), (256, 1), (384, 4), (512, 3), (640, 2)])
 @pytest.mark.parametrize("transpose", [0, 1])
 def test_kp_apply_bf16_modes(n, k, transpose):
     need_gpu()
@@ -76,7 +76,7 @@ def test_kp_apply_bf16_modes(n, k, transpose):
     assert np.linalg.norm(y2 - ref32) / np.linalg.norm(ref32) < 1e-2
 
 
-@pytest.mark.parametrize("n,k", [(64, 5), (100, 3), (200, 7)])
+@pytest.mark.parametrize("n,k", [(64, 5), (100, 3), (200, 7), (520, 2), (1024, 2)])
 @pytest.mark.parametrize("transpose", [0, 1])
 def test_kp_apply_tf32_modes_at_masked_sizes(n, k, transpose):
     need_gpu()

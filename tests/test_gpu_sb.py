@@ -241,7 +241,7 @@ def test_resident_fused_and_two_stage_tensor_core_paths_agree(prec_name, transpo
 
     prec = getattr(K, prec_name)
     tol = 1e-4 if prec == K.P_TF32X3 else 2e-3
-    for n, k in ((128, 7), (128, 1), (128, 30), (256, 3)):
+    for n, k in ((128, 7), (128, 1), (128, 30), (256, 3), (512, 4)):
         Ax, Ay, sig = _rand_factors(n, k, 11 * n + k)
         X = I.rng(8 + k).standard_normal((n, n))
         op = _oracle_op(Ax, Ay, sig)
