@@ -1325,9 +1325,6 @@ static bool variant_ok(int v, int n, int prec) {
 // Fused kernel where its TMEM fits (R + 2) x BN columns: n <= 768 with BN = 64.
 static bool fused_ok(int n) { return n % 128 == 0 && (n / 128 + 2) * FUSED_BN <= 512 && !getenv("KPSB_TWO_STAGE"); }
 
-int tc_fused_tiles(int n, int prec) {
-  return (tc_supported(n, prec) && !prec_bf16(prec) && fused_ok(n)) ? n / FUSED_BN : 0;
-}
 
 template <int BN, int STAGES, int STAGE, int FPL, bool BF>
 static kpsb_status prepare_gemm() {
@@ -1464,9 +1461,10 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
                            int prec, cudaStream_t st, TCPlan** out) {
   KPSB_REQUIRE(tc_supported(n, prec), "no tensor-core kernel for n = %d, precision %d", n, prec);
   const bool bf = prec_bf16(prec);
-  // a caller's split planes are TF32 planes with leading dimension n (fused CGLS path)
+  // a caller's split planes have leading dimension n and the plan's element type (the split
+  // Bregman vector kernels write them in 32 x 32 tiles)
   for (int p = 0; p < njobs; ++p)
-    KPSB_REQUIRE(!fwd_h[p].xt_ext || (!bf && n % 128 == 0), "caller-split planes need a TF32 mode and n %% 128 == 0");
+    KPSB_REQUIRE(!fwd_h[p].xt_ext || n % 32 == 0, "caller-split planes need n %% 32 == 0 (n = %d)", n);
   // kernel attributes are set here, before any graph capture that replays the applies
   KPSB_TRY((prepare_gemm<S1_BN, S1_STAGES, 1, 2, false>()));
   KPSB_TRY((prepare_gemm<S2_BN, S2_STAGES, 2, 2, false>()));

@@ -94,9 +94,11 @@ struct SBProb {
   SBScal* sc;
   double* part;           // reduction partials
   unsigned int* counter;  // last-block counter
-  float* xt;              // split TF32 planes of the next KP apply's input (tensor-core path)
-  float* z1f;             // FP32 KP-apply results (fused tensor-core path), else null
+  float* xt;              // split planes of the next KP apply's input (tensor-core path):
+                          // TF32 values in FP32 storage, or BF16 when xt_bf16
+  float* z1f;             // FP32 KP-apply results (tensor-core path with split planes), else null
   float* f1f;
+  int xt_bf16;            // the planes hold BF16 (BF16X3 / BF16X2 applies)
 };
 // Device-resident state of one problem; persists across sb_advance calls.
 struct SBState {
@@ -188,8 +190,6 @@ bool tc_plan_fused(const TCPlan* P);
 // Kernel launches of one apply of the plan (split kernel when not supplied, then one fused
 // launch or the two-stage pair).
 int tc_plan_launches(const TCPlan* P);
-// Column tiles of the fused kernel for size n, 0 if n is not handled by it.
-int tc_fused_tiles(int n, int prec);
 void tc_plan_free(TCPlan* P, cudaStream_t st);
 kpsb_status tc_check_error();
 kpsb_status tc_apply_batch(kpsb_kp** kps, const KPJob* jobs_d, const KPJob* jobs_h, int njobs,

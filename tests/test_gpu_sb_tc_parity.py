@@ -133,3 +133,23 @@ def test_fp64_sb_matches_oracle_at_n128(iso):
         assert np.abs(x - ref.x).max() <= 1e-10 * np.abs(ref.x).max()
         assert st.iota_total == iters * i_max
         assert abs(st.rc_sb - ref.rc_sb) <= 1e-8 * ref.rc_sb
+
+
+@pytest.mark.parametrize("prec_name", ["P_TF32X2", "P_BF16X3"])
+def test_tensor_core_sb_matches_oracle_elementwise_n1024(prec_name):
+    """The largest serving size: 256-column stage-1 tiles, split planes written by the vector
+    kernels, FP32 apply results; same bounds as above."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    n = 1024
+    x_true, b, Ax, Ay, sig = _problem(n, 1900)
+    kp = K.kp_from_factors(Ax, Ay, sig)
+    op = _rounded_operator(Ax, Ay, sig, prec_name)
+    x, st = K.sb_solve(kp, b, MU, LAM, K.ISO, 2, i_max=6, fixed_inner=True, prec=getattr(K, prec_name))
+    ref = O.split_bregman(lambda X: O.kp_apply(op, X), lambda Y: O.kp_apply_t(op, Y), b, MU, LAM, BETA, True,
+                          2, i_max=6, fixed_inner=True)
+    b_max, b_fro = _BOUNDS[prec_name]
+    err_max = np.abs(x - ref.x).max() / np.abs(ref.x).max()
+    err_fro = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+    assert err_max < b_max and err_fro < b_fro, (err_max, err_fro)
