@@ -1308,9 +1308,9 @@ static kpsb_status launch_resident(const TCJob* jobs, int njobs, int* queue, cud
   return KPSB_OK;
 }
 
-// n = 128 runs the resident kernel (KPSB_FUSED_TILED=1 selects the tiled fused kernel).  The
-// fused and resident kernels are TF32 kernels for n a multiple of 128; the two-stage kernel
-// runs every tensor-core precision and any n.
+// Valid variants per size and precision (the autotuner picks among them; KPSB_TC_VARIANT pins
+// one).  The fused and resident kernels are TF32 kernels for n a multiple of 128; the
+// two-stage kernel runs every tensor-core precision and any n.
 static bool variant_ok(int v, int n, int prec) {
   const bool tf = !prec_bf16(prec) && n % 128 == 0;
   switch (v) {
@@ -1323,7 +1323,7 @@ static bool variant_ok(int v, int n, int prec) {
 }
 
 // Fused kernel where its TMEM fits (R + 2) x BN columns: n <= 768 with BN = 64.
-static bool fused_ok(int n) { return n % 128 == 0 && (n / 128 + 2) * FUSED_BN <= 512 && !getenv("KPSB_TWO_STAGE"); }
+static bool fused_ok(int n) { return n % 128 == 0 && (n / 128 + 2) * FUSED_BN <= 512; }
 
 
 template <int BN, int STAGES, int STAGE, int FPL, bool BF>
@@ -1391,12 +1391,10 @@ static kpsb_status launch_variant(const TCPlan* P, const TCJob* jobs, int njobs,
 
 static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStream_t st) {
   const int n = P->n;
-  if (getenv("KPSB_TWO_STAGE")) { P->variant = TCV_TWO_STAGE; return KPSB_OK; }
   if (const char* f = getenv("KPSB_TC_VARIANT")) {
     const int v = atoi(f);
     if (variant_ok(v, n, P->prec)) { P->variant = v; return KPSB_OK; }
   }
-  if (n == 128 && !P->bf && getenv("KPSB_FUSED_TILED")) { P->variant = TCV_FUSED64; return KPSB_OK; }
   std::vector<int> cand;
   for (int v = 0; v < TCV_COUNT; ++v)
     if (variant_ok(v, n, P->prec)) cand.push_back(v);

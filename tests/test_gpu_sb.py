@@ -249,8 +249,8 @@ def test_resident_fused_and_two_stage_tensor_core_paths_agree(prec_name, transpo
         ys = {}
         # default = the autotuned variant; KPSB_TC_VARIANT forces one (0 two-stage, 1 fused
         # BN 64, 2 fused BN 32, 3 resident n = 128)
-        for name, env, val in (("default", None, None), ("tiled", "KPSB_FUSED_TILED", "1"),
-                               ("two_stage", "KPSB_TWO_STAGE", "1"), ("fused64", "KPSB_TC_VARIANT", "1"),
+        for name, env, val in (("default", None, None), ("resident", "KPSB_TC_VARIANT", "3"),
+                               ("two_stage", "KPSB_TC_VARIANT", "0"), ("fused64", "KPSB_TC_VARIANT", "1"),
                                ("fused32", "KPSB_TC_VARIANT", "2"), ("v0", "KPSB_TC_VARIANT", "0")):
             if env:
                 monkeypatch.setenv(env, val)
