@@ -98,6 +98,8 @@ struct SBProb {
                           // TF32 values in FP32 storage, or BF16 when xt_bf16
   float* z1f;             // FP32 KP-apply results (tensor-core path with split planes), else null
   float* f1f;
+  float* wf;              // FP32 value of the CGLS direction w, the vector the forward apply
+                          // sees (tensor-core path with split planes), else null
   int xt_bf16;            // the planes hold BF16 (BF16X3 / BF16X2 applies)
 };
 // Device-resident state of one problem; persists across sb_advance calls.

@@ -367,9 +367,18 @@ __device__ __forceinline__ void store_xt_tile(float* __restrict__ xt, int n, int
 
 // Writes the TF32 hi / lo split of v into the tile; returns v rounded to FP32.
 // KPSB_SPLIT_INT_ROUND 1 rounds v to FP32 on the integer pipes (same bits as the conversion
-// instruction, which issues to the FP64 pipe).
+// instruction, which issues to the FP64 pipe); 0 uses the conversion instruction.
 #ifndef KPSB_SPLIT_INT_ROUND
-#define KPSB_SPLIT_INT_ROUND 0
+#define KPSB_SPLIT_INT_ROUND 1
+#endif
+// KPSB_X_INT_WIDEN 1: the x update widens the FP32 apply result on the integer pipes.
+#ifndef KPSB_X_INT_WIDEN
+#define KPSB_X_INT_WIDEN 1
+#endif
+// KPSB_X_NORM_F32 1: ||x||^2 of the stop test from the FP32 rounding of x, summed in FP32 per
+// thread (integer-pipe rounding, one FP32 FMA instead of an FP64 FMA per element).
+#ifndef KPSB_X_NORM_F32
+#define KPSB_X_NORM_F32 1
 #endif
 // With bf the split is BF16 (hi = bf16(f), lo = bf16(f - hi), round to nearest even), the
 // same split the two-stage kernel's own split applies, held exactly in the FP32 tile.
@@ -415,7 +424,7 @@ __global__ void SB_BOUNDS sb_outer_init_tc_kernel(const SBProb* __restrict__ pro
 }
 
 // w = f + delta w (step 10; delta from the f kernel), init: w = f (step 2, w not read), and
-// the planes of w for the next forward apply.
+// the planes and the FP32 value w_f of w for the next forward apply and ||z||^2.
 __global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
   (void)N; (void)e_hi;
@@ -430,6 +439,7 @@ __global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int i
     const double w = init ? P.f[e] : fma(dl, P.w[e], P.f[e]);
     P.w[e] = w;
     const float wf = put_split(th, tl, ly + 8 * j, lx, w, P.xt_bf16);
+    P.wf[e] = wf;
     wwf = fmaf(wf, wf, wwf);
   }
   store_xt_tile(P.xt, n, tr, tcol, th, tl, lx, ly, P.xt_bf16);
@@ -437,6 +447,42 @@ __global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int i
   double tot[2];
   if (!prob_reduce2(P, (double)wwf, 0.0, tot)) return;
   if (threadIdx.x == 0) P.sc->ww = tot[0];
+}
+
+// ||z||^2 with z = Ahat w_f (steps 3-4) on the tensor-core path: w_f = fl32(w) is the vector
+// the forward apply saw and z1 = A_k w_f its FP32 result, so both sums,
+// |z|^2 = mu |z1|^2 + (lambda/2)^2 |raw D w_f|^2, are sums of squares of FP32 values: taken
+// in FP32 per thread (SB_EPT elements), the partials in FP64.  No FP64 arithmetic per element.
+__global__ void SB_BOUNDS sb_zz_tc_kernel(const SBProb* __restrict__ probs) {
+  SB_PROLOGUE(P.sc->active)
+  float sz = 0.0f, sd = 0.0f;
+  SB_FOR_RC {
+    const int r = r_, c = c_;
+    const float z = P.z1f[e];
+    sz = fmaf(z, z, sz);
+    const float w = P.wf[e];
+    if (c < n - 1) {
+      const float d = w - P.wf[e + n];
+      sd = fmaf(d, d, sd);
+    }
+    if (r < n - 1) {
+      const float d = w - P.wf[e + 1];
+      sd = fmaf(d, d, sd);
+    }
+  }
+  double tot[2];
+  if (!prob_reduce2(P, (double)sz, (double)sd, tot)) return;
+  if (threadIdx.x == 0) {
+    SBScal* s = P.sc;
+    const double hl = 0.5 * P.lam;
+    const double zz = fma(hl * hl, tot[1], P.mu * tot[0]);
+    if (zz > 0.0) {
+      s->step = s->tau / zz;
+    } else {
+      s->step = 0.0;
+      s->active = 0;
+    }
+  }
 }
 
 // x += mu w, r -= mu z (steps 5-6, mu from the zz kernel); RC_CGLS (5.1) and the stop
@@ -447,7 +493,12 @@ __global__ void SB_BOUNDS_X sb_x_tc_kernel(const SBProb* __restrict__ probs) {
   __shared__ float th[32][33], tl[32][33];
   const double mu = P.sc->step;
   const double c1 = -mu * P.sqrt_mu, c2 = -mu * (0.5 * P.lam);  // r -= mu z, one FMA each
-  double sx = 0.0;  // ||w||^2 for RC_CGLS comes from the w kernel (sc->ww)
+  // ||w||^2 for RC_CGLS comes from the w kernel (sc->ww)
+#if KPSB_X_NORM_F32
+  float sxf = 0.0f;
+#else
+  double sx = 0.0;
+#endif
   SB_TILES_BEGIN
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -456,17 +507,31 @@ __global__ void SB_BOUNDS_X sb_x_tc_kernel(const SBProb* __restrict__ probs) {
     const double w = P.w[e];
     const double xn = fma(mu, w, P.x[e]);
     P.x[e] = xn;
-    const double r1 = fma(c1, (double)P.z1f[e], P.r1[e]);
+#if KPSB_X_INT_WIDEN
+    const double z1 = f2d_bits(P.z1f[e]);
+#else
+    const double z1 = (double)P.z1f[e];
+#endif
+    const double r1 = fma(c1, z1, P.r1[e]);
     P.r1[e] = r1;
     if (c < n - 1) P.r2[e] = fma(c2, w - P.w[e + n], P.r2[e]);
     if (r < n - 1) P.r3[e] = fma(c2, w - P.w[e + 1], P.r3[e]);
+#if KPSB_X_NORM_F32
+    const float xf = d2f_rn_bits(xn);
+    sxf = fmaf(xf, xf, sxf);
+#else
     sx = fma(xn, xn, sx);
+#endif
     put_split(th, tl, ly + 8 * j, lx, r1, P.xt_bf16);
   }
   store_xt_tile(P.xt, n, tr, tcol, th, tl, lx, ly, P.xt_bf16);
   SB_TILES_END
   double tot[2];
+#if KPSB_X_NORM_F32
+  if (!prob_reduce2(P, (double)sxf, 0.0, tot)) return;
+#else
   if (!prob_reduce2(P, sx, 0.0, tot)) return;
+#endif
   if (threadIdx.x == 0) {
     SBScal* s = P.sc;
     const double xn = sqrt(tot[0]);
@@ -637,7 +702,7 @@ size_t sb_state_bytes(int n, int k, int prec) {
   const size_t zbytes = tc_supported(n, gp) ? 0 : a256(kp_z_bytes(n, k, gp));
   size_t tc_ws = tc_supported(n, gp) ? a256(tc_plan_ws_bytes(n, k, gp)) : 0;
   return a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
-         a256(sizeof(double) * sb_blocks(n) * 2) + 256 + tc_ws + a256(sizeof(float) * 4 * N) + 256;
+         a256(sizeof(double) * sb_blocks(n) * 2) + 256 + tc_ws + a256(sizeof(float) * 5 * N) + 256;
 }
 
 kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* x_dev, double mu,
@@ -656,7 +721,7 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   // tensor-core applies with the split planes written by the vector kernels (32 x 32 tiles)
   // and FP32 results: any tensor-core precision, n a multiple of 32
   const bool fused = !dense && tc_supported(n, S->gemm_prec) && n % 32 == 0;
-  const size_t xtbytes = fused ? a256(sizeof(float) * 4 * N) : 0;  // Xt planes + z1f + f1f
+  const size_t xtbytes = fused ? a256(sizeof(float) * 5 * N) : 0;  // Xt planes + z1f + f1f + wf
   S->bytes = a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
              a256(sizeof(double) * sb_blocks(n) * 2) + 256 + xtbytes;
   KPSB_TRY_CUDA(cudaMallocAsync((void**)&S->mem, S->bytes, st));
@@ -692,6 +757,7 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   P.xt_bf16 = S->gemm_prec == KPSB_P_BF16X3 || S->gemm_prec == KPSB_P_BF16X2;
   P.z1f = fused ? P.xt + 2 * N : nullptr;
   P.f1f = fused ? P.xt + 3 * N : nullptr;
+  P.wf = fused ? P.xt + 4 * N : nullptr;
   // the block comes from the stream-ordered pool with whatever its last user left: clear it
   // all, so that no read of a not-yet-written vector can depend on that history
   KPSB_TRY_CUDA(cudaMemsetAsync(S->mem, 0, S->bytes, st));
@@ -845,7 +911,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     auto cgls_iter = [&](cudaStream_t sx) -> kpsb_status {
       if (fz) {
         KPSB_TRY(kp_apply_on(0, sx));
-        SB_LAUNCH(TIMER_SB_ZZ, sb_cgls_zz_kernel, dprobs);
+        SB_LAUNCH(TIMER_SB_ZZ, sb_zz_tc_kernel, dprobs);
         SB_LAUNCH(TIMER_SB_X, sb_x_tc_kernel, dprobs);
         KPSB_TRY(kp_apply_on(1, sx));
         SB_LAUNCH(TIMER_SB_F, sb_cgls_f_kernel, dprobs, 0);
