@@ -1029,7 +1029,7 @@ def main():
     while bucket < B:
         bucket <<= 1
     for t in K.kpsb_tuned_variants():
-        if t["n"] == N_IMG and t["prec"] == prec and t["bucket"] == bucket:
+        if t["n"] == N_IMG and t["prec"] == prec and t["bucket"] == bucket and not t["shared"]:
             replay_variant = t["variant"]
     # DRAM traffic per launch of that kernel: ncu captures (dram__bytes_read.sum +
     # dram__bytes_write.sum) of each variant on this workload (256 requests, one part, every

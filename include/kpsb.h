@@ -365,8 +365,9 @@ kpsb_status kpsb_conversion_check(unsigned long long n_random, unsigned long lon
                                   unsigned long long* mismatches);
 
 /* The tensor-core apply variants the autotuner has chosen in this process (every variant
- * gives the same bits; the choice only moves time).  Writes up to max_rows rows of 6 ints
+ * gives the same bits; the choice only moves time).  Writes up to max_rows rows of 7 ints
  * (n, precision, k_max, batch-size bucket (next power of two), caller-split planes 0/1,
+ * shared SMs 0/1 (the batch ran as concurrent parts: variants ranked by SM time),
  * variant: 0 two-stage, 1 fused 64-column, 2 fused 32-column, 3 resident n = 128) to rows
  * (host, may be NULL) and returns the number of choices made. */
 int kpsb_tuned_variants(int* rows, int max_rows);

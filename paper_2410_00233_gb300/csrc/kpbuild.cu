@@ -34,15 +34,6 @@ struct EgkbState {
 // Device address of a field of the device-resident state (no host dereference).
 #define ST_FIELD(st, f) ((decltype(&((EgkbState*)0)->f))((char*)(st) + offsetof(EgkbState, f)))
 
-struct EgkbParams {
-  int k_fixed;      // > 0: fixed rank
-  int k_cap;
-  int p;
-  int k_min;
-  double tau;       // relative tolerance (auto mode)
-  double bd_tol;    // breakdown tolerance relative to bnorm
-};
-
 // Decide after t_j (s-phase of step j).  j = 1 is the start vector.
 __global__ void egkb_after_t(EgkbState* st, EgkbParams P, int j) {
   if (st->gate[2 * j]) return;
@@ -428,7 +419,7 @@ static kpsb_status egkb_run(BuildWork<T>& w, int n, int s0, int s1, int bc, cons
   return KPSB_OK;
 }
 
-static kpsb_status handle_alloc(kpsb_kp** out, int n, int k, int kpsize) {
+kpsb_status kp_handle_alloc(kpsb_kp** out, int n, int k, int kpsize) {
   kpsb_kp* h = new (std::nothrow) kpsb_kp();
   if (!h) {
     set_error("out of host memory");
@@ -451,9 +442,10 @@ static kpsb_status handle_alloc(kpsb_kp** out, int n, int k, int kpsize) {
   return KPSB_OK;
 }
 
+// Rank rule and breakdown tolerance of one EGKB build (k: the fixed rank, or the cap in the
+// automatic mode tau > 0).
 template <typename T>
-static kpsb_status build_egkb(const float* A32, const T* psf_host, int s0, int s1, int n, int bc, int k,
-                              double tau, const kpsb_build_opts& o, cudaStream_t st, kpsb_kp** out) {
+static EgkbParams egkb_params(int k, double tau, const kpsb_build_opts& o) {
   EgkbParams P;
   P.k_fixed = tau > 0.0 ? 0 : k;
   P.k_cap = tau > 0.0 ? std::min(k, K_CAP) : k;
@@ -461,6 +453,13 @@ static kpsb_status build_egkb(const float* A32, const T* psf_host, int s0, int s
   P.k_min = o.k_min;
   P.tau = tau;
   P.bd_tol = 30.0 * eps_of<T>();
+  return P;
+}
+
+template <typename T>
+static kpsb_status build_egkb(const float* A32, const T* psf_host, int s0, int s1, int n, int bc, int k,
+                              double tau, const kpsb_build_opts& o, cudaStream_t st, kpsb_kp** out) {
+  const EgkbParams P = egkb_params<T>(k, tau, o);
   const int kpmax = P.k_cap + P.p;
   KPSB_REQUIRE(kpmax <= KP_MAX, "k + p = %d exceeds %d", kpmax, KP_MAX);
   const long long N = (long long)n * n;
@@ -498,7 +497,7 @@ static kpsb_status build_egkb(const float* A32, const T* psf_host, int s0, int s
     s = la_small_svd(dC, m, m, nc, dU, dSg, dV, nullptr, st);
     if (s) break;
     kpsb_kp* h = nullptr;
-    s = handle_alloc(&h, n, kk, nq);
+    s = kp_handle_alloc(&h, n, kk, nq);
     if (s) break;
     // Ritz vectors (steps 16-17): U = S_{nq+1} Uc[:, :k], V = Q_nq Vc[:, :k]
     s = la_matmul_small(w.S, (int)N, N, m, dU, m, kk, h->Ax, (int)N, st);
@@ -627,7 +626,7 @@ static kpsb_status build_rsvd(const float* A32, const T* psf_host, int s0, int s
       break;
     }
     kpsb_kp* h = nullptr;
-    s = handle_alloc(&h, n, kk, kp);
+    s = kp_handle_alloc(&h, n, kk, kp);
     if (s) break;
     s = la_matmul_small(Y, (int)N, N, kp, W, kp, kk, h->Ax, (int)N, st);  // U = Q U_H
     if (!s) s = la_matmul_small(Ht, (int)N, N, kp, T2, kp, kk, h->Ay, (int)N, st);
@@ -653,20 +652,16 @@ static kpsb_status build_rsvd(const float* A32, const T* psf_host, int s0, int s
 
 using namespace kpsb;
 
-// ---- C ABI ----------------------------------------------------------------------------------------
-extern "C" kpsb_status kp_build(const double* psf, int s0, int s1, int n, int bc, double rank_or_tol,
-                                int method, const kpsb_build_opts* opts, kpsb_kp_t* out) {
-  clear_error();
-  KPSB_REQUIRE(psf && out, "null pointer");
-  *out = nullptr;
+// Checks a build request and fills the option defaults (kp_build and kp_build_batched).
+static kpsb_status build_args(const double* psf, int s0, int s1, int n, int bc, double rank_or_tol, int method,
+                              const kpsb_build_opts* opts, kpsb_build_opts& o, int& k, double& tau) {
+  KPSB_REQUIRE(psf, "null pointer");
   KPSB_TRY(ra_check(s0, s1, n, bc));
   KPSB_REQUIRE(method == KPSB_EGKB || method == KPSB_RSVD, "unknown method %d", method);
   KPSB_REQUIRE(rank_or_tol > 0.0 && isfinite(rank_or_tol), "rank_or_tol must be > 0");
-  kpsb_build_opts o;
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  double tau = 0.0;
-  int k;
+  tau = 0.0;
   if (rank_or_tol >= 1.0) {
     k = (int)rank_or_tol;
   } else {
@@ -679,7 +674,51 @@ extern "C" kpsb_status kp_build(const double* psf, int s0, int s1, int n, int bc
   if (o.power_iters <= 0) o.power_iters = 1;
   if (o.k_min <= 0) o.k_min = 3;
   KPSB_REQUIRE(std::min(k, K_CAP) + o.p <= KP_MAX || tau == 0.0, "k_cap + p exceeds %d", KP_MAX);
+  return KPSB_OK;
+}
+
+// Single-precision EGKB on small images runs as one thread block per problem (egkb_block.cu),
+// alone and in batches alike; KPSB_EGKB_BLOCK=0 selects the multi-kernel path instead.
+static bool use_block_path(int n, int s0, int s1, int method, const kpsb_build_opts& o) {
+  if (method != KPSB_EGKB || o.fp64) return false;
+  const char* f = getenv("KPSB_EGKB_BLOCK");
+  if (f && f[0] == '0') return false;
+  return eb_eligible(n, s0, s1);
+}
+
+static EbProblem eb_problem(const double* psf, int s0, int s1, int n, int bc, int k, double tau,
+                            const kpsb_build_opts& o) {
+  EbProblem e;
+  e.psf = psf;
+  e.s0 = s0;
+  e.s1 = s1;
+  e.n = n;
+  e.bc = bc;
+  e.P = egkb_params<float>(k, tau, o);
+  e.full_reorth = !o.one_sided;
+  e.kpmax = e.P.k_cap + e.P.p;
+  e.start_host = o.start_host;
+  e.seed = o.seed;
+  return e;
+}
+
+// ---- C ABI ----------------------------------------------------------------------------------------
+extern "C" kpsb_status kp_build(const double* psf, int s0, int s1, int n, int bc, double rank_or_tol,
+                                int method, const kpsb_build_opts* opts, kpsb_kp_t* out) {
+  clear_error();
+  KPSB_REQUIRE(psf && out, "null pointer");
+  *out = nullptr;
+  kpsb_build_opts o;
+  int k = 0;
+  double tau = 0.0;
+  KPSB_TRY(build_args(psf, s0, s1, n, bc, rank_or_tol, method, opts, o, k, tau));
   cudaStream_t st = (cudaStream_t)o.stream;
+  if (use_block_path(n, s0, s1, method, o)) {
+    const EbProblem ep = eb_problem(psf, s0, s1, n, bc, k, tau, o);
+    kpsb_status ps = KPSB_OK;
+    std::string msg;
+    return egkb_block_build(&ep, 1, out, &ps, &msg, st);
+  }
   if (o.fp64) {  // the TSVD in FP64 throughout (PSF, bases, R(A) products)
     std::vector<double> pd(psf, psf + (size_t)s0 * s1);
     if (method == KPSB_EGKB) return build_egkb<double>(nullptr, pd.data(), s0, s1, n, bc, k, tau, o, st, out);
@@ -770,7 +809,7 @@ extern "C" kpsb_status kp_from_factors(int n, int k, const float* Ax, const floa
   KPSB_REQUIRE(Ax && Ay && sigma && out, "null pointer");
   KPSB_REQUIRE(n >= 2 && n <= KPSB_MAX_N && k >= 1 && k <= KP_MAX, "bad sizes n=%d k=%d", n, k);
   kpsb_kp* h = nullptr;
-  KPSB_TRY(handle_alloc(&h, n, k, k));
+  KPSB_TRY(kp_handle_alloc(&h, n, k, k));
   size_t bytes = sizeof(float) * (size_t)n * n * k;
   cudaError_t e = cudaMemcpy(h->Ax, Ax, bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->Ay, Ay, bytes, cudaMemcpyHostToDevice);
@@ -799,22 +838,64 @@ extern "C" kpsb_status kp_build_batched(int count, const kpsb_problem* probs, kp
   if (count == 0) return KPSB_OK;
   int dev = 0;
   KPSB_TRY_CUDA(cudaGetDevice(&dev));
-  // Problems are independent: up to 8 host threads, each with its own stream, so the
-  // builds (and their few host synchronisations) overlap on the device.
-  const int NT = std::min(count, 8);
   std::vector<kpsb_status> st(count, KPSB_OK);
   std::vector<std::string> msg(count);
+  // Problems of the one-block path share two launches per chunk; the others run through
+  // kp_build on up to 8 host threads, each with its own stream, so their builds (and their few
+  // host synchronisations) overlap on the device.
+  std::vector<int> blk, rest;
+  std::vector<EbProblem> ebp;
+  for (int i = 0; i < count; ++i) {
+    outs[i] = nullptr;
+    kpsb_build_opts o;
+    int k = 0;
+    double tau = 0.0;
+    const kpsb_problem& q = probs[i];
+    st[i] = build_args(q.psf, q.s0, q.s1, q.n, q.bc, q.rank_or_tol, q.method, &q.opts, o, k, tau);
+    if (st[i] != KPSB_OK) {
+      msg[i] = kpsb_last_error();
+      continue;
+    }
+    if (use_block_path(q.n, q.s0, q.s1, q.method, o)) {
+      blk.push_back(i);
+      ebp.push_back(eb_problem(q.psf, q.s0, q.s1, q.n, q.bc, k, tau, o));
+    } else {
+      rest.push_back(i);
+    }
+  }
+  if (!blk.empty()) {
+    cudaStream_t s = nullptr;
+    KPSB_TRY_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    constexpr int CHUNK = 256;  // bounds the bases held at once (about 5 MB per problem at n = 128)
+    for (size_t c0 = 0; c0 < blk.size(); c0 += CHUNK) {
+      const int cnt = (int)std::min<size_t>(CHUNK, blk.size() - c0);
+      std::vector<kpsb_kp_t> o2(cnt, nullptr);
+      std::vector<kpsb_status> s2(cnt, KPSB_OK);
+      std::vector<std::string> m2(cnt);
+      const kpsb_status sc = egkb_block_build(ebp.data() + c0, cnt, o2.data(), s2.data(), m2.data(), s);
+      const std::string chunk_msg = sc != KPSB_OK ? kpsb_last_error() : "";
+      for (int u = 0; u < cnt; ++u) {
+        const int i = blk[c0 + u];
+        outs[i] = o2[u];
+        st[i] = s2[u];
+        if (s2[u] != KPSB_OK) msg[i] = m2[u].empty() ? chunk_msg : m2[u];
+      }
+    }
+    cudaStreamDestroy(s);
+  }
+  const int NR = (int)rest.size();
+  const int NT = std::min(NR, 8);
   auto worker = [&](int t) {
     cudaSetDevice(dev);
     cudaStream_t s = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-      for (int i = t; i < count; i += NT) { st[i] = KPSB_ECUDA; msg[i] = "stream creation failed"; }
+      for (int u = t; u < NR; u += NT) { st[rest[u]] = KPSB_ECUDA; msg[rest[u]] = "stream creation failed"; }
       return;
     }
-    for (int i = t; i < count; i += NT) {
+    for (int u = t; u < NR; u += NT) {
+      const int i = rest[u];
       kpsb_build_opts o = probs[i].opts;
       o.stream = s;
-      outs[i] = nullptr;
       st[i] = kp_build(probs[i].psf, probs[i].s0, probs[i].s1, probs[i].n, probs[i].bc,
                        probs[i].rank_or_tol, probs[i].method, &o, &outs[i]);
       if (st[i] != KPSB_OK) msg[i] = kpsb_last_error();

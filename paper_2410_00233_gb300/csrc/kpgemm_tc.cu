@@ -975,8 +975,8 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
   unsigned char* ring = smem + C::X_BYTES;
   uint64_t* full = (uint64_t*)(ring + STAGES * C::SLOT);
   uint64_t* empty = full + STAGES;
-  uint64_t* x_full = empty + STAGES;
-  uint64_t* x_free = x_full + 1;
+  uint64_t* x_full = empty + STAGES;  // [4]: K slice kb of the iterate (hi and lo planes) loaded
+  uint64_t* x_free = x_full + 4;
   uint64_t* d1_full = x_free + 1;
   uint64_t* d1_free = d1_full + 1;
   uint64_t* z_full = d1_free + 1;
@@ -997,7 +997,7 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
       mbar_init(&empty[q], 1);
     }
     for (int q = 0; q < 4; ++q) mbar_init(&pq[q], 1);
-    mbar_init(x_full, 1);
+    for (int q = 0; q < 4; ++q) mbar_init(&x_full[q], 1);
     mbar_init(x_free, 1);
     mbar_init(d1_full, 1);
     mbar_init(d1_free, 4);
@@ -1050,10 +1050,9 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)&J.m2A) : "memory");
       // the iterate buffer is free once the previous problem's stage-1 MMAs have completed
       if (j > 0 && !fwait(x_free, (j - 1) & 1, s_fail)) { ok = false; break; }
-      mbar_expect_tx(x_full, C::X_BYTES);
-      for (int pl = 0; pl < 2; ++pl)
-        for (int kb = 0; kb < 4; ++kb) tma_load_3d(xs + (pl * 4 + kb) * C::TILE, &J.m1A, x_full, kb * 32, 0, pl);
-      // slots in consumption order: S1(0), then S1(i + 1), S2(i) for every i
+      // slots in consumption order: S1(0), then S1(i + 1), S2(i) for every i; each K slice
+      // of the iterate is requested just before the S1(0) table slice it meets, so the first
+      // MMAs start once 32 KB of the iterate has landed
       for (int v = -1; v < k && ok; ++v) {
         const int i1 = v + 1;
         for (int part = 0; part < 2 && ok; ++part) {
@@ -1061,6 +1060,11 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
           if (s1 && i1 >= k) continue;
           if (!s1 && v < 0) continue;
           for (int kb = 0; kb < 4; ++kb, ++si) {
+            if (v < 0) {
+              mbar_expect_tx(&x_full[kb], 2 * C::TILE);
+              for (int pl = 0; pl < 2; ++pl)
+                tma_load_3d(xs + (pl * 4 + kb) * C::TILE, &J.m1A, &x_full[kb], kb * 32, 0, pl);
+            }
             const int q = si % STAGES, round = si / STAGES;
             if (round > 0 && !fwait(&empty[q], (round - 1) & 1, s_fail)) { ok = false; break; }
             unsigned char* st = ring + q * C::SLOT;
@@ -1078,8 +1082,9 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
     int si = 0, g = 0, j = 0;  // ring slot, CTA-wide term, problem
     bool ok = true;
     const uint32_t x_hi = smem_u32(xs), x_lo = x_hi + 4 * C::TILE;
-    // S1 of CTA-wide term gi: D1 = T1 Xt^T, products T1hi*Xlo, T1lo*Xhi, T1hi*Xhi
-    auto stage1 = [&](int gi) -> bool {
+    // S1 of CTA-wide term gi: D1 = T1 Xt^T, products T1hi*Xlo, T1lo*Xhi, T1hi*Xhi; xw: the
+    // problem's first term, which also waits for each K slice of the iterate
+    auto stage1 = [&](int gi, bool xw) -> bool {
       if (gi >= 1) {
         if (!fwait(d1_free, (gi - 1) & 1, s_fail)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1087,6 +1092,7 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
       for (int kb = 0; kb < 4; ++kb, ++si) {
         const int q = si % STAGES, round = si / STAGES;
         if (!fwait(&full[q], round & 1, s_fail)) return false;
+        if (xw && !fwait(&x_full[kb], j & 1, s_fail)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t t_hi = smem_u32(ring + q * C::SLOT), t_lo = t_hi + (FPL == 2 ? C::TILE : 0);
         const uint32_t xh = x_hi + kb * C::TILE, xl = x_lo + kb * C::TILE;
@@ -1132,12 +1138,11 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
       if (p < 0) break;
       const TCJob& J = jobs[p];
       const int k = J.k;
-      ok = fwait(x_full, j & 1, s_fail);
-      if (ok) ok = stage1(g);
+      ok = stage1(g, true);
       if (ok && k == 1) mma_commit(x_free);
       for (int i = 0; i < k && ok; ++i) {
         if (i + 1 < k) {
-          ok = stage1(g + i + 1);
+          ok = stage1(g + i + 1, false);
           if (ok && i + 2 == k) mma_commit(x_free);  // last stage-1 MMAs of this problem issued
         }
         if (ok) ok = stage2(g + i, i);
@@ -1220,7 +1225,7 @@ __global__ void __launch_bounds__(192, 1) tc_resident_kernel(const TCJob* __rest
   __syncthreads();
   if (*s_fail && threadIdx.x == 0) {
     atomicExch(&g_tc_error, 1);
-    mbar_wait(x_full, 0);  // bounded drain of copies in flight
+    for (int q = 0; q < 4; ++q) mbar_wait(&x_full[q], 0);  // bounded drain of copies in flight
     for (int q = 0; q < STAGES; ++q) mbar_wait(&full[q], 0);
   }
   __syncthreads();
@@ -1377,19 +1382,37 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
 // the same bits and the choice only moves time.  The first plan of each (n, precision, k_max,
 // batch-size bucket, split mode) times every valid variant on its own operands (two warm-up
 // and four timed forward applies, CUDA events on the plan's stream, activity flags ignored)
-// and keeps the fastest for the process.  KPSB_TC_VARIANT=v forces variant v where valid;
+// and keeps the fastest for the process.  A plan that is one of several concurrent parts of
+// a batch (shared SMs) is ranked by SM time instead, duration x the CTAs the variant occupies
+// (capped at the SM count): a variant that is faster alone only because it spreads over more
+// SMs takes them from the other parts (measured on the 256-request step: a fused choice for one
+// of four parts cost 12 % of the step).  KPSB_TC_VARIANT=v forces variant v where valid;
 // KPSB_TUNE_LOG=1 prints the choices.
 struct TuneKey {
-  int n, prec, kmax, pbucket, ext;
+  int n, prec, kmax, pbucket, ext, shared;
   bool operator<(const TuneKey& o) const {
-    return std::tie(n, prec, kmax, pbucket, ext) < std::tie(o.n, o.prec, o.kmax, o.pbucket, o.ext);
+    return std::tie(n, prec, kmax, pbucket, ext, shared) <
+           std::tie(o.n, o.prec, o.kmax, o.pbucket, o.ext, o.shared);
   }
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, int> g_tune;
 static kpsb_status launch_variant(const TCPlan* P, const TCJob* jobs, int njobs, int variant, cudaStream_t st);
 
-static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStream_t st) {
+// CTAs a variant keeps busy at once, capped at the SM count.
+static int variant_ctas(int variant, int n, int njobs, int kmax, int sms) {
+  const long long tm = (n + 127) / 128;
+  long long c;
+  switch (variant) {
+    case TCV_RESIDENT: c = njobs; break;
+    case TCV_FUSED64: c = (long long)((n + 63) / 64) * njobs; break;
+    case TCV_FUSED32: c = (long long)((n + 31) / 32) * njobs; break;
+    default: c = tm * ((n + 127) / 128) * kmax * njobs; break;  // stage 1, the wider launch
+  }
+  return (int)std::max(1LL, std::min<long long>(c, sms));
+}
+
+static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, bool shared, cudaStream_t st) {
   const int n = P->n;
   if (const char* f = getenv("KPSB_TC_VARIANT")) {
     const int v = atoi(f);
@@ -1401,7 +1424,7 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
   if (cand.size() == 1 || P->njobs == 0) { P->variant = cand[0]; return KPSB_OK; }
   int pb = 1;
   while (pb < P->njobs) pb <<= 1;
-  const TuneKey key{n, P->prec, P->kmax, pb, P->ext_split ? 1 : 0};
+  const TuneKey key{n, P->prec, P->kmax, pb, P->ext_split ? 1 : 0, shared ? 1 : 0};
   std::lock_guard<std::mutex> lk(g_tune_mu);  // one tuner at a time; later plans reuse the choice
   auto it = g_tune.find(key);
   if (it != g_tune.end()) { P->variant = it->second; return KPSB_OK; }
@@ -1419,6 +1442,9 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
   if (e == cudaSuccess) e = cudaMemcpyFromSymbol(saved, g_tc_work, sizeof(saved));  // tuning is not work
   if (e == cudaSuccess) e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
+  int dev = 0, sms = 1;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int best = cand[0];
   float best_ms = 0.f;
   constexpr int TUNE_REPS = 4;  // timed applies per candidate, after two warm-up applies
@@ -1431,13 +1457,14 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
     if (s == KPSB_OK && e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
     if (s == KPSB_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (shared) ms *= (float)variant_ctas(cand[c], n, R, P->kmax, sms);  // SM time
     if (s == KPSB_OK && e == cudaSuccess && (c == 0 || ms < best_ms)) {
       best = cand[c];
       best_ms = ms;
     }
     if (getenv("KPSB_TUNE_LOG") && e == cudaSuccess)
-      fprintf(stderr, "[kpsb tune] n=%d prec=%d kmax=%d jobs<=%d variant %d: %.3f ms\n", n, P->prec, P->kmax, pb,
-              cand[c], ms / TUNE_REPS);
+      fprintf(stderr, "[kpsb tune] n=%d prec=%d kmax=%d jobs<=%d shared=%d variant %d: %.3f %s\n", n, P->prec,
+              P->kmax, pb, shared ? 1 : 0, cand[c], ms / TUNE_REPS, shared ? "SM-ms" : "ms");
   }
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_work, saved, sizeof(saved));
   if (a) cudaEventDestroy(a);
@@ -1456,7 +1483,7 @@ static kpsb_status tune_variant(TCPlan* P, const std::vector<TCJob>& hf, cudaStr
 }
 
 kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h, int njobs, int n,
-                           int prec, cudaStream_t st, TCPlan** out) {
+                           int prec, cudaStream_t st, TCPlan** out, bool shared_sms) {
   KPSB_REQUIRE(tc_supported(n, prec), "no tensor-core kernel for n = %d, precision %d", n, prec);
   const bool bf = prec_bf16(prec);
   // a caller's split planes have leading dimension n and the plan's element type (the split
@@ -1557,7 +1584,7 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
     set_error("tensor-core plan upload: %s", cudaGetErrorString(e));
     return KPSB_ECUDA;
   }
-  kpsb_status ts = tune_variant(P, hf, st);
+  kpsb_status ts = tune_variant(P, hf, shared_sms, st);
   if (ts != KPSB_OK) {
     tc_plan_free(P, st);
     return ts;
@@ -1669,13 +1696,14 @@ extern "C" int kpsb_tuned_variants(int* rows, int max_rows) {
   int i = 0;
   for (const auto& kv : g_tune) {
     if (rows && i < max_rows) {
-      int* r = rows + 6 * i;
+      int* r = rows + 7 * i;
       r[0] = kv.first.n;
       r[1] = kv.first.prec;
       r[2] = kv.first.kmax;
       r[3] = kv.first.pbucket;
       r[4] = kv.first.ext;
-      r[5] = kv.second;
+      r[5] = kv.first.shared;
+      r[6] = kv.second;
     }
     ++i;
   }

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -80,6 +81,35 @@ kpsb_status la_small_svd(const double* A, int lda, int m, int nc, double* U, dou
 // Box-Muller transform (computed in FP64, stored as T).
 template <typename T>
 kpsb_status la_randn(T* out, long long count, unsigned long long seed, cudaStream_t st);
+
+// ---- EGKB parameters (kpbuild.cu, egkb_block.cu) ------------------------------------------
+struct EgkbParams {
+  int k_fixed;      // > 0: fixed rank
+  int k_cap;
+  int p;
+  int k_min;
+  double tau;       // relative tolerance (auto mode)
+  double bd_tol;    // breakdown tolerance relative to bnorm
+};
+
+// ---- one-block EGKB for small images (egkb_block.cu) -----------------------------------
+struct EbProblem {
+  const double* psf;  // host, s0 x s1 column-major FP64
+  int s0, s1, n, bc;
+  EgkbParams P;
+  int full_reorth;    // reorthogonalise the s_j too (the single-precision variant)
+  int kpmax;          // k_cap + p
+  const float* start_host;  // host start vector (n^2), or null: Philox from seed
+  unsigned long long seed;
+};
+// Problems the one-block path takes: single precision, index-map R(A), n <= 128, the PSF
+// staged in shared memory.
+bool eb_eligible(int n, int s0, int s1);
+// Builds every problem (all eligible) with one block per problem on stream st and waits for
+// it.  outs[i] is null where problem i failed (st_out[i] / msg_out[i] say why).
+kpsb_status egkb_block_build(const EbProblem* probs, int count, kpsb_kp_t* outs,
+                             kpsb_status* st_out, std::string* msg_out, cudaStream_t st);
+kpsb_status kp_handle_alloc(kpsb_kp_t* out, int n, int k, int kpsize);
 
 // ---- KP operator handle ---------------------------------------------------------------
 struct TCTables;  // tensor-core operand tables (kpgemm_tc.cu)
@@ -184,8 +214,10 @@ bool tc_supported(int n, int prec);
 size_t tc_table_bytes(int n, int k, int prec);
 size_t tc_plan_ws_bytes(int n, int k, int prec);
 void tc_free(TCTables* t);
+// shared_sms: the plan's applies run beside other parts of the same batch (the autotuner then
+// ranks variants by SM time, not duration).
 kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h, int njobs, int n,
-                           int prec, cudaStream_t st, TCPlan** out);
+                           int prec, cudaStream_t st, TCPlan** out, bool shared_sms = false);
 kpsb_status tc_plan_apply(TCPlan* P, int transpose, cudaStream_t st);
 // True when the plan runs the fused kernel with CGLS epilogues (inputs split by the caller).
 bool tc_plan_fused(const TCPlan* P);

@@ -868,7 +868,9 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
     for (int p = 0; p < P; ++p) ksum += set[p]->kp->k;
     const double apply_flops = 4.0 * ksum * (double)n * n * n;  // 4 k n^3 per problem (Sec. 4.2)
     trace(st, "advance setup queued");
-    if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, gemm_prec, st, &plan))) break;
+    // one of several concurrent parts of a batch: its applies share the SMs with the others
+    const bool shared = t_gate && t_gate->total > 1;
+    if (tc && (s = tc_plan_create(kps.data(), fwd.data(), bwd.data(), P, n, gemm_prec, st, &plan, shared))) break;
     trace(st, "apply plan ready");
     // kernel launches of one apply (forward / transpose)
     const int apply_launches = tc ? tc_plan_launches(plan) : 3;

@@ -570,9 +570,9 @@ VARIANT_NAMES = {0: "two-stage", 1: "fused 64-column", 2: "fused 32-column", 3: 
 
 
 def kpsb_tuned_variants():
-    """The autotuner's choices so far: list of dicts (n, prec, kmax, bucket, ext, variant)."""
+    """The autotuner's choices so far: list of dicts (n, prec, kmax, bucket, ext, shared, variant)."""
     cnt = lib().kpsb_tuned_variants(None, 0)
-    buf = (C.c_int * (6 * max(1, cnt)))()
+    buf = (C.c_int * (7 * max(1, cnt)))()
     cnt = lib().kpsb_tuned_variants(buf, cnt)
-    keys = ("n", "prec", "kmax", "bucket", "ext", "variant")
-    return [dict(zip(keys, buf[6 * i:6 * i + 6])) for i in range(cnt)]
+    keys = ("n", "prec", "kmax", "bucket", "ext", "shared", "variant")
+    return [dict(zip(keys, buf[7 * i:7 * i + 7])) for i in range(cnt)]
