@@ -26,12 +26,16 @@
  *    entries stated for it (the Python binding checks host arrays before the call).
  *
  * Environment switches (the first two only print; the third picks which kernel computes
- * the apply; every variant gives the same bits, only the time changes):
+ * the apply, where every variant gives the same bits and only the time changes; the fourth
+ * picks the build path, whose two forms round differently):
  *   KPSB_TRACE=1        host phase trace of batched solves on stderr (plan ready, graph
  *                       instantiated and uploaded, launch, done; per stream)
  *   KPSB_TUNE_LOG=1     the tensor-core apply autotuner's timings on stderr
  *   KPSB_TC_VARIANT=v   pin the tensor-core apply variant (0 two-stage, 1 fused 64-column,
  *                       2 fused 32-column, 3 resident n = 128) instead of autotuning
+ *   KPSB_EGKB_BLOCK=0   single-precision EGKB builds with n <= 128 use the multi-kernel path
+ *                       instead of one thread block per problem (the default; both follow
+ *                       Alg. 1 with the same arithmetic classes, summation orders differ)
  */
 #ifndef KPSB_H
 #define KPSB_H
@@ -144,7 +148,11 @@ typedef struct {
  * The effective k may be smaller than asked when R(A) has smaller rank (rank <= s0*s1):
  * the GKB recurrence stops at breakdown and RSVD drops null directions; kp_info reports
  * the k and k_p used.  Errors: EINVAL (sizes, n < 2, s > 2n, k < 1, k_p > 64),
- * ENOMEM, ECUDA, EBREAKDOWN (R(A) = 0). */
+ * ENOMEM, ECUDA, EBREAKDOWN (R(A) = 0).
+ * Single-precision EGKB with n <= 128 and a PSF of at most 4096 entries (sides <= 128) runs
+ * as one thread block per problem (the whole recurrence, the SVD of C and the Ritz vectors
+ * in one launch pair), alone and in kp_build_batched alike, so a problem's factors do not
+ * depend on its batch; other builds run as a sequence of grid-wide kernels. */
 kpsb_status kp_build(const double* psf, int s0, int s1, int n, int bc, double rank_or_tol,
                      int method, const kpsb_build_opts* opts, kpsb_kp_t* out);
 
@@ -218,8 +226,10 @@ typedef struct {
   kpsb_build_opts opts;  /* opts.stream is ignored: the batch picks its streams */
 } kpsb_problem;
 
-/* Builds `count` handles; problems run concurrently on internal streams.  outs[i] is
- * NULL where problem i failed; the first error is returned. */
+/* Builds `count` handles: the problems of kp_build's one-block path share one launch pair
+ * per chunk of 256 (one thread block each), the others run concurrently on internal streams.
+ * outs[i] is NULL where problem i failed; the first error is returned.  Each handle equals
+ * the one kp_build gives for the same problem alone. */
 kpsb_status kp_build_batched(int count, const kpsb_problem* probs, kpsb_kp_t* outs);
 
 typedef struct {
