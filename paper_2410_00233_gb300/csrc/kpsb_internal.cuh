@@ -121,6 +121,8 @@ struct SBProb {
   double mu, sqrt_mu, lam, thr, tau_cgls, tau_sb;
   const double* b;
   double *x, *xprev, *w, *f, *r1, *r2, *r3, *z1, *f1, *dx, *dy, *gx, *gy;
+  double* q;              // tensor-core path: raw TV part of Ahat^T r (2 (Dx^T r2 + Dy^T r3) / lambda),
+                          // kept in r2's storage instead of r2 and r3
   SBScal* sc;
   double* part;           // reduction partials
   unsigned int* counter;  // last-block counter

@@ -178,6 +178,13 @@ __global__ void SB_BOUNDS_WIDE sb_outer_init_kernel(const SBProb* __restrict__ p
   }
 }
 
+// tau' = ||f||^2 (step 8), delta = tau'/tau (step 9); init: tau = tau', delta = 0.
+__device__ __forceinline__ void f_scalars(SBScal* s, double taun, int init) {
+  s->delta = init ? 0.0 : (s->tau > 0.0 ? taun / s->tau : 0.0);
+  s->tau = taun;
+  if (!(taun > 0.0)) s->active = 0;  // exact solution reached (or b-hat = 0)
+}
+
 // f = Ahat^T r = sqrt(mu) f1 + lam Dx^T r2 + lam Dy^T r3 (Alg. 5 step 7 / init) and
 // tau' = ||f||^2 (step 8); delta = tau'/tau (step 9).  init: tau = tau', delta = 0.
 __global__ void SB_BOUNDS sb_cgls_f_kernel(const SBProb* __restrict__ probs, int init) {
@@ -199,17 +206,7 @@ __global__ void SB_BOUNDS sb_cgls_f_kernel(const SBProb* __restrict__ probs, int
   }
   double tot[2];
   if (!prob_reduce2(P, ss, 0.0, tot)) return;
-  if (threadIdx.x == 0) {
-    SBScal* s = P.sc;
-    double taun = tot[0];
-    if (init) {
-      s->delta = 0.0;
-    } else {
-      s->delta = s->tau > 0.0 ? taun / s->tau : 0.0;
-    }
-    s->tau = taun;
-    if (!(taun > 0.0)) s->active = 0;  // exact solution reached (or b-hat = 0)
-  }
+  if (threadIdx.x == 0) f_scalars(P.sc, tot[0], init);
 }
 
 // w = f + delta w (step 10); init: w = f (step 2).  The start does not read w, which holds
@@ -397,7 +394,9 @@ __device__ __forceinline__ float put_split(float (*th)[33], float (*tl)[33], int
   return f;
 }
 
-// Outer step start (as sb_outer_init_kernel) plus the split planes of r1 = sqrt(mu) b.
+// Outer step start (as sb_outer_init_kernel) plus the split planes of r1 = sqrt(mu) b.  The
+// tensor-core path keeps the TV rows r2, r3 of the residual only as q = 2 (Dx^T r2 + Dy^T r3)
+// / lambda (the raw differences): they enter the iteration only through Ahat^T r (step 7).
 __global__ void SB_BOUNDS sb_outer_init_tc_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->sb_active)
   (void)N; (void)e_hi;
@@ -411,8 +410,14 @@ __global__ void SB_BOUNDS sb_outer_init_tc_kernel(const SBProb* __restrict__ pro
     P.x[e] = 0.0;
     const double r1 = P.sqrt_mu * P.b[e];
     P.r1[e] = r1;
-    P.r2[e] = P.lam * (P.dx[e] - P.gx[e]);
-    P.r3[e] = P.lam * (P.dy[e] - P.gy[e]);
+    // q = raw TV part of Ahat^T r for r2 = lam (dx - gx), r3 = lam (dy - gy):
+    // [c < n-1] r2(e) + [r < n-1] r3(e) - [c >= 1] r2(e - n) - [r >= 1] r3(e - 1)
+    double t = 0.0;
+    if (c < n - 1) t += P.dx[e] - P.gx[e];
+    if (r < n - 1) t += P.dy[e] - P.gy[e];
+    if (c >= 1) t -= P.dx[e - n] - P.gx[e - n];
+    if (r >= 1) t -= P.dy[e - 1] - P.gy[e - 1];
+    P.q[e] = P.lam * t;
     put_split(th, tl, ly + 8 * j, lx, r1, P.xt_bf16);
   }
   store_xt_tile(P.xt, n, tr, tcol, th, tl, lx, ly, P.xt_bf16);
@@ -447,6 +452,24 @@ __global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int i
   double tot[2];
   if (!prob_reduce2(P, (double)wwf, 0.0, tot)) return;
   if (threadIdx.x == 0) P.sc->ww = tot[0];
+}
+
+// f = Ahat^T r = sqrt(mu) f1 + (lambda/2) q (step 7 / init) on the tensor-core path, f1 the
+// FP32 apply result widened on the integer pipes; tau' = ||f||^2 and delta (steps 8-9).
+__global__ void SB_BOUNDS sb_f_tc_kernel(const SBProb* __restrict__ probs, int init) {
+  SB_PROLOGUE(P.sc->active)
+  const double hl = 0.5 * P.lam;
+  const bool unit_mu = P.sqrt_mu == 1.0;
+  double ss = 0.0;
+  SB_FOR_E {
+    const double f1 = f2d_bits(P.f1f[e]);
+    const double v = fma(hl, P.q[e], unit_mu ? f1 : P.sqrt_mu * f1);
+    P.f[e] = v;
+    ss = fma(v, v, ss);
+  }
+  double tot[2];
+  if (!prob_reduce2(P, ss, 0.0, tot)) return;
+  if (threadIdx.x == 0) f_scalars(P.sc, tot[0], init);
 }
 
 // ||z||^2 with z = Ahat w_f (steps 3-4) on the tensor-core path: w_f = fl32(w) is the vector
@@ -514,8 +537,15 @@ __global__ void SB_BOUNDS_X sb_x_tc_kernel(const SBProb* __restrict__ probs) {
 #endif
     const double r1 = fma(c1, z1, P.r1[e]);
     P.r1[e] = r1;
-    if (c < n - 1) P.r2[e] = fma(c2, w - P.w[e + n], P.r2[e]);
-    if (r < n - 1) P.r3[e] = fma(c2, w - P.w[e + 1], P.r3[e]);
+    // r2, r3 -= mu lam (Dx w, Dy w) moves q by c2 (raw D^T D w)(e) = c2 (cnt w(e) - the sum of
+    // its cnt neighbours inside the image)
+    double nb = 0.0;
+    int cnt = 0;
+    if (c < n - 1) { nb = P.w[e + n]; ++cnt; }
+    if (r < n - 1) { nb = cnt ? nb + P.w[e + 1] : P.w[e + 1]; ++cnt; }
+    if (c >= 1) { nb = cnt ? nb + P.w[e - n] : P.w[e - n]; ++cnt; }
+    if (r >= 1) { nb = cnt ? nb + P.w[e - 1] : P.w[e - 1]; ++cnt; }
+    P.q[e] = fma(c2, fma((double)cnt, w, -nb), P.q[e]);
 #if KPSB_X_NORM_F32
     const float xf = d2f_rn_bits(xn);
     sxf = fmaf(xf, xf, sxf);
@@ -744,6 +774,7 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   P.xprev = v + 0 * N; P.w = v + 1 * N; P.f = v + 2 * N; P.r1 = v + 3 * N; P.r2 = v + 4 * N;
   P.r3 = v + 5 * N; P.z1 = v + 6 * N; P.f1 = v + 7 * N; P.dx = v + 8 * N; P.dy = v + 9 * N;
   P.gx = v + 10 * N; P.gy = v + 11 * N;
+  P.q = P.r2;  // the tensor-core path keeps q where the other paths keep r2 (and no r3)
   q += a256(13 * N * sizeof(double));
   S->Z = zbytes ? (void*)q : nullptr;
   q += zbytes;
@@ -899,7 +930,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
       if (fz) {
         SB_LAUNCH(TIMER_SB_OUTER, sb_outer_init_tc_kernel, dprobs);
         KPSB_TRY(kp_apply_on(1, sx));
-        SB_LAUNCH(TIMER_SB_F, sb_cgls_f_kernel, dprobs, 1);
+        SB_LAUNCH(TIMER_SB_F, sb_f_tc_kernel, dprobs, 1);
         SB_LAUNCH(TIMER_SB_W, sb_w_tc_kernel, dprobs, 1);
         return KPSB_OK;
       }
@@ -916,7 +947,7 @@ kpsb_status sb_advance(SBState* const* set, int count, int outer_steps, const kp
         SB_LAUNCH(TIMER_SB_ZZ, sb_zz_tc_kernel, dprobs);
         SB_LAUNCH(TIMER_SB_X, sb_x_tc_kernel, dprobs);
         KPSB_TRY(kp_apply_on(1, sx));
-        SB_LAUNCH(TIMER_SB_F, sb_cgls_f_kernel, dprobs, 0);
+        SB_LAUNCH(TIMER_SB_F, sb_f_tc_kernel, dprobs, 0);
         SB_LAUNCH(TIMER_SB_W, sb_w_tc_kernel, dprobs, 0);
         return KPSB_OK;
       }
