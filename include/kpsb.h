@@ -360,7 +360,9 @@ kpsb_status kpsb_apply_counts(unsigned long long* problem_applies, unsigned long
  * of the EGKB bases, 8 SVQB orthonormalisation of the RSVD blocks; for these three the
  * first value counts calls and the third holds ALGORITHMIC BYTES instead of flops (R(A):
  * the vectors read and written plus the PSF, or 4 n^4 per pass over an explicit A; CGS2:
- * 2 (2m + 3) N elements for m basis vectors; SVQB2: 10 m N elements).  KPSB_EINVAL for
+ * 2 (2m + 3) N elements for m basis vectors; SVQB2: 10 m N elements); 9 the one-block EGKB
+ * recurrence launches (n <= 128; one thread block per problem), whose third value is the sum of
+ * the same R(A) and CGS2 byte counts over every problem of the launch.  KPSB_EINVAL for
  * another category. */
 kpsb_status kpsb_timer_stats(int category, unsigned long long* launches, double* ms, double* flops);
 

@@ -34,10 +34,13 @@ enum TimerCategory {
   TIMER_RA = 6,        // R(A) products of the TSVD (index map or explicit matrix)
   TIMER_REORTH = 7,    // CGS2 reorthogonalisation of the EGKB bases
   TIMER_QR = 8,        // SVQB orthonormalisation of the RSVD blocks
-  TIMER_CATEGORIES = 9
+  TIMER_EGKB_BLOCK = 9,  // one-block EGKB recurrence launches (all problems of a batch)
+  TIMER_CATEGORIES = 10
 };
 int timer_begin(cudaStream_t st);
 void timer_end(int slot, cudaStream_t st, int cat, double flops, int launches);
+// Sets the work value of a recorded slot once it is known (counted on the device).
+void timer_set_value(int slot, double v);
 int gemm_timer_begin(cudaStream_t st);
 void gemm_timer_end(int slot, cudaStream_t st, double flops, int launches);
 

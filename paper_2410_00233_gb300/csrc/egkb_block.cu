@@ -34,6 +34,7 @@ bool eb_eligible(int n, int s0, int s1) {
 
 struct EbInfo {  // per problem, read by the host between the two launches
   int nq, ns, ksel, finished, kk, pad[3];
+  double bytes;  // algorithmic bytes of the R(A) products and CGS2 passes (as the TSVD timers)
   double sigma[EB_KP];
 };
 
@@ -55,8 +56,20 @@ struct EbJob {
 struct EbState {
   double alpha[EB_KP + 4], t[EB_KP + 4], zeta[EB_KP + 4], nu[EB_KP + 4];
   double norm, coef_s, coef_q, bnorm;
+  double bytes;  // algorithmic bytes so far: R(A) products and CGS2 passes
   int nq, ns, k_sel, kp_target, finished, stop;
 };
+
+// Algorithmic bytes of one R(A) product of one vector (read V, write U, read prev when given,
+// the PSF) and of one CGS2 against m basis vectors (two passes: the basis read twice and v
+// three times per pass; a plain norm when m = 0), the same counts as the multi-kernel path's
+// TSVD timers.
+__device__ __forceinline__ double eb_ra_bytes(int N, bool prev, int s0, int s1) {
+  return 4.0 * N * (prev ? 3.0 : 2.0) + 4.0 * s0 * s1;
+}
+__device__ __forceinline__ double eb_cgs2_bytes(int N, int m) {
+  return m > 0 ? 2.0 * (2.0 * m + 3.0) * N * 4.0 : 4.0 * N;
+}
 
 // ---- block-level building blocks (every thread calls; each ends synchronised) ---------------
 
@@ -195,16 +208,30 @@ __device__ double eb_cgs2(const float* __restrict__ B, int m, float* v, int N, f
       }
       __syncthreads();
     }
-    // v -= B h (FP32, columns in order)
+    // v -= B h (FP32, columns in order), two elements per iteration so that twice as many
+    // basis loads are in flight
     ss0 = ss1 = 0.f;
-    int k = 0;
-    for (int e = threadIdx.x; e < N; e += EB_T, ++k) {
+    int e = threadIdx.x;
+    for (; e + EB_T < N; e += 2 * EB_T) {
+      float c0r = 0.f, c1r = 0.f;
+#pragma unroll 4
+      for (int c = 0; c < m; ++c) {
+        const float* b = B + (size_t)c * N;
+        c0r = fmaf(b[e], hf[c], c0r);
+        c1r = fmaf(b[e + EB_T], hf[c], c1r);
+      }
+      const float x0 = v[e] - c0r, x1 = v[e + EB_T] - c1r;
+      v[e] = x0;
+      v[e + EB_T] = x1;
+      ss0 = fmaf(x0, x0, ss0);
+      ss1 = fmaf(x1, x1, ss1);
+    }
+    if (e < N) {
       float corr = 0.f;
       for (int c = 0; c < m; ++c) corr = fmaf(B[e + (size_t)c * N], hf[c], corr);
       const float x = v[e] - corr;
       v[e] = x;
-      if (k & 1) ss1 = fmaf(x, x, ss1);
-      else ss0 = fmaf(x, x, ss0);
+      ss0 = fmaf(x, x, ss0);
     }
     __syncthreads();
   }
@@ -306,7 +333,10 @@ __global__ void __launch_bounds__(EB_T, 2) egkb_block_kernel(const EbJob* __rest
   if (!stop) {  // q_1 = R^T s_1 / alpha_1
     eb_ra(psf, J.s0, J.s1, n, J.bc, S, Q, nullptr, 0.f, true, Dsh, wsh);
     nrm = eb_norm(Q, N, red);
-    if (tid == 0) eb_after_alpha(es, J.P, 1, nrm);
+    if (tid == 0) {
+      es.bytes += eb_ra_bytes(N, false, J.s0, J.s1);
+      eb_after_alpha(es, J.P, 1, nrm);
+    }
     __syncthreads();
     eb_scale(Q, N, es.norm);
     stop = es.stop;
@@ -319,7 +349,10 @@ __global__ void __launch_bounds__(EB_T, 2) egkb_block_kernel(const EbJob* __rest
     // s-phase: s_j = R q_{j-1} - alpha_{j-1} s_{j-1}, reorthogonalised, t_j
     eb_ra(psf, J.s0, J.s1, n, J.bc, qjm1, sj, sjm1, (float)es.coef_s, false, Dsh, wsh);
     nrm = eb_cgs2(S, J.full_reorth ? j - 1 : 0, sj, N, wpart, hd, hf, red);
-    if (tid == 0) eb_after_t(es, J.P, j, nrm);
+    if (tid == 0) {
+      es.bytes += eb_ra_bytes(N, true, J.s0, J.s1) + eb_cgs2_bytes(N, J.full_reorth ? j - 1 : 0);
+      eb_after_t(es, J.P, j, nrm);
+    }
     __syncthreads();
     eb_scale(sj, N, es.norm);
     stop = es.stop;
@@ -327,7 +360,10 @@ __global__ void __launch_bounds__(EB_T, 2) egkb_block_kernel(const EbJob* __rest
     // q-phase: q_j = R^T s_j - t_j q_{j-1}, reorthogonalised, alpha_j and the nu rule
     eb_ra(psf, J.s0, J.s1, n, J.bc, sj, qj, qjm1, (float)es.coef_q, true, Dsh, wsh);
     nrm = eb_cgs2(Q, j - 1, qj, N, wpart, hd, hf, red);
-    if (tid == 0) eb_after_alpha(es, J.P, j, nrm);
+    if (tid == 0) {
+      es.bytes += eb_ra_bytes(N, true, J.s0, J.s1) + eb_cgs2_bytes(N, j - 1);
+      eb_after_alpha(es, J.P, j, nrm);
+    }
     __syncthreads();
     eb_scale(qj, N, es.norm);
     stop = es.stop;
@@ -340,6 +376,7 @@ __global__ void __launch_bounds__(EB_T, 2) egkb_block_kernel(const EbJob* __rest
     J.info->ksel = es.k_sel;
     J.info->finished = es.finished;
     J.info->kk = nq >= 1 ? kk : 0;
+    J.info->bytes = es.bytes;
   }
   if (nq < 1) return;
   // C ((nq + 1) x nq lower bidiagonal) and its FP64 SVD (step 15)
@@ -513,9 +550,11 @@ kpsb_status egkb_block_build(const EbProblem* pr, int count, kpsb_kp_t* outs, kp
       s = KPSB_ECUDA;
       break;
     }
+    const int slot = timer_begin(st);
     egkb_block_kernel<<<count, EB_T, std::max(dyn, 1), st>>>((const EbJob*)(base + o_jobs));
     count_launch();
     e = cudaGetLastError();
+    timer_end(slot, st, TIMER_EGKB_BLOCK, 0.0, 1);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(info.data(), base + o_info, sizeof(EbInfo) * count, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -524,6 +563,9 @@ kpsb_status egkb_block_build(const EbProblem* pr, int count, kpsb_kp_t* outs, kp
       s = KPSB_ECUDA;
       break;
     }
+    double bytes = 0.0;
+    for (int p = 0; p < count; ++p) bytes += info[p].bytes;
+    timer_set_value(slot, bytes);
     // handles sized by the selected rank
     for (int p = 0; p < count; ++p) {
       if (info[p].nq < 1) {

@@ -523,7 +523,7 @@ def kpsb_gemm_stats():
 
 TIMER_NAMES = ("kp_apply", "cgls_zz", "cgls_x", "cgls_f", "cgls_w", "sb_outer")
 # TSVD timer categories: (launches = calls, ms, algorithmic bytes)
-TSVD_TIMERS = {"ra_products": 6, "cgs2": 7, "svqb2": 8}
+TSVD_TIMERS = {"ra_products": 6, "cgs2": 7, "svqb2": 8, "egkb_block": 9}
 
 
 def kpsb_timer_stats(category: int):
