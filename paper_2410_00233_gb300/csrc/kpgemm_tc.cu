@@ -282,6 +282,8 @@ struct alignas(128) TCJob {
   int n, k, ldz, ldx;
   const int* active;
   float* Yf;         // when set (fused kernel): FP32 output instead of Y
+  float* part;       // two-stage stage 2 split over K: FP32 partial tiles [split][tiles][BN][128]
+  unsigned int* tctr;  // ... and one arrival counter per output tile (zero between launches)
 };
 
 // Leading dimensions of the planes: K extents padded to 8 elements, so every TMA stride is a
@@ -321,9 +323,12 @@ size_t tc_table_bytes(int n, int k, int prec) {
   return per * 2 * (prec_bf16(prec) ? sizeof(__nv_bfloat16) : sizeof(float));
 }
 
+static size_t s2_split_bytes(int n, bool bf);  // stage-2 partial tiles and counters of one problem
+
 size_t tc_plan_ws_bytes(int n, int k, int prec) {
   const size_t es = prec_bf16(prec) ? sizeof(__nv_bfloat16) : sizeof(float);
-  return es * ((size_t)2 * n * pad8(n) + (size_t)2 * n * pad8((long long)k * n)) + 1024;
+  return es * ((size_t)2 * n * pad8(n) + (size_t)2 * n * pad8((long long)k * n)) + s2_split_bytes(n, prec_bf16(prec)) +
+         1024;
 }
 
 // ---- table build ---------------------------------------------------------------------------
@@ -509,13 +514,17 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
   const int term = STAGE == 1 ? (int)blockIdx.y : 0;
   if (term >= J.k) return;
   if (J.active && !*J.active) return;
-  if (STAGE == 2 && blockIdx.x == 0 && threadIdx.x == 0) count_apply_work(J.k, J.n);
+  if (STAGE == 2 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) count_apply_work(J.k, J.n);
   const int n = J.n;
   const int m0 = (blockIdx.x % tiles_m) * 128;
   const int c0 = (blockIdx.x / tiles_m) * BN;
   if (m0 >= n || c0 >= n) return;
   const int KT = STAGE == 1 ? n : J.k * n;  // K extent (zero-filled past it)
-  const int nkb = (KT + C::KS - 1) / C::KS;
+  const int nkb_all = (KT + C::KS - 1) / C::KS;
+  // stage 2 split over K (grid.y ranges, fixed by n): this CTA's K slices [kb0, kb1)
+  const int S = STAGE == 2 ? (int)gridDim.y : 1, ks = STAGE == 2 ? (int)blockIdx.y : 0;
+  const int kb0 = (int)((long long)nkb_all * ks / S), kb1 = (int)((long long)nkb_all * (ks + 1) / S);
+  const bool has_k = kb1 > kb0;
 
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -555,8 +564,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
     const CUtensorMap* mB = STAGE == 1 ? &J.m1B : &J.m2B;
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)mA) : "memory");
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)mB) : "memory");
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, round = kb / STAGES;
+    for (int kb = kb0; kb < kb1; ++kb) {
+      const int s = (kb - kb0) % STAGES, round = (kb - kb0) / STAGES;
       if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1)) {
         s_fail = 1;
         break;
@@ -585,8 +594,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
       else mma_tf32(tmem, a, b, idesc, acc);
     };
     bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, round = kb / STAGES;
+    for (int kb = kb0; kb < kb1; ++kb) {
+      const int s = (kb - kb0) % STAGES, round = (kb - kb0) / STAGES;
       if (!mbar_wait(&full[s], round & 1)) {
         s_fail = 1;
         ok = false;
@@ -600,7 +609,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {  // four 32-byte K steps (8 TF32 / 16 BF16) per row
         const uint32_t off = kk * 32;
-        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+        const uint32_t acc0 = (kb > kb0 || kk > 0) ? 1u : 0u;
         // Product order shared by every apply kernel: iterate lo x factor hi, iterate hi x
         // factor lo (split factors only), then hi x hi.  The iterate (X or Z, two planes) is
         // the A operand in stage 1 and the B operand in stage 2.
@@ -631,7 +640,12 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
     for (int cc = 0; cc < BN; cc += 16) {
       float v[16];
       tmem_ld16(tbase + cc, v);
-      if (row < n) {
+      if (STAGE == 2 && S > 1) {
+        // partial tile of this K range: [column][row], rows contiguous (coalesced)
+        float* pt = J.part + ((size_t)ks * gridDim.x + blockIdx.x) * (size_t)(BN * 128);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) pt[(size_t)(cc + j) * 128 + warp * 32 + lane] = has_k ? v[j] : 0.f;
+      } else if (row < n) {
         if (STAGE == 1) {
           // D1[r][c] = Z_term(r, c) -> Zt[c][term n + r], hi/lo planes
           const size_t plane = (size_t)n * J.ldz;
@@ -661,6 +675,60 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
     }
   } else if (threadIdx.x == 0) {
     atomicExch(&g_tc_error, 1);
+  }
+  if (STAGE == 2 && S > 1) {
+    // every CTA of the tile arrives (a failed one too, so the counter returns to zero; the
+    // error flag then reports the launch); the last to arrive adds the partials in range order
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned prev = atomicAdd(&J.tctr[blockIdx.x], 1u);
+      s_last = prev == (unsigned)S - 1;
+      if (s_last) J.tctr[blockIdx.x] = 0u;  // no other CTA of this tile touches it again
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      // element i of the tile (column i / 128, row i % 128): 0 + p_0 + p_1 + ... in range order;
+      // four elements per load, eight loads per partial in flight per thread
+      constexpr int NF4 = BN * 128 / 4, U = 8;
+      const float4* pb = (const float4*)(J.part + (size_t)blockIdx.x * (BN * 128));
+      const size_t rs4 = (size_t)gridDim.x * (BN * 128 / 4);
+#pragma unroll 1
+      for (int base = threadIdx.x; base < NF4; base += 128 * U) {
+        float4 a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < S; ++q) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int i = base + u * 128;
+            if (i < NF4) {
+              const float4 t = __ldcg(pb + q * rs4 + i);
+              a[u].x += t.x;
+              a[u].y += t.y;
+              a[u].z += t.z;
+              a[u].w += t.w;
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = base + u * 128;
+          if (i >= NF4) continue;
+          const int c = c0 + (4 * i) / 128, r = m0 + (4 * i) % 128;
+          if (c >= n) continue;
+          const float vv[4] = {a[u].x, a[u].y, a[u].z, a[u].w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            if (r + t >= n) break;
+            if (J.Yf) J.Yf[r + t + (size_t)c * n] = vv[t];
+            else J.Y[r + t + (size_t)c * n] = (double)vv[t];
+          }
+        }
+      }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -1278,6 +1346,32 @@ static constexpr int S1L_BN = KPSB_S1_BN_LARGE;
 static constexpr int s1l_stages(int fpl) { return S1L_BN == 128 ? S1_STAGES : (fpl == 2 ? 2 : 3); }
 static inline bool s1_large(int n) { return n > 768; }
 
+// Stage 2 where the two-stage kernel is the only variant for (n, precision), so its bits need
+// not match the fused and resident kernels': BF16 planes, or TF32 with n > 768 or n not a
+// multiple of 128.  From n = 512 on it takes 128-column output tiles (half the operand bytes
+// per MMA of 64-column tiles) and splits K into a fixed number of ranges, set by n alone so
+// that about 128 CTAs share one problem; the last CTA of a tile to finish adds the FP32
+// partial tiles in range order.  The split depends on n only, so a problem gives the same bits
+// alone and in any batch.  Measured on one BF16x3 request (20 outer steps): n = 1024
+// 0.443 -> 0.387 s (split 2), n = 512 0.219 -> 0.173 s (split 8); 256-column tiles (two
+// pipeline stages) and other splits were slower.
+struct S2Shape {
+  int bn, split;
+};
+static constexpr int S2W_BN = 128, S2W_STAGES = 3;
+static S2Shape s2_shape(int n, bool bf) {
+  const bool only_two_stage = bf || n % 128 != 0 || n > 768;
+  if (!only_two_stage || n < 512) return {S2_BN, 1};
+  const int tiles = ((n + 127) / 128) * ((n + S2W_BN - 1) / S2W_BN);
+  return {S2W_BN, std::max(1, std::min(8, (128 + tiles / 2) / tiles))};
+}
+static size_t s2_split_bytes(int n, bool bf) {
+  const S2Shape sh = s2_shape(n, bf);
+  if (sh.split <= 1) return 0;
+  const size_t tiles = (size_t)((n + 127) / 128) * ((n + sh.bn - 1) / sh.bn);
+  return sizeof(float) * sh.split * tiles * 128 * sh.bn + sizeof(unsigned int) * tiles + 512;
+}
+
 template <int BN, int FPL>
 static kpsb_status prepare_fused() {
   KPSB_TRY_CUDA(cudaFuncSetAttribute(tc_fused_kernel<BN, FPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1372,7 +1466,7 @@ static kpsb_status fill_job(TCJob& J, const KPJob& src, const TCTables* T, int t
   cuuint64_t d2[3] = {(cuuint64_t)k * n, (cuuint64_t)n, 2};
   cuuint64_t s2[2] = {es * l2, es * l2 * n};
   KPSB_TRY(make_map(&J.m2A, t2, 3, d2, s2, 128, bf));    // T2: {k n, n, 2}
-  KPSB_TRY(make_map(&J.m2B, Zt, 3, d2, s2, S2_BN, bf));  // Zt: {k n, n, 2}
+  KPSB_TRY(make_map(&J.m2B, Zt, 3, d2, s2, s2_shape(n, bf).bn, bf));  // Zt: {k n, n, 2}
   return KPSB_OK;
 }
 
@@ -1503,6 +1597,10 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
   KPSB_TRY((prepare_gemm<S1L_BN, s1l_stages(1), 1, 1, false>()));
   KPSB_TRY((prepare_gemm<S1L_BN, s1l_stages(2), 1, 2, true>()));
   KPSB_TRY((prepare_gemm<S1L_BN, s1l_stages(1), 1, 1, true>()));
+  KPSB_TRY((prepare_gemm<S2W_BN, S2W_STAGES, 2, 2, false>()));
+  KPSB_TRY((prepare_gemm<S2W_BN, S2W_STAGES, 2, 1, false>()));
+  KPSB_TRY((prepare_gemm<S2W_BN, S2W_STAGES, 2, 2, true>()));
+  KPSB_TRY((prepare_gemm<S2W_BN, S2W_STAGES, 2, 1, true>()));
   KPSB_TRY((prepare_fused<FUSED_BN, 1>()));
   KPSB_TRY((prepare_fused<FUSED_BN, 2>()));
   KPSB_TRY((prepare_fused<32, 1>()));
@@ -1529,6 +1627,13 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
     P->kmax = std::max(P->kmax, kps[p]->k);
     bytes += (fwd_h[p].xt_ext ? 0 : a256(es * 2 * n * ldx)) + a256(es * 2 * n * tabs[p]->ld2);
   }
+  // stage-2 K split: FP32 partial tiles per problem (shared by its forward and transpose
+  // applies, which never overlap) and one arrival counter per output tile, all zeroed once
+  const S2Shape sh = s2_shape(n, bf);
+  const size_t s2_tiles = (size_t)((n + 127) / 128) * ((n + sh.bn - 1) / sh.bn);
+  const size_t part_bytes = sh.split > 1 ? a256(sizeof(float) * sh.split * s2_tiles * 128 * sh.bn) : 0;
+  const size_t ctr_bytes = sh.split > 1 ? a256(sizeof(unsigned int) * s2_tiles * njobs) : 0;
+  bytes += part_bytes * njobs + ctr_bytes;
   cudaError_t e = cudaMallocAsync((void**)&P->work, bytes + 2 * sizeof(TCJob) * njobs + 512, st);
   if (e != cudaSuccess) {
     delete P;
@@ -1537,6 +1642,15 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
   }
   std::vector<TCJob> hf(njobs), hb(njobs);
   char* q = P->work;
+  unsigned int* ctrs = (unsigned int*)q;  // the counters first: one memset covers them
+  q += ctr_bytes;
+  if (ctr_bytes) e = cudaMemsetAsync(ctrs, 0, ctr_bytes, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(P->work, st);
+    delete P;
+    set_error("tensor-core workspace: %s", cudaGetErrorString(e));
+    return KPSB_ECUDA;
+  }
   P->ext_split = njobs > 0 && fwd_h[0].xt_ext != nullptr;
   for (int p = 0; p < njobs; ++p) {
     void* Xt = fwd_h[p].xt_ext;
@@ -1548,6 +1662,13 @@ kpsb_status tc_plan_create(kpsb_kp** kps, const KPJob* fwd_h, const KPJob* bwd_h
     q += a256(es * 2 * n * tabs[p]->ld2);
     kpsb_status s = fill_job(hf[p], fwd_h[p], tabs[p], 0, bf, Xt, ldx, Zt);
     if (!s) s = fill_job(hb[p], bwd_h[p], tabs[p], 1, bf, Xt, ldx, Zt);
+    float* part = nullptr;
+    if (part_bytes) {
+      part = (float*)q;
+      q += part_bytes;
+    }
+    hf[p].part = hb[p].part = part;
+    hf[p].tctr = hb[p].tctr = part ? ctrs + s2_tiles * p : nullptr;
     if (s) {
       cudaFreeAsync(P->work, st);
       delete P;
@@ -1601,10 +1722,10 @@ void tc_plan_free(TCPlan* P, cudaStream_t st) {
 }
 
 template <int BN, int STAGES, int STAGE, int FPL, bool BF>
-static kpsb_status launch_gemm(const TCJob* jobs, int njobs, int n, int kmax, cudaStream_t st) {
+static kpsb_status launch_gemm(const TCJob* jobs, int njobs, int n, int kmax, cudaStream_t st, int split = 1) {
   using C = TCCfg<BN, STAGES, STAGE, FPL, BF>;
   const int tiles_m = (n + 127) / 128, tiles_n = (n + BN - 1) / BN;
-  dim3 grid(tiles_m * tiles_n, STAGE == 1 ? kmax : 1, njobs);
+  dim3 grid(tiles_m * tiles_n, STAGE == 1 ? kmax : split, njobs);
   tc_gemm_kernel<BN, STAGES, STAGE, FPL, BF><<<grid, 128, C::SMEM, st>>>(jobs, tiles_m);
   KPSB_CHECK_LAUNCH();
   return KPSB_OK;
@@ -1614,7 +1735,9 @@ template <int FPL, bool BF>
 static kpsb_status launch_two_stage(const TCJob* jobs, int njobs, int n, int kmax, cudaStream_t st) {
   if (s1_large(n)) KPSB_TRY((launch_gemm<S1L_BN, s1l_stages(FPL), 1, FPL, BF>(jobs, njobs, n, kmax, st)));
   else KPSB_TRY((launch_gemm<S1_BN, S1_STAGES, 1, FPL, BF>(jobs, njobs, n, kmax, st)));
-  KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, FPL, BF>(jobs, njobs, n, kmax, st)));
+  const S2Shape sh = s2_shape(n, BF);
+  if (sh.bn == S2W_BN) KPSB_TRY((launch_gemm<S2W_BN, S2W_STAGES, 2, FPL, BF>(jobs, njobs, n, kmax, st, sh.split)));
+  else KPSB_TRY((launch_gemm<S2_BN, S2_STAGES, 2, FPL, BF>(jobs, njobs, n, kmax, st)));
   return KPSB_OK;
 }
 
