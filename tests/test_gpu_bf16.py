@@ -109,3 +109,32 @@ def test_bf16_and_masked_apply_count_their_work():
             assert K.kpsb_apply_counts() == (1, k * n ** 3)
         finally:
             K.kpsb_gemm_timing(False)
+
+
+@pytest.mark.parametrize("prec_name,sizes", [("P_BF16X3", (512, 512, 640)), ("P_TF32X2", (1024, 520))])
+def test_split_stage2_batched_equals_alone(prec_name, sizes):
+    """The two-stage apply's stage 2 splits K into ranges fixed by n where it is the only
+    variant (BF16 modes; TF32 at n > 768 or n not a multiple of 128) and the tile's last CTA
+    adds the partial tiles in range order: problems with different k in one batched solve give
+    the bits of their solves alone, and the apply stays within the oracle bounds above."""
+    need_gpu()
+    from paper_2410_00233_gb300 import kpsb as K
+
+    prec = getattr(K, prec_name)
+    jobs, alone = [], []
+    for i, n in enumerate(sizes):
+        k = 2 + 2 * i
+        Ax, Ay, sig = _rand_factors(n, k, 7700 + 10 * n + i)
+        kp = K.kp_from_factors(Ax, Ay, sig)
+        X = I.rng(31 + i).standard_normal((n, n))
+        rnd = _tf32 if prec_name == "P_TF32X2" else None
+        ref = O.kp_apply(_op(Ax, Ay, sig, rnd), X)
+        y = K.kp_apply(kp, X, 0, prec)
+        assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-4, (n, k)
+        b = I.rng(77 + i).uniform(0.0, 1.0, (n, n))
+        x, st = K.sb_solve(kp, b, 1.0, 0.1, K.ISO, 2, i_max=3, fixed_inner=True, prec=prec)
+        alone.append(x)
+        jobs.append(dict(kp=kp, b=b, mu=1.0, lam=0.1, tv=K.ISO, iters=2))
+    outs, _ = K.sb_solve_batched(jobs, prec=prec, i_max=3, fixed_inner=True)
+    for x, xb in zip(alone, outs):
+        assert np.array_equal(x, xb)
