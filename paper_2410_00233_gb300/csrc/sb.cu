@@ -36,7 +36,8 @@ static constexpr int SB_T = 256;
 #endif
 #define SB_BOUNDS __launch_bounds__(SB_T, KPSB_SB_MIN_BLOCKS)
 #ifndef KPSB_SB_MIN_BLOCKS_X
-#define KPSB_SB_MIN_BLOCKS_X 5  // 48 registers: 6 spills in the x update
+#define KPSB_SB_MIN_BLOCKS_X 6  // 40 registers and a few bytes of spill in the tensor-core x update:
+                                // measured 100.0 vs 98.5 deblurs/s (5 blocks, 48 registers)
 #endif
 #define SB_BOUNDS_X __launch_bounds__(SB_T, KPSB_SB_MIN_BLOCKS_X)  // x and r update kernels
 // once-per-outer-step kernels and the CUDA-core path's x update, which would spill under
@@ -459,13 +460,20 @@ __global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int i
 __global__ void SB_BOUNDS sb_f_tc_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
   const double hl = 0.5 * P.lam;
-  const bool unit_mu = P.sqrt_mu == 1.0;
   double ss = 0.0;
-  SB_FOR_E {
-    const double f1 = f2d_bits(P.f1f[e]);
-    const double v = fma(hl, P.q[e], unit_mu ? f1 : P.sqrt_mu * f1);
-    P.f[e] = v;
-    ss = fma(v, v, ss);
+  if (P.sqrt_mu == 1.0) {  // mu = 1: f1 as it is (the branch outside the loop: no product per element)
+    SB_FOR_E {
+      const double v = fma(hl, P.q[e], f2d_bits(P.f1f[e]));
+      P.f[e] = v;
+      ss = fma(v, v, ss);
+    }
+  } else {
+    const double smu = P.sqrt_mu;
+    SB_FOR_E {
+      const double v = fma(hl, P.q[e], smu * f2d_bits(P.f1f[e]));
+      P.f[e] = v;
+      ss = fma(v, v, ss);
+    }
   }
   double tot[2];
   if (!prob_reduce2(P, ss, 0.0, tot)) return;
@@ -539,13 +547,14 @@ __global__ void SB_BOUNDS_X sb_x_tc_kernel(const SBProb* __restrict__ probs) {
     P.r1[e] = r1;
     // r2, r3 -= mu lam (Dx w, Dy w) moves q by c2 (raw D^T D w)(e) = c2 (cnt w(e) - the sum of
     // its cnt neighbours inside the image)
-    double nb = 0.0;
-    int cnt = 0;
-    if (c < n - 1) { nb = P.w[e + n]; ++cnt; }
-    if (r < n - 1) { nb = cnt ? nb + P.w[e + 1] : P.w[e + 1]; ++cnt; }
-    if (c >= 1) { nb = cnt ? nb + P.w[e - n] : P.w[e - n]; ++cnt; }
-    if (r >= 1) { nb = cnt ? nb + P.w[e - 1] : P.w[e - 1]; ++cnt; }
-    P.q[e] = fma(c2, fma((double)cnt, w, -nb), P.q[e]);
+    const double wr = c < n - 1 ? P.w[e + n] : 0.0, wd = r < n - 1 ? P.w[e + 1] : 0.0;
+    const double wl = c >= 1 ? P.w[e - n] : 0.0, wu = r >= 1 ? P.w[e - 1] : 0.0;
+    const double nb = (wr + wd) + (wl + wu);
+    // the neighbour count (2, 3 or 4 for n >= 2) as a double from its bit pattern, not a
+    // conversion instruction (which issues to the FP64 pipe)
+    const int cnt = (c < n - 1) + (r < n - 1) + (c >= 1) + (r >= 1);
+    const double cd = __hiloint2double(cnt == 4 ? 0x40100000 : cnt == 3 ? 0x40080000 : 0x40000000, 0);
+    P.q[e] = fma(c2, fma(cd, w, -nb), P.q[e]);
 #if KPSB_X_NORM_F32
     const float xf = d2f_rn_bits(xn);
     sxf = fmaf(xf, xf, sxf);
