@@ -119,6 +119,7 @@ struct SBScal;
 struct SBProb {
   int n, iters, iso, fixed_inner, i_max;
   double mu, sqrt_mu, lam, thr, tau_cgls, tau_sb;
+  double half_lam;        // lambda / 2
   const double* b;
   double *x, *xprev, *w, *f, *r1, *r2, *r3, *z1, *f1, *dx, *dy, *gx, *gy;
   double* q;              // tensor-core path: raw TV part of Ahat^T r (2 (Dx^T r2 + Dy^T r3) / lambda),

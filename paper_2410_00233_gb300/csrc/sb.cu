@@ -61,6 +61,7 @@ struct SBScal {
   double rc_cgls;
   double rc_sb;
   double ww;       // ||w||^2 of the current direction (tensor-core path: from the w kernel)
+  double c1, c2;   // tensor-core path: -step sqrt(mu), -step lambda/2 (the x update's coefficients)
   int active;      // CGLS of the current outer step still running
   int sb_active;   // outer loop still running
   int it;          // CGLS steps in the current outer step
@@ -123,6 +124,34 @@ __device__ __forceinline__ bool prob_reduce2(const SBProb& P, double a, double b
     out[0] = ta;
     out[1] = tb;
   }
+  return true;
+}
+
+// The same for one value (the kernels whose second total would be zero): half the FP64
+// additions of the block and final sums.
+__device__ __forceinline__ bool prob_reduce1(const SBProb& P, double a, double* out) {
+  __shared__ double sa[SB_T];
+  sa[threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double ta = 0.0;
+#pragma unroll
+    for (int i = 0; i < SB_T / 32; ++i) ta += sa[threadIdx.x + 32 * i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ta += __shfl_down_sync(0xffffffffu, ta, o);
+    if (threadIdx.x == 0) P.part[2 * blockIdx.x] = ta;
+  }
+  const unsigned nb = (unsigned)sb_blocks(P.n);
+  if (!last_block_arrive(P.counter, nb)) return false;
+  if (nb <= 32) {
+    if (threadIdx.x < 32) {
+      const double ta = warp_sum_strided(P.part, 2, (int)nb);
+      if (threadIdx.x == 0) out[0] = ta;
+    }
+    return true;
+  }
+  const double ta = block_sum_strided(P.part, 2, (int)nb, sa);
+  if (threadIdx.x == 0) out[0] = ta;
   return true;
 }
 
@@ -450,8 +479,8 @@ __global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int i
   }
   store_xt_tile(P.xt, n, tr, tcol, th, tl, lx, ly, P.xt_bf16);
   SB_TILES_END
-  double tot[2];
-  if (!prob_reduce2(P, (double)wwf, 0.0, tot)) return;
+  double tot[1];
+  if (!prob_reduce1(P, f2d_bits(wwf), tot)) return;
   if (threadIdx.x == 0) P.sc->ww = tot[0];
 }
 
@@ -459,7 +488,7 @@ __global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int i
 // FP32 apply result widened on the integer pipes; tau' = ||f||^2 and delta (steps 8-9).
 __global__ void SB_BOUNDS sb_f_tc_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
-  const double hl = 0.5 * P.lam;
+  const double hl = P.half_lam;
   double ss = 0.0;
   if (P.sqrt_mu == 1.0) {  // mu = 1: f1 as it is (the branch outside the loop: no product per element)
     SB_FOR_E {
@@ -475,8 +504,8 @@ __global__ void SB_BOUNDS sb_f_tc_kernel(const SBProb* __restrict__ probs, int i
       ss = fma(v, v, ss);
     }
   }
-  double tot[2];
-  if (!prob_reduce2(P, ss, 0.0, tot)) return;
+  double tot[1];
+  if (!prob_reduce1(P, ss, tot)) return;
   if (threadIdx.x == 0) f_scalars(P.sc, tot[0], init);
 }
 
@@ -502,7 +531,7 @@ __global__ void SB_BOUNDS sb_zz_tc_kernel(const SBProb* __restrict__ probs) {
     }
   }
   double tot[2];
-  if (!prob_reduce2(P, (double)sz, (double)sd, tot)) return;
+  if (!prob_reduce2(P, f2d_bits(sz), f2d_bits(sd), tot)) return;
   if (threadIdx.x == 0) {
     SBScal* s = P.sc;
     const double hl = 0.5 * P.lam;
@@ -513,6 +542,8 @@ __global__ void SB_BOUNDS sb_zz_tc_kernel(const SBProb* __restrict__ probs) {
       s->step = 0.0;
       s->active = 0;
     }
+    s->c1 = -s->step * P.sqrt_mu;  // once here, not in every thread of the x update
+    s->c2 = -s->step * (0.5 * P.lam);
   }
 }
 
@@ -523,7 +554,7 @@ __global__ void SB_BOUNDS_X sb_x_tc_kernel(const SBProb* __restrict__ probs) {
   (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
   const double mu = P.sc->step;
-  const double c1 = -mu * P.sqrt_mu, c2 = -mu * (0.5 * P.lam);  // r -= mu z, one FMA each
+  const double c1 = P.sc->c1, c2 = P.sc->c2;  // r -= mu z, one FMA each (from the zz kernel)
   // ||w||^2 for RC_CGLS comes from the w kernel (sc->ww)
 #if KPSB_X_NORM_F32
   float sxf = 0.0f;
@@ -567,9 +598,9 @@ __global__ void SB_BOUNDS_X sb_x_tc_kernel(const SBProb* __restrict__ probs) {
   SB_TILES_END
   double tot[2];
 #if KPSB_X_NORM_F32
-  if (!prob_reduce2(P, (double)sxf, 0.0, tot)) return;
+  if (!prob_reduce1(P, f2d_bits(sxf), tot)) return;
 #else
-  if (!prob_reduce2(P, sx, 0.0, tot)) return;
+  if (!prob_reduce1(P, sx, tot)) return;
 #endif
   if (threadIdx.x == 0) {
     SBScal* s = P.sc;
@@ -775,6 +806,7 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   P.mu = mu;
   P.sqrt_mu = sqrt(mu);
   P.lam = lambda;
+  P.half_lam = 0.5 * lambda;
   P.thr = o.threshold_rule == KPSB_THR_PAPER ? beta / (lambda * lambda) : beta / (2.0 * lambda * lambda);
   P.tau_cgls = o.tau_cgls;
   P.tau_sb = o.tau_sb;
