@@ -576,16 +576,17 @@ __global__ void SB_BOUNDS_X sb_x_tc_kernel(const SBProb* __restrict__ probs) {
 #endif
     const double r1 = fma(c1, z1, P.r1[e]);
     P.r1[e] = r1;
-    // r2, r3 -= mu lam (Dx w, Dy w) moves q by c2 (raw D^T D w)(e) = c2 (cnt w(e) - the sum of
-    // its cnt neighbours inside the image)
-    const double wr = c < n - 1 ? P.w[e + n] : 0.0, wd = r < n - 1 ? P.w[e + 1] : 0.0;
-    const double wl = c >= 1 ? P.w[e - n] : 0.0, wu = r >= 1 ? P.w[e - 1] : 0.0;
-    const double nb = (wr + wd) + (wl + wu);
-    // the neighbour count (2, 3 or 4 for n >= 2) as a double from its bit pattern, not a
-    // conversion instruction (which issues to the FP64 pipe)
+    // r2, r3 -= mu lam (Dx w_f, Dy w_f), the TV rows of z = Ahat w_f (the data row moves with
+    // z1 = A_k w_f above), moves q by c2 (raw D^T D w_f)(e) = c2 (cnt w_f(e) - the sum of its cnt
+    // neighbours inside the image): evaluated in FP32 on the FP32 values of the direction,
+    // widened exactly, one FP64 FMA
+    const float wr = c < n - 1 ? P.wf[e + n] : 0.f, wd = r < n - 1 ? P.wf[e + 1] : 0.f;
+    const float wl = c >= 1 ? P.wf[e - n] : 0.f, wu = r >= 1 ? P.wf[e - 1] : 0.f;
+    const float nb = (wr + wd) + (wl + wu);
+    // the neighbour count (2, 3 or 4 for n >= 2) as a float from its bit pattern
     const int cnt = (c < n - 1) + (r < n - 1) + (c >= 1) + (r >= 1);
-    const double cd = __hiloint2double(cnt == 4 ? 0x40100000 : cnt == 3 ? 0x40080000 : 0x40000000, 0);
-    P.q[e] = fma(c2, fma(cd, w, -nb), P.q[e]);
+    const float cf = __int_as_float(cnt == 4 ? 0x40800000 : cnt == 3 ? 0x40400000 : 0x40000000);
+    P.q[e] = fma(c2, f2d_bits(fmaf(cf, P.wf[e], -nb)), P.q[e]);
 #if KPSB_X_NORM_F32
     const float xf = d2f_rn_bits(xn);
     sxf = fmaf(xf, xf, sxf);

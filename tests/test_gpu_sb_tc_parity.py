@@ -5,7 +5,8 @@ keeps every CGLS vector, update and ||f||^2 in FP64; the sums of squares of FP32
 taken in FP32 per thread: ||z||^2 = mu ||z1||^2 + (lambda/2)^2 ||D w_f||^2 of the vector the
 apply saw (w_f = fl32(w), z1 its FP32 product), and ||w_f||^2, ||fl32(x)||^2 of RC_CGLS.
 The TV rows r2, r3 of the residual are carried as q = Dx^T r2 + Dy^T r3 (the only way they
-enter step 7), updated by the image of step 6: the same iteration in exact arithmetic.
+enter step 7), updated by the image of step 6 on the FP32 direction w_f, as the data row is
+(z1 = A w_f): the same iteration in exact arithmetic, ~1e-7 |w| per step besides.
 Against the oracle run on the SAME rounded operator, what is left is per-apply rounding:
 the iterate rounded to FP32 and split in two TF32 parts (2^-22 relative), the split
 intermediate (2^-22), the tensor-core FP32 accumulation (about sqrt(K) 2^-24, K <= 1536
