@@ -1176,7 +1176,33 @@ def main():
             peak = 152 * 2 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             roof = {"bound": "alu", "peak_note": "FP64 FMA: 152 SM x 2 lanes x 2 x max SM clock"}
         roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "frac": (achieved / peak) if achieved else None})
+        tc_prec = {K.P_TF32X2: (4, 1, 2), K.P_TF32X3: (4, 2, 3), K.P_BF16X3: (2, 2, 3), K.P_BF16X2: (2, 1, 2)}
+        if prec in tc_prec and gl and gms > 0 and pa:
+            # Which ceiling binds: per problem and apply the kernel must read the factor tables (two
+            # n x n tables per term, in `fpl` planes of `es` bytes), the split iterate (two planes)
+            # and write the FP32 result; its useful work is 4 k n^3 flops (Sec. 4.2).  Below the
+            # ridge (the split mode's useful tensor peak over HBM) the apply is HBM-bound.
+            es, fpl, prods = tc_prec[prec]
+            nn = float(N_IMG) * N_IMG
+            sum_k = kn3 / float(N_IMG) ** 3
+            alg_bytes = sum_k * 2 * nn * es * fpl + pa * (2 * nn * es + 4 * nn)
+            hbm_peak = peaks.get("hbm_gbs", 6800.0)
+            ach_gbs = alg_bytes / (gms / 1000.0) / 1e9
+            oi = gflops / alg_bytes
+            ridge = (peak / prods) * 1e12 / (hbm_peak * 1e9)
+            tensor_view = {"achieved_tflops": achieved, "peak_tflops": peak, "frac": roof["frac"],
+                           "peak_note": roof["peak_note"],
+                           "useful_ceiling_note": "a split mode does %d products per useful one" % prods}
+            hbm_view = {"achieved_gbs": ach_gbs, "peak_gbs": hbm_peak, "frac": ach_gbs / hbm_peak,
+                        "algorithmic_bytes_per_launch": alg_bytes / gl,
+                        "peak_note": "of measured" if "hbm_gbs" in peaks else "of fallback"}
+            if oi < ridge:
+                roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": ach_gbs / hbm_peak, "peak_note": hbm_view["peak_note"]}
+            roof.update({"operational_intensity_flop_per_byte": oi, "ridge_flop_per_byte": ridge,
+                         "tensor_view": tensor_view, "hbm_view": hbm_view})
+        roof.update({"traffic": traffic,
                      "traffic_note": "bytes per launch (DRAM read + write): ncu capture of the same kernel on "
                                      "this workload with all 256 problems active, times the replay's mean "
                                      "active fraction" if traffic is not None else
