@@ -27,17 +27,20 @@ namespace kpsb {
 
 static constexpr int SB_T = 256;
 // Minimum resident blocks per SM requested from the compiler for the vector kernels
-// (register cap 65536 / (SB_T * KPSB_SB_MIN_BLOCKS)).
-// Measured on the 256-request medium batch (4 concurrent parts): 6 (40 registers; a few
-// bytes of spill in the ||z||^2 kernel) beats 4 (64 registers) by 3 %: these kernels wait on
-// memory, and more resident warps hide more of it.
+// (register cap 65536 / (SB_T * blocks)).  They wait on memory latency, so more resident warps
+// pay: the tensor-core path's kernels run 8 blocks (32 registers, a few bytes of spill; on the
+// 256-request step 108.1 deblurs/s against 106.0 with 6 blocks, x update 684 -> 575 ms); the
+// FP64 / FP32 path's kernels keep 6 (at 32 registers their spills grow to 48-80 bytes).
 #ifndef KPSB_SB_MIN_BLOCKS
 #define KPSB_SB_MIN_BLOCKS 6
 #endif
 #define SB_BOUNDS __launch_bounds__(SB_T, KPSB_SB_MIN_BLOCKS)
+#ifndef KPSB_SB_MIN_BLOCKS_TC
+#define KPSB_SB_MIN_BLOCKS_TC 8
+#endif
+#define SB_BOUNDS_TC __launch_bounds__(SB_T, KPSB_SB_MIN_BLOCKS_TC)
 #ifndef KPSB_SB_MIN_BLOCKS_X
-#define KPSB_SB_MIN_BLOCKS_X 6  // 40 registers and a few bytes of spill in the tensor-core x update:
-                                // measured 100.0 vs 98.5 deblurs/s (5 blocks, 48 registers)
+#define KPSB_SB_MIN_BLOCKS_X 8
 #endif
 #define SB_BOUNDS_X __launch_bounds__(SB_T, KPSB_SB_MIN_BLOCKS_X)  // x and r update kernels
 // once-per-outer-step kernels and the CUDA-core path's x update, which would spill under
@@ -427,7 +430,7 @@ __device__ __forceinline__ float put_split(float (*th)[33], float (*tl)[33], int
 // Outer step start (as sb_outer_init_kernel) plus the split planes of r1 = sqrt(mu) b.  The
 // tensor-core path keeps the TV rows r2, r3 of the residual only as q = 2 (Dx^T r2 + Dy^T r3)
 // / lambda (the raw differences): they enter the iteration only through Ahat^T r (step 7).
-__global__ void SB_BOUNDS sb_outer_init_tc_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS_TC sb_outer_init_tc_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->sb_active)
   (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
@@ -460,7 +463,7 @@ __global__ void SB_BOUNDS sb_outer_init_tc_kernel(const SBProb* __restrict__ pro
 
 // w = f + delta w (step 10; delta from the f kernel), init: w = f (step 2, w not read), and
 // the planes and the FP32 value w_f of w for the next forward apply and ||z||^2.
-__global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int init) {
+__global__ void SB_BOUNDS_TC sb_w_tc_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
   (void)N; (void)e_hi;
   __shared__ float th[32][33], tl[32][33];
@@ -486,7 +489,7 @@ __global__ void SB_BOUNDS sb_w_tc_kernel(const SBProb* __restrict__ probs, int i
 
 // f = Ahat^T r = sqrt(mu) f1 + (lambda/2) q (step 7 / init) on the tensor-core path, f1 the
 // FP32 apply result widened on the integer pipes; tau' = ||f||^2 and delta (steps 8-9).
-__global__ void SB_BOUNDS sb_f_tc_kernel(const SBProb* __restrict__ probs, int init) {
+__global__ void SB_BOUNDS_TC sb_f_tc_kernel(const SBProb* __restrict__ probs, int init) {
   SB_PROLOGUE(P.sc->active)
   const double hl = P.half_lam;
   double ss = 0.0;
@@ -513,7 +516,7 @@ __global__ void SB_BOUNDS sb_f_tc_kernel(const SBProb* __restrict__ probs, int i
 // the forward apply saw and z1 = A_k w_f its FP32 result, so both sums,
 // |z|^2 = mu |z1|^2 + (lambda/2)^2 |raw D w_f|^2, are sums of squares of FP32 values: taken
 // in FP32 per thread (SB_EPT elements), the partials in FP64.  No FP64 arithmetic per element.
-__global__ void SB_BOUNDS sb_zz_tc_kernel(const SBProb* __restrict__ probs) {
+__global__ void SB_BOUNDS_TC sb_zz_tc_kernel(const SBProb* __restrict__ probs) {
   SB_PROLOGUE(P.sc->active)
   float sz = 0.0f, sd = 0.0f;
   SB_FOR_RC {
