@@ -344,6 +344,28 @@ def serve_main(args):
 SERVE_SIZES = (128, 256, 512, 1024)
 SERVE_RATES = (10.0, 50.0, 500.0)
 
+# Arithmetic of a split mode's KP apply: bytes per element of a factor-table plane and of an
+# iterate plane, table planes, tensor products per useful product.
+SPLIT_MODES = {"tf32x2": (4, 1, 2), "tf32x3": (4, 2, 3), "bf16x3": (2, 2, 3), "bf16x2": (2, 1, 2)}
+
+
+def apply_roofline(mode: str, n: int, problem_applies: float, sum_kn3: float, flops: float, seconds: float,
+                   tensor_peak_tflops: float, hbm_peak_gbs: float) -> dict:
+    """Which ceiling binds a batch of KP applies, and how close they came.  Per problem and
+    apply the kernel must read the factor tables (two n x n tables per term, in `fpl` planes),
+    the split iterate (two planes) and write the FP32 result; its useful work is 4 k n^3 flops
+    (Sec. 4.2).  Below the ridge (the mode's useful tensor peak, the dtype's peak over its
+    products per useful product, divided by HBM bandwidth) the apply is HBM-bound."""
+    es, fpl, prods = SPLIT_MODES[mode]
+    nn = float(n) * n
+    sum_k = sum_kn3 / float(n) ** 3
+    nbytes = sum_k * 2 * nn * es * fpl + problem_applies * (2 * nn * es + 4 * nn)
+    intensity = flops / nbytes
+    ridge = (tensor_peak_tflops / prods) * 1e12 / (hbm_peak_gbs * 1e9)
+    return {"bytes": nbytes, "achieved_gbs": nbytes / seconds / 1e9, "intensity": intensity, "ridge": ridge,
+            "bound": "hbm" if intensity < ridge else "tensor"}
+
+
 
 def _isnr(x, b, xt):
     import numpy as np
@@ -1177,27 +1199,19 @@ def main():
             roof = {"bound": "alu", "peak_note": "FP64 FMA: 152 SM x 2 lanes x 2 x max SM clock"}
         roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None})
-        tc_prec = {K.P_TF32X2: (4, 1, 2), K.P_TF32X3: (4, 2, 3), K.P_BF16X3: (2, 2, 3), K.P_BF16X2: (2, 1, 2)}
+        tc_prec = {K.P_TF32X2: "tf32x2", K.P_TF32X3: "tf32x3", K.P_BF16X3: "bf16x3", K.P_BF16X2: "bf16x2"}
         if prec in tc_prec and gl and gms > 0 and pa:
-            # Which ceiling binds: per problem and apply the kernel must read the factor tables (two
-            # n x n tables per term, in `fpl` planes of `es` bytes), the split iterate (two planes)
-            # and write the FP32 result; its useful work is 4 k n^3 flops (Sec. 4.2).  Below the
-            # ridge (the split mode's useful tensor peak over HBM) the apply is HBM-bound.
-            es, fpl, prods = tc_prec[prec]
-            nn = float(N_IMG) * N_IMG
-            sum_k = kn3 / float(N_IMG) ** 3
-            alg_bytes = sum_k * 2 * nn * es * fpl + pa * (2 * nn * es + 4 * nn)
             hbm_peak = peaks.get("hbm_gbs", 6800.0)
-            ach_gbs = alg_bytes / (gms / 1000.0) / 1e9
-            oi = gflops / alg_bytes
-            ridge = (peak / prods) * 1e12 / (hbm_peak * 1e9)
+            rl = apply_roofline(tc_prec[prec], N_IMG, pa, kn3, gflops, gms / 1000.0, peak, hbm_peak)
+            alg_bytes, ach_gbs, oi, ridge = rl["bytes"], rl["achieved_gbs"], rl["intensity"], rl["ridge"]
+            prods = SPLIT_MODES[tc_prec[prec]][2]
             tensor_view = {"achieved_tflops": achieved, "peak_tflops": peak, "frac": roof["frac"],
                            "peak_note": roof["peak_note"],
                            "useful_ceiling_note": "a split mode does %d products per useful one" % prods}
             hbm_view = {"achieved_gbs": ach_gbs, "peak_gbs": hbm_peak, "frac": ach_gbs / hbm_peak,
                         "algorithmic_bytes_per_launch": alg_bytes / gl,
                         "peak_note": "of measured" if "hbm_gbs" in peaks else "of fallback"}
-            if oi < ridge:
+            if rl["bound"] == "hbm":
                 roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": ach_gbs / hbm_peak, "peak_note": hbm_view["peak_note"]}
             roof.update({"operational_intensity_flop_per_byte": oi, "ridge_flop_per_byte": ridge,
