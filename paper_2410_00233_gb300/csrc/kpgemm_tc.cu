@@ -759,6 +759,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TCJob* __restrict
 // 2..5 = converter and epilogue (TMEM lane quarters 2, 3, 0, 1).
 // ------------------------------------------------------------------------------------------
 static constexpr int FUSED_BN = 64;
+static constexpr int FUSED_MAX_N = 384;  // largest n offered to the fused kernels (a multiple of 128)
 
 template <int BN, int FPL>
 struct FCfg {
@@ -1347,8 +1348,8 @@ static constexpr int s1l_stages(int fpl) { return S1L_BN == 128 ? S1_STAGES : (f
 static inline bool s1_large(int n) { return n > 768; }
 
 // Stage 2 where the two-stage kernel is the only variant for (n, precision), so its bits need
-// not match the fused and resident kernels': BF16 planes, or TF32 with n > 768 or n not a
-// multiple of 128.  From n = 512 on it takes 128-column output tiles (half the operand bytes
+// not match the fused and resident kernels': BF16 planes, or TF32 with n > FUSED_MAX_N or n not
+// a multiple of 128.  From n = 512 on it takes 128-column output tiles (half the operand bytes
 // per MMA of 64-column tiles) and splits K into a fixed number of ranges, set by n alone so
 // that about 128 CTAs share one problem; the last CTA of a tile to finish adds the FP32
 // partial tiles in range order.  The split depends on n only, so a problem gives the same bits
@@ -1360,7 +1361,7 @@ struct S2Shape {
 };
 static constexpr int S2W_BN = 128, S2W_STAGES = 3;
 static S2Shape s2_shape(int n, bool bf) {
-  const bool only_two_stage = bf || n % 128 != 0 || n > 768;
+  const bool only_two_stage = bf || n % 128 != 0 || n > FUSED_MAX_N;
   if (!only_two_stage || n < 512) return {S2_BN, 1};
   const int tiles = ((n + 127) / 128) * ((n + S2W_BN - 1) / S2W_BN);
   return {S2W_BN, std::max(1, std::min(8, (128 + tiles / 2) / tiles))};
@@ -1414,15 +1415,17 @@ static bool variant_ok(int v, int n, int prec) {
   const bool tf = !prec_bf16(prec) && n % 128 == 0;
   switch (v) {
     case TCV_TWO_STAGE: return true;
-    case TCV_FUSED64: return tf && (n / 128 + 2) * 64 <= 512;
-    case TCV_FUSED32: return tf && n <= 768;
+    case TCV_FUSED64: return tf && n <= FUSED_MAX_N;
+    case TCV_FUSED32: return tf && n <= FUSED_MAX_N;
     case TCV_RESIDENT: return tf && n == 128;
     default: return false;
   }
 }
 
-// Fused kernel where its TMEM fits (R + 2) x BN columns: n <= 768 with BN = 64.
-static bool fused_ok(int n) { return n % 128 == 0 && (n / 128 + 2) * FUSED_BN <= 512; }
+// Fused kernel up to n = FUSED_MAX_N (its TMEM would fit (R + 2) x BN columns up to n = 768, but
+// from n = 512 on a fused CTA re-reads every stage-2 table for its 64 or 32 output columns, and
+// the two-stage kernel with a K split is the better apply there).
+static bool fused_ok(int n) { return n % 128 == 0 && n <= FUSED_MAX_N && (n / 128 + 2) * FUSED_BN <= 512; }
 
 
 template <int BN, int STAGES, int STAGE, int FPL, bool BF>
