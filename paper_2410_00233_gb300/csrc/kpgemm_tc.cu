@@ -1349,20 +1349,21 @@ static inline bool s1_large(int n) { return n > 768; }
 
 // Stage 2 where the two-stage kernel is the only variant for (n, precision), so its bits need
 // not match the fused and resident kernels': BF16 planes, or TF32 with n > FUSED_MAX_N or n not
-// a multiple of 128.  From n = 512 on it takes 128-column output tiles (half the operand bytes
+// a multiple of 128.  From n = 256 on it takes 128-column output tiles (half the operand bytes
 // per MMA of 64-column tiles) and splits K into a fixed number of ranges, set by n alone so
-// that about 128 CTAs share one problem; the last CTA of a tile to finish adds the FP32
-// partial tiles in range order.  The split depends on n only, so a problem gives the same bits
-// alone and in any batch.  Measured on one BF16x3 request (20 outer steps): n = 1024
-// 0.443 -> 0.387 s (split 2), n = 512 0.219 -> 0.173 s (split 8); 256-column tiles (two
-// pipeline stages) and other splits were slower.
+// that up to about 128 CTAs share one problem (at most 8 ranges); the last CTA of a tile to
+// finish adds the FP32 partial tiles in range order.  The split depends on n only, so a
+// problem gives the same bits alone and in any batch.  Measured on one BF16x3 request (20
+// outer steps): n = 1024 0.443 -> 0.387 s (split 2), n = 512 0.219 -> 0.173 s (split 8),
+// n = 384 0.130 -> 0.113 s, n = 256 0.232 -> 0.166 s; 256-column tiles (two pipeline stages)
+// and other splits were slower.
 struct S2Shape {
   int bn, split;
 };
 static constexpr int S2W_BN = 128, S2W_STAGES = 3;
 static S2Shape s2_shape(int n, bool bf) {
   const bool only_two_stage = bf || n % 128 != 0 || n > FUSED_MAX_N;
-  if (!only_two_stage || n < 512) return {S2_BN, 1};
+  if (!only_two_stage || n < 256) return {S2_BN, 1};
   const int tiles = ((n + 127) / 128) * ((n + S2W_BN - 1) / S2W_BN);
   return {S2W_BN, std::max(1, std::min(8, (128 + tiles / 2) / tiles))};
 }

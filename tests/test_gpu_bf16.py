@@ -111,10 +111,11 @@ def test_bf16_and_masked_apply_count_their_work():
             K.kpsb_gemm_timing(False)
 
 
-@pytest.mark.parametrize("prec_name,sizes", [("P_BF16X3", (512, 512, 640)), ("P_TF32X2", (1024, 520))])
+@pytest.mark.parametrize("prec_name,sizes", [("P_BF16X3", (512, 512, 640)), ("P_BF16X3", (256, 384)),
+                                             ("P_TF32X2", (1024, 520))])
 def test_split_stage2_batched_equals_alone(prec_name, sizes):
     """The two-stage apply's stage 2 splits K into ranges fixed by n where it is the only
-    variant (BF16 modes; TF32 at n > 768 or n not a multiple of 128) and the tile's last CTA
+    variant (BF16 modes; TF32 at n > 384 or n not a multiple of 128) and the tile's last CTA
     adds the partial tiles in range order: problems with different k in one batched solve give
     the bits of their solves alone, and the apply stays within the oracle bounds above."""
     need_gpu()
