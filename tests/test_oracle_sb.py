@@ -102,15 +102,19 @@ def _chambolle_pock(A, b, mu, beta, iso, iters):
     return O.array(x, n, n)
 
 
-@pytest.mark.parametrize("iso", [False, True])
-def test_split_bregman_reaches_tv_minimiser(iso):
+@pytest.mark.parametrize("iso,mu", [(False, 1.0), (True, 1.0), (False, 0.4), (True, 2.5)])
+def test_split_bregman_reaches_tv_minimiser(iso, mu):
+    # mu != 1 separates the minimisers (they move by ~0.1 between mu = 1 and 0.4 or 2.5 here),
+    # so a sqrt(mu) dropped from the operator or the data block of A-hat fails
     n = 8
     A, Af, ATf, b, _ = _small_problem(n)
-    mu, lam, beta = 1.0, 0.3, 0.01
+    lam, beta = 0.3, 0.01
     x_cp = _chambolle_pock(A, b, mu, beta, iso, 60000)
     res = O.split_bregman(Af, ATf, b, mu, lam, beta, iso, iters=1500, tau_cgls=1e-15, i_max=400)
     tol = 1e-4 if iso else 1e-10  # isotropic SB converges more slowly
     assert np.abs(res.x - x_cp).max() < tol
+    if mu != 1.0:
+        assert np.abs(_chambolle_pock(A, b, 1.0, beta, iso, 60000) - x_cp).max() > 1e-2
     # the printed threshold 1/gamma solves the problem with 2*beta instead
     res_p = O.split_bregman(Af, ATf, b, mu, lam, beta, iso, iters=300, tau_cgls=1e-15, i_max=400,
                             threshold_rule="paper")
