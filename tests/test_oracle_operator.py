@@ -39,6 +39,18 @@ def test_reflexive_is_half_sample_mirror():
     np.testing.assert_array_equal(Bz[0], 0.0)
 
 
+def test_reflexive_extension_bounds():
+    # one half-sample reflection per side: -n..-1 -> n-1..0 and n..2n-1 -> n-1..0; a PSF
+    # reaching further than the image is refused
+    n = 5
+    assert [O.ext(q, n, O.BC_REFLEXIVE) for q in range(-n, 0)] == list(range(n - 1, -1, -1))
+    assert [O.ext(q, n, O.BC_REFLEXIVE) for q in range(n, 2 * n)] == list(range(n - 1, -1, -1))
+    assert [O.ext(q, n, O.BC_ZERO) for q in (-1, n)] == [None, None]
+    for q in (-n - 1, 2 * n):
+        with pytest.raises(ValueError):
+            O.ext(q, n, O.BC_REFLEXIVE)
+
+
 def test_rearrangement_of_kronecker_product():
     # R(B (x) C) = vec(B) vec(C)^T (the identity behind Theorem 2.1)
     g = I.rng(5)
@@ -61,6 +73,32 @@ def test_factored_R_equals_explicit_rearrangement(bc, n, s):
     V = g.standard_normal((n * n, 3))
     np.testing.assert_allclose(O.r_apply(F, V), R @ V, rtol=1e-13, atol=1e-14)
     np.testing.assert_allclose(O.r_apply_t(F, V), R.T @ V, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("bc", [O.BC_ZERO, O.BC_REFLEXIVE])
+@pytest.mark.parametrize("shape", [(3, 7), (7, 3), (5, 1)])
+def test_non_square_psf(bc, shape):
+    # s0 != s1 separates the row (y) factor from the column (x) factor: the blur against
+    # scipy's 2-D convolution, and R(A) from its factors against the explicit rearrangement
+    n = 9
+    g = I.rng(300 + 10 * shape[0] + shape[1] + bc)
+    psf = g.uniform(0.05, 1.0, size=shape)
+    psf /= psf.sum()
+    X = g.uniform(size=(n, n))
+    A = O.blur_matrix(psf, n, bc)
+    ref = convolve2d(X, psf, mode="same", boundary="fill" if bc == O.BC_ZERO else "symm")
+    np.testing.assert_allclose(O.array(A @ O.vec(X), n, n), ref, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(O.blur(psf, X, bc), ref, rtol=0, atol=1e-14)
+    R = O.rearrange(A, n, n, n, n)
+    F = O.r_factors(psf, n, bc)
+    np.testing.assert_allclose(F.Kx @ (F.P.T @ F.Ky.T.toarray()), R, rtol=0, atol=1e-15)
+    V = g.standard_normal((n * n, 2))
+    np.testing.assert_allclose(O.r_apply(F, V), R @ V, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(O.r_apply_t(F, V), R.T @ V, rtol=1e-13, atol=1e-14)
+    sv = np.linalg.svd(R, compute_uv=False)
+    r = min(shape)
+    np.testing.assert_allclose(O.r_sigma_closed_form(F)[:r], sv[:r], rtol=0, atol=1e-12 * sv[0])
+    assert sv[r] < 1e-12 * sv[0]  # rank <= min(s0, s1)
 
 
 @pytest.mark.parametrize("bc", [O.BC_ZERO, O.BC_REFLEXIVE])
@@ -157,6 +195,8 @@ def test_metrics_special_cases():
     xt = g.uniform(size=(5, 5))
     b = xt + 0.1 * g.standard_normal((5, 5))
     assert O.rel_error(xt, xt) == 0.0
+    assert O.rel_error(3 * xt, xt) == pytest.approx(2.0, rel=1e-14)  # error measured in ||x_true||
+    assert O.rel_error(np.zeros_like(xt), xt) == pytest.approx(1.0, rel=1e-14)
     assert abs(O.isnr(b, b, xt)) < 1e-12  # x = b: no improvement
     x_half = xt + 0.5 * (b - xt)  # error halved: +6.02 dB
     np.testing.assert_allclose(O.isnr(x_half, b, xt), 20 * np.log10(2.0), rtol=1e-12)

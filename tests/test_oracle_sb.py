@@ -77,6 +77,42 @@ def test_cgls_solves_augmented_least_squares():
     assert res3.iters == 7
 
 
+@pytest.mark.parametrize("i", [1, 3, 6])
+def test_cgls_iterate_minimises_over_the_krylov_space(i):
+    # the i-th CGLS iterate from x = 0 is argmin ||Ahat x - bhat|| over the Krylov space
+    # K_i(Ahat^T Ahat, Ahat^T bhat) (textbook property of CG on the normal equations); the
+    # reference solves that i-dimensional least-squares problem in an orthonormal basis
+    n = 8
+    A, Af, ATf, b, _ = _small_problem(n)
+    mu, lam = 0.7, 0.3
+    g = I.rng(12)
+    hx, hy = g.standard_normal((n, n)), g.standard_normal((n, n))
+    L = O.L_matrix(n)
+    Ah = np.vstack([math.sqrt(mu) * A, lam * np.kron(L, np.eye(n)), lam * np.kron(np.eye(n), L)])
+    bh = np.concatenate([math.sqrt(mu) * O.vec(b), lam * O.vec(hx), lam * O.vec(hy)])
+    G = Ah.T @ Ah
+    basis = []
+    v = Ah.T @ bh
+    for _ in range(i):  # Lanczos-style orthonormal basis with full reorthogonalisation
+        for q in basis:
+            v = v - (q @ v) * q
+        for q in basis:
+            v = v - (q @ v) * q
+        basis.append(v / np.linalg.norm(v))
+        v = G @ basis[-1]
+    Qk = np.stack(basis, axis=1)
+    x_ref = Qk @ np.linalg.lstsq(Ah @ Qk, bh, rcond=None)[0]
+
+    def Ahat(X):
+        return (math.sqrt(mu) * Af(X), lam * O.Dx(X), lam * O.Dy(X))
+
+    def AhatT(r):
+        return math.sqrt(mu) * ATf(r[0]) + lam * O.Dx_t(r[1]) + lam * O.Dy_t(r[2])
+
+    res = O.cgls(Ahat, AhatT, (math.sqrt(mu) * b, lam * hx, lam * hy), (n, n), i_max=i, fixed=True)
+    np.testing.assert_allclose(O.vec(res.x), x_ref, rtol=0, atol=1e-10 * np.abs(x_ref).max())
+
+
 def _chambolle_pock(A, b, mu, beta, iso, iters):
     """Primal-dual solve of min mu||Ax-b||^2 + beta TV(x) (a different algorithm)."""
     n = b.shape[0]
@@ -131,3 +167,39 @@ def test_split_bregman_stopping_and_counts():
     assert res2.l_end == 4 and res2.iota_total == 24
     # deblurring improves on the data (positive ISNR) for this well-posed toy case
     assert O.isnr(res.x, b, xt) > 0
+
+
+def test_relative_changes_are_the_steps_between_iterates():
+    # RC_CGLS (5.1) is the relative change of the CGLS iterate and RC_SB (5.2) that of the
+    # outer iterate against the previous one, from x^(0) = b (Alg. 3/4 initialisation):
+    # both checked against the differences of consecutive iterates
+    n = 8
+    A, Af, ATf, b, _ = _small_problem(n)
+    mu, lam = 0.7, 0.3
+    g = I.rng(9)
+    hx, hy = g.standard_normal((n, n)), g.standard_normal((n, n))
+
+    def Ahat(X):
+        return (math.sqrt(mu) * Af(X), lam * O.Dx(X), lam * O.Dy(X))
+
+    def AhatT(r):
+        return math.sqrt(mu) * ATf(r[0]) + lam * O.Dx_t(r[1]) + lam * O.Dy_t(r[2])
+
+    bh = (math.sqrt(mu) * b, lam * hx, lam * hy)
+    xs = [O.cgls(Ahat, AhatT, bh, (n, n), i_max=i, fixed=True) for i in (1, 5, 6)]
+    assert xs[0].rc == pytest.approx(1.0, rel=1e-12)  # from x^(0) = 0 the first step is all change
+    step = np.linalg.norm(xs[2].x - xs[1].x) / np.linalg.norm(xs[2].x)
+    assert xs[2].rc == pytest.approx(step, rel=1e-9)
+    # the tolerance stop ends at the first iteration whose change is below tau
+    rcs = [O.cgls(Ahat, AhatT, bh, (n, n), i_max=i, fixed=True).rc for i in range(1, 7)]
+    tau = rcs[5] * (1 + 1e-9)
+    first = next(i for i, r in enumerate(rcs, start=1) if r < tau)
+    assert O.cgls(Ahat, AhatT, bh, (n, n), i_max=50, tau=tau).iters == first
+
+    sb = [O.split_bregman(Af, ATf, b, 1.0, 0.3, 0.01, False, iters=i, i_max=30, fixed_inner=True)
+          for i in (1, 2)]
+    assert sb[0].rc_sb == pytest.approx(np.linalg.norm(sb[0].x - b) / np.linalg.norm(b), rel=1e-12)
+    assert sb[1].rc_sb == pytest.approx(
+        np.linalg.norm(sb[1].x - sb[0].x) / np.linalg.norm(sb[0].x), rel=1e-9)
+    assert [h["rc_sb"] for h in sb[1].history][0] == pytest.approx(sb[0].rc_sb, rel=1e-12)
+

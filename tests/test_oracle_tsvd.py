@@ -116,6 +116,45 @@ def test_nu_rule_on_known_bidiagonal():
     assert ts3.k == 3 and ts3.kp == 5
 
 
+def test_nu_rule_ignores_a_single_rise_of_zeta():
+    # zeta_j = alpha_j t_j decays non-monotonically; the rule watches the two-term geometric
+    # mean nu_j instead (Sec. 2.2).  Unit alpha and t_j = zeta_j: zeta rises at j = 4
+    # (0.35 > 0.3) while nu_3 > nu_4 > nu_5 > nu_6 < nu_7, so k = 6, not 3.
+    zeta = [0.5, 0.3, 0.35, 0.2, 0.1, 0.3, 0.05, 0.02, 0.01, 0.005, 0.002, 0.001]  # j = 2..13
+    alpha = [1.0] * len(zeta)
+    C = _bidiag_problem(alpha, zeta)
+    e1 = np.zeros(C.shape[0])
+    e1[0] = 1.0
+    ts = O.egkb(lambda v: C @ v, lambda u: C.T @ u, e1, k=10, p=2, tau=1e-6)
+    nu = {j: math.sqrt(zeta[j - 2] * zeta[j - 3]) for j in range(3, 9)}
+    assert nu[3] > nu[4] > nu[5] > nu[6] < nu[7]
+    assert ts.k == 6 and ts.kp == 8
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_rsvd_is_rayleigh_ritz_on_the_power_range(q):
+    # Alg. 2 with q power steps returns the Rayleigh-Ritz values of R(A) on
+    # range((R R^T)^q R F): here k_p = 5 < rank 9, so the values depend on q
+    n, s, k, kp = 10, 9, 3, 5
+    g = I.rng(70 + q)
+    psf = I.psf_random(s, g)
+    F = O.r_factors(psf, n, O.BC_ZERO)
+    B, BT = _ops(F)
+    R = O.rearrange(O.blur_matrix(psf, n, O.BC_ZERO), n, n, n, n)
+    Om = I.gaussian((n * n, kp), g)
+    Y = R @ Om
+    for _ in range(q):
+        Y = R @ (R.T @ Y)
+    Uy, sy, _ = np.linalg.svd(Y, full_matrices=False)  # orthonormal basis of range(Y)
+    ref = np.linalg.svd(Uy.T @ R, compute_uv=False)[:k]
+    ts = O.rsvd(B, BT, Om, k=k, q=q)
+    np.testing.assert_allclose(ts.sigma, ref, rtol=0, atol=1e-9 * ref[0])
+    if q < 2:  # each power step moves the values toward the true ones
+        nxt = O.rsvd(B, BT, Om, k=k, q=q + 1).sigma
+        sv = np.linalg.svd(R, compute_uv=False)[:k]
+        assert np.abs(nxt - sv).max() < np.abs(ts.sigma - sv).max()
+
+
 @pytest.mark.parametrize("bc", [O.BC_ZERO, O.BC_REFLEXIVE])
 def test_rsvd_exact_when_oversampled_past_rank(bc):
     n, s = 16, 5
