@@ -145,7 +145,8 @@ typedef struct {
  *              (nu_i < tau*nu_3), capped at k <= 30.
  *   method     KPSB_EGKB or KPSB_RSVD.
  *   out        receives a new handle (device factors resident until kp_free).
- * The effective k may be smaller than asked when R(A) has smaller rank (rank <= s0*s1):
+ * The effective k may be smaller than asked when R(A) has smaller rank (R(A) = Kx P^T Ky^T,
+ * so rank R(A) <= rank P <= min(s0, s1)):
  * the GKB recurrence stops at breakdown and RSVD drops null directions; kp_info reports
  * the k and k_p used.  Errors: EINVAL (sizes, n < 2, s > 2n, k < 1, k_p > 64),
  * ENOMEM, ECUDA, EBREAKDOWN (R(A) = 0).
