@@ -229,8 +229,10 @@ typedef struct {
 
 /* Builds `count` handles: the problems of kp_build's one-block path share one launch pair
  * per chunk of 256 (one thread block each), the others run concurrently on internal streams.
- * outs[i] is NULL where problem i failed; the first error is returned.  Each handle equals
- * the one kp_build gives for the same problem alone. */
+ * outs[i] is NULL where problem i failed; the first error is returned.  The other problems
+ * are still built, and their handles belong to the caller (kp_free each non-NULL outs[i],
+ * also after an error).  Each handle equals the one kp_build gives for the same problem
+ * alone. */
 kpsb_status kp_build_batched(int count, const kpsb_problem* probs, kpsb_kp_t* outs);
 
 typedef struct {

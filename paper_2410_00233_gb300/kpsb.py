@@ -391,8 +391,16 @@ def kp_build_batched(problems) -> list:
         arr[i].method = int(pr.get("method", EGKB))
         arr[i].opts = o
     outs = (C.c_void_p * len(problems))()
-    _check("kp_build_batched", lib().kp_build_batched(len(problems), arr, outs))
-    return [KP(outs[i], int(pr["n"])) for i, pr in enumerate(problems)]
+    code = lib().kp_build_batched(len(problems), arr, outs)
+    # every non-NULL handle is the caller's, also when another problem failed
+    kps = [KP(outs[i], int(pr["n"])) if outs[i] else None for i, pr in enumerate(problems)]
+    if code != KPSB_OK:
+        err = KpsbError("kp_build_batched", code, last_error())
+        for kp in kps:
+            if kp is not None:
+                kp.close()
+        raise err
+    return kps
 
 
 def sb_solve_batched(jobs, on_device: bool = False, **opts):

@@ -61,3 +61,28 @@ def test_psf_must_be_two_dimensional():
         K.kp_build(np.ones(9), 8, K.BC_ZERO, 2, K.EGKB)
     with pytest.raises(ValueError):
         K.kp_dense_blur(np.ones((0, 3)), 8, K.BC_ZERO)
+
+
+def test_batched_build_frees_the_built_handles_when_one_problem_fails(monkeypatch):
+    """kp_build_batched returns the first error but still builds the other problems; the
+    binding frees those handles before it raises (a fake library stands in for the C ABI)."""
+    freed = []
+
+    class FakeLib:
+        def kp_build_batched(self, count, arr, outs):
+            outs[0], outs[1], outs[2] = 0x1000, None, 0x2000  # problem 1 failed
+            return -1
+
+        def kp_free(self, ptr):
+            freed.append(ptr.value)
+
+        def kpsb_last_error(self):
+            return b"problem 1: rank 0 outside [1, 64]"
+
+    monkeypatch.setattr(K, "lib", lambda: FakeLib())
+    psf = np.ones((3, 3)) / 9
+    probs = [dict(psf=psf, n=8, bc=K.BC_ZERO, rank_or_tol=4) for _ in range(3)]
+    with pytest.raises(K.KpsbError) as e:
+        K.kp_build_batched(probs)
+    assert e.value.code == -1 and "problem 1" in str(e.value)
+    assert sorted(freed) == [0x1000, 0x2000]
