@@ -78,3 +78,59 @@ def test_invalid_arguments_fail_without_touching_the_gpu():
     with pytest.raises(K.KpsbError) as e:
         K.kp_build_dense(np.eye(16), 4, 2.0, K.EGKB, fp64=True)  # explicit operators: SP TSVD only
     assert e.value.code == -1
+
+
+def test_binding_constants_match_the_header():
+    """Every status code and enum value the binding hard-codes equals the header's."""
+    from paper_2410_00233_gb300 import kpsb as K
+
+    txt = open(os.path.join(ROOT, "include", "kpsb.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    hdr = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(KPSB_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt)}
+    block = re.search(r"typedef enum \{(.*?)\} kpsb_status;", txt, flags=re.S).group(1)
+    status = {int(v): name for name, v in re.findall(r"KPSB_([A-Z0-9_]+)\s*=\s*(-?\d+)", block)}
+    assert status == K.STATUS
+    for py, c in [("BC_ZERO", "KPSB_BC_ZERO"), ("BC_REFLEXIVE", "KPSB_BC_REFLEXIVE"),
+                  ("EGKB", "KPSB_EGKB"), ("RSVD", "KPSB_RSVD"), ("ANISO", "KPSB_ANISO"),
+                  ("ISO", "KPSB_ISO"), ("P_FP64", "KPSB_P_FP64"), ("P_FP32", "KPSB_P_FP32"),
+                  ("P_TF32X3", "KPSB_P_TF32X3"), ("P_TF32X2", "KPSB_P_TF32X2"),
+                  ("P_BF16X3", "KPSB_P_BF16X3"), ("P_BF16X2", "KPSB_P_BF16X2"),
+                  ("THR_EXACT", "KPSB_THR_EXACT"), ("THR_PAPER", "KPSB_THR_PAPER"),
+                  ("KPSB_OK", "KPSB_OK")]:
+        assert getattr(K, py) == hdr[c], py
+    assert int(re.search(r"#define KPSB_MAX_N (\d+)", txt).group(1)) == 16384
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and every field offset of the header's structs, as a C compiler lays them out,
+    equal the binding's ctypes structures (a C program built against include/kpsb.h)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2410_00233_gb300 import kpsb as K
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("kpsb_build_opts", K.BuildOpts), ("kpsb_sb_opts", K.SBOpts),
+             ("kpsb_sb_stats", K.SBStats), ("kpsb_problem", K.Problem), ("kpsb_sb_job", K.SBJob),
+             ("kpsb_request", K.Request), ("kpsb_srv_stats", K.SrvStats)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kpsb.h"', "int main(void) {"]
+    expect = []
+    for cname, cls in pairs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(cls))
+        for f, _ in cls._fields_:
+            field = "lambda" if f == "lambda_" else f
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {field}));')
+            expect.append(getattr(cls, f).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == expect
