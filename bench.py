@@ -43,7 +43,7 @@ WORKLOAD = ("n=128 images, 31x31 two-Gaussian-mixture PSF, reflexive boundary, E
             "automatic rank (tau=1e-3, cap 30), isotropic split Bregman 100 outer, noise 1%/5%")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--serve-count", type=int, default=12, help="serving block: requests per arrival rate")
     ap.add_argument("--cpu-worker", type=float, default=0.0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-samples", type=int, default=1, help=argparse.SUPPRESS)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------------------------------

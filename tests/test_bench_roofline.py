@@ -49,3 +49,34 @@ def test_table_bytes_follow_planes_and_element_size(mode, planes, es):
     r1 = _case(mode, 64, 1, 1, 1.0, 1000.0, 1000.0)
     r2 = _case(mode, 64, 2, 1, 1.0, 1000.0, 1000.0)
     assert math.isclose(r2["bytes"] - r1["bytes"], 2 * 64 * 64 * es * planes, rel_tol=1e-12)
+
+
+def _bench_commands(text):
+    """The bench.py argument lists of every `python bench.py ...` command in a text (shell
+    line continuations joined, the `python bench.py` prefix and environment assignments
+    dropped)."""
+    import re
+    import shlex
+
+    text = re.sub(r"\\\n\s*", " ", text)
+    out = []
+    for line in text.splitlines():
+        for m in re.finditer(r"python bench\.py([^|&;>]*)", line):
+            out.append(shlex.split(m.group(1).replace("$v", "0"), comments=True))
+    return out
+
+
+def test_profile_and_readme_commands_parse():
+    """Every bench command that a profile summary or the README gives is accepted by
+    bench.py's own argument parser (so the recorded commands stay runnable)."""
+    import glob
+    import os
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    files = sorted(glob.glob(os.path.join(root, "profiles", "*.txt"))) + [os.path.join(root, "README.md")]
+    seen = 0
+    for f in files:
+        for argv in _bench_commands(open(f).read()):
+            bench.parse(argv)  # argparse exits (SystemExit) on an unknown flag or value
+            seen += 1
+    assert seen >= 10
