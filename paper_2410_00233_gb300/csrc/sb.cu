@@ -770,12 +770,16 @@ static int gemm_prec_for(int n, int prec) {
   return prec == KPSB_P_FP64 ? KPSB_P_FP64 : KPSB_P_FP32;
 }
 
+// FP64 n^2 vectors of a problem's state: xprev, w, f, r1, r2, r3, z1, f1, dx, dy, gx, gy
+// (b and x are the caller's)
+static constexpr int SB_NVEC = 12;
+
 size_t sb_state_bytes(int n, int k, int prec) {
   const size_t N = (size_t)n * n;
   const int gp = gemm_prec_for(n, prec);
   const size_t zbytes = tc_supported(n, gp) ? 0 : a256(kp_z_bytes(n, k, gp));
   size_t tc_ws = tc_supported(n, gp) ? a256(tc_plan_ws_bytes(n, k, gp)) : 0;
-  return a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
+  return a256(SB_NVEC * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
          a256(sizeof(double) * sb_blocks(n) * 2) + 256 + tc_ws + a256(sizeof(float) * 5 * N) + 256;
 }
 
@@ -796,7 +800,7 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   // and FP32 results: any tensor-core precision, n a multiple of 32
   const bool fused = !dense && tc_supported(n, S->gemm_prec) && n % 32 == 0;
   const size_t xtbytes = fused ? a256(sizeof(float) * 5 * N) : 0;  // Xt planes + z1f + f1f + wf
-  S->bytes = a256(13 * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
+  S->bytes = a256(SB_NVEC * N * sizeof(double)) + zbytes + a256(sizeof(SBScal)) +
              a256(sizeof(double) * sb_blocks(n) * 2) + 256 + xtbytes;
   KPSB_TRY_CUDA(cudaMallocAsync((void**)&S->mem, S->bytes, st));
   char* q = S->mem;
@@ -820,7 +824,7 @@ kpsb_status sb_state_init(SBState* S, kpsb_kp* kp, const double* b_dev, double* 
   P.r3 = v + 5 * N; P.z1 = v + 6 * N; P.f1 = v + 7 * N; P.dx = v + 8 * N; P.dy = v + 9 * N;
   P.gx = v + 10 * N; P.gy = v + 11 * N;
   P.q = P.r2;  // the tensor-core path keeps q where the other paths keep r2 (and no r3)
-  q += a256(13 * N * sizeof(double));
+  q += a256(SB_NVEC * N * sizeof(double));
   S->Z = zbytes ? (void*)q : nullptr;
   q += zbytes;
   P.sc = (SBScal*)q;
