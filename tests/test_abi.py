@@ -134,3 +134,36 @@ def test_struct_layouts_match_the_header(tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
                                           text=True).stdout.split()]
     assert got == expect
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every entry point raises; there is no fallback path."""
+    import numpy as np
+
+    from paper_2410_00233_gb300 import kpsb as K
+
+    monkeypatch.setattr(K, "_lib", None)
+    monkeypatch.setattr(K, "LIB_PATH", str(tmp_path / "libkpsb.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        K.kp_build(np.ones((3, 3)) / 9, 8, K.BC_ZERO, 2, K.EGKB)
+    with pytest.raises(RuntimeError, match="missing"):
+        K.kpsb_kernel_launches()
+
+
+def test_package_never_imports_the_oracle():
+    """The product package (binding, inputs, cost model, sharding, build) has no import of
+    oracle/: the oracle is test infrastructure only."""
+    import ast
+
+    pkg = os.path.join(ROOT, "paper_2410_00233_gb300")
+    for f in sorted(os.listdir(pkg)):
+        if not f.endswith(".py"):
+            continue
+        tree = ast.parse(open(os.path.join(pkg, f)).read())
+        for node in ast.walk(tree):
+            names = []
+            if isinstance(node, ast.Import):
+                names = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                names = [node.module or ""]
+            assert not any(n == "oracle" or n.startswith("oracle.") for n in names), (f, names)
