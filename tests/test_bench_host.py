@@ -32,3 +32,33 @@ def test_percentiles_are_nearest_rank():
     assert bench._pct(vals, 0.0) == 1
     assert bench._pct([7.0], 0.99) == 7.0
     assert bench._pct([3, 1, 2], 0.5) == 2  # order of the input does not matter
+
+
+def test_clock_rows_give_median_max_and_reasons():
+    rows = "\n".join([
+        "0, 2070, 2070, 910.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1395.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",  # skipped
+        "garbage",
+    ])
+    c = bench.parse_clocks(rows)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = bench.parse_clocks("0, 1500, 2070, 1400, 0x40, Not Active, Active, Not Active, Not Active\n")
+    assert hot["reasons"] == ["hw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
+    assert bench.parse_clocks("") == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_clock_sampler_stop_reads_its_process():
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def communicate(self, timeout=None):
+            return "0, 2070, 2070, 1000, 0x0, Not Active, Not Active, Not Active, Not Active\n", ""
+
+    s = bench.ClockSampler.__new__(bench.ClockSampler)
+    s.proc, s.gpu = FakeProc(), 0
+    assert s.stop()["sm_mhz"] == 2070.0
+    s.proc = None
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
