@@ -32,7 +32,7 @@ against an independent fact (explicit matrices, scipy's 2-D convolution, LAPACK 
 full R(A), closed-form singular values, Van Loan-Pitsianis identity, Kronecker identity,
 brute-force convex solves, a Chambolle-Pock solve of the TV problem, dense normal
 equations, the Krylov-space minimiser of CGLS, Rayleigh-Ritz values of the RSVD range, GKB
-coefficients of a hand-built bidiagonal).  tests/oracle_mutations.py plants 65 plausible
+coefficients of a hand-built bidiagonal).  tests/oracle_mutations.py plants 86 plausible
 mistakes in a copy of this file one at a time; the pins catch every one.  None is marked
 "parity unpinned".
 """

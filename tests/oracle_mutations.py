@@ -136,6 +136,39 @@ MUTATIONS = [
     ("sb-rc-denominator", "RC_SB over ||x^(l-1)||", "rc_sb = np.linalg.norm(x_new - x) / nx",
      "rc_sb = np.linalg.norm(x_new - x) / np.linalg.norm(x_new)"),
     ("sb-stop", "stop when RC_SB < tau_SB", "if rc_sb < tau_sb:", "if rc_sb <= tau_sb * 10:"),
+    # more of the same families: centres, boundary rows, caps and thresholds, counters
+    ("ext-zero-outside", "zero boundary reads nothing outside", "    if bc == BC_ZERO:\n        return None",
+     "    if bc == BC_ZERO:\n        return 0"),
+    ("blur-centre", "centre tap at s // 2", "    s0, s1 = psf.shape\n    ca, cb = s0 // 2, s1 // 2\n    N = n * n",
+     "    s0, s1 = psf.shape\n    ca, cb = (s0 - 1) // 2, (s1 - 1) // 2\n    N = n * n"),
+    ("factors-centre", "centre tap at s // 2", "return RFactors(Kx=kmat(s1, s1 // 2), Ky=kmat(s0, s0 // 2)",
+     "return RFactors(Kx=kmat(s1, (s1 - 1) // 2), Ky=kmat(s0, (s0 - 1) // 2)"),
+    ("index-map-col-transposed", "column map of R(A)", "lst.extend([a] * int(round(My[a][r, rp])))",
+     "lst.extend([a] * int(round(My[a][rp, r])))"),
+    ("closed-form-Gy", "Gy = Ky^T Ky", "    Gy = (F.Ky.T @ F.Ky).toarray()\n    return np.linalg.svd",
+     "    Gy = (F.Kx.T @ F.Kx).toarray()\n    return np.linalg.svd"),
+    ("L-last-row", "zero last row of L", "    for i in range(n - 1):\n        L[i, i] = 0.5",
+     "    for i in range(n):\n        L[i, i] = 0.5"),
+    ("auto-k-cap", "k capped as soon as i reaches the cap", "            elif i >= k_cap:\n                k_sel = k_cap",
+     "            elif i > k_cap:\n                k_sel = k_cap"),
+    ("auto-k-kp", "k_p = k + p once k is chosen", "                if len(Q) >= kp:\n                    kp = len(Q)",
+     "                if len(Q) >= kp:\n                    kp = len(Q) + 1"),
+    ("breakdown-t", "breakdown only at rounding level", "if tj <= 100.0 * eps * bnorm:", "if tj <= 1e-3 * bnorm:"),
+    ("breakdown-alpha", "breakdown only at rounding level", "if aj <= 100.0 * eps * bnorm:", "if aj <= 1e-3 * bnorm:"),
+    ("egkb-k-not-truncated", "truncate to k terms", "k_eff = min(k_sel, kp_eff)", "k_eff = kp_eff"),
+    ("egkb-sigma-offset", "leading singular values of C", "sigma=sc[:k_eff]", "sigma=sc[1:k_eff + 1]"),
+    ("rsvd-sigma-offset", "leading singular values of H", "sigma=sh[:k]", "sigma=sh[1:k + 1]"),
+    ("rsvd-power-BT-dropped", "power step through B^T", "        Z, _ = np.linalg.qr(BT(Qb))",
+     "        Z, _ = np.linalg.qr(BT(Qb) * 0 + Qb)"),
+    ("terms-sigma-dropped", "sigma_i kept with the terms", "sigma=np.array(ts.sigma[:k], dtype=np.float64)",
+     "sigma=np.ones(k)"),
+    ("cgls-early-exit", "stop only when tau = 0", "        if tau_k == 0.0:\n            break",
+     "        if tau_k < 1e-3:\n            break"),
+    ("cgls-step-length", "mu = tau / ||z||^2", "mu = tau_k / zz  # step 4", "mu = tau_k / (zz + tau_k)  # step 4"),
+    ("shrink-no-sign", "shrink keeps the sign", "return np.sign(w) * np.maximum", "return np.abs(w) * 0 + np.maximum"),
+    ("sb-outer-count", "one outer step per loop", "        ell += 1\n        rec", "        ell += 2\n        rec"),
+    ("sb-iota", "iota_total sums the CGLS counts", "iota_total += res.iters", "iota_total += res.iters + 1"),
+    ("snr-noise", "noise = b - b_true", "np.sum((b_true - b) ** 2)", "np.sum((b_true + b) ** 2)"),
     # metrics (Sec. 5.3.2)
     ("rel-error-denominator", "RE over ||x_true||", "np.linalg.norm(x - x_true) / np.linalg.norm(x_true)",
      "np.linalg.norm(x - x_true) / np.linalg.norm(x)"),

@@ -114,6 +114,10 @@ def test_nu_rule_on_known_bidiagonal():
     # cap: k never exceeds the given cap
     ts3 = O.egkb(B, BT, e1, k=3, p=2, tau=1e-12)
     assert ts3.k == 3 and ts3.kp == 5
+    # the cap is taken as soon as i reaches it, also when the rule would fire one step later
+    # (nu_6 > nu_5 would give k = 5 here)
+    ts4 = O.egkb(B, BT, e1, k=4, p=2, tau=1e-12)
+    assert ts4.k == 4 and ts4.kp == 6
 
 
 def test_nu_rule_ignores_a_single_rise_of_zeta():
