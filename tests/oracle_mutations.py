@@ -24,7 +24,7 @@ from concurrent.futures import ThreadPoolExecutor
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle", "kpsb_oracle.py")
 PINS = ["test_oracle_golden.py", "test_oracle_operator.py", "test_oracle_sb.py",
-        "test_oracle_tsvd.py"]
+        "test_oracle_tsvd.py", "test_oracle_properties.py"]
 
 # (name, what it breaks, text in the oracle, replacement)
 MUTATIONS = [
