@@ -148,7 +148,9 @@ typedef struct {
  * The effective k may be smaller than asked when R(A) has smaller rank (R(A) = Kx P^T Ky^T,
  * so rank R(A) <= rank P <= min(s0, s1)):
  * the GKB recurrence stops at breakdown and RSVD drops null directions; kp_info reports
- * the k and k_p used.  Errors: EINVAL (sizes, n < 2, s > 2n, k < 1, k_p > 64),
+ * the k and k_p used.  Errors: EINVAL (n outside [2, KPSB_MAX_N], a PSF side outside
+ * [1, 1024], a reflexive PSF overhang beyond the image, k < 1, k_p = k + p > 64, automatic
+ * rank with RSVD; a zero-boundary PSF may be larger than the image),
  * ENOMEM, ECUDA, EBREAKDOWN (R(A) = 0).
  * Single-precision EGKB with n <= 128 and a PSF of at most 4096 entries (sides <= 128) runs
  * as one thread block per problem (the whole recurrence, the SVD of C and the Ritz vectors
